@@ -1,0 +1,309 @@
+"""FP64 CPU oracle of preconditioned Wirtinger flow (PWF), arXiv 2503.20146.
+
+TEST INFRASTRUCTURE ONLY. This module is imported by ``tests/``, by
+``__graft_entry__.smoke()`` and by the CPU-baseline / reference leg of
+``bench.py``. The CUDA library never calls it, links it or imports it, and it
+shares no code with the CUDA path: only the seeded input generators of
+``paper_2503_20146_gb300.synth`` serve both.
+
+What it computes, in the paper's order and notation:
+  * Algorithm S1 (PWF): psi = 0, phi = 0, mu = 1; per iteration the physical
+    model, residual e = y - f, Wirtinger derivative, preconditioner plus
+    regularizer, and Nesterov's update.
+  * Algorithm S2: PhysicalModel, WirtingerDerivative, Preconditioner,
+    Regularizer, FreePropagation and Filter.
+  * Eq. (1) forward model, Eq. (2) loss, Eq. (5) IOTF, Eq. (11)
+    preconditioning filter, Eqs. (14)-(15) STF and regularization window.
+Every array is complex128 / float64; numpy's FFT is the one library primitive
+(Filter of Algorithm S2 is F^-1{F{x} W}, circular, no padding).
+
+Readings where the paper is silent or ambiguous (each is listed in the design doc):
+  R1  FreePropagation: Q = exp(i 2 pi w L) carries the constant piston
+      exp(i 2 pi L / lambda). It is a global phase that cancels in |v|^2 and in
+      the back-propagation, so it is dropped, and w - 1/lambda is evaluated in
+      the cancellation-free form -rho^2 / (1/lambda + w).
+  R2  Bins with rho^2 > lambda^-2 (evanescent) get Q = 0. None occur at the
+      geometries used here, so P(-L) = conj(Q) = the exact adjoint.
+  R3  Frequencies u, v are numpy fftfreq in cycles per metre for Q, IOTF and
+      STF (they multiply lengths in metres). For the preconditioner P^-1 =
+      1/(u^2 + v^2) the units are not stated; it is evaluated in cycles per
+      PIXEL, so P^-1 ranges over [2, N^2]. The overall scale is the step size's.
+  R4  x_coh = y_coh = 0 means a fully coherent beam: IOTF = 1, STF = 1 and the
+      regularization window Gamma^2 = 0 (the regularizer vanishes).
+  R5  Filter of a real field (the intensity, the residual, Im g) keeps the real
+      part of the inverse transform.
+  R6  The stopping test compares the object fields x = exp(psi) of successive
+      iterations by |<x_k, x_{k-1}>| / (||x_k|| ||x_{k-1}||); the threshold is
+      10^(-0.00001) (Reconstruction procedure, Methods).
+  R7  The gradient w.r.t. the diffuser (simultaneous retrieval, Methods and
+      Fig. S12) is not printed; it is derived here from Eq. (1) in the same
+      Wirtinger convention as the sample gradient.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+STOP_CORRELATION = 10.0 ** (-0.00001)
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """Inputs of Algorithm S1 other than y and t.
+
+    Lengths in metres. ``xcoh``/``ycoh`` are the coherence lengths of Eqs. (4),
+    (5) and (14); zero means fully coherent (reading R4).
+    """
+    ny: int
+    nx: int
+    pixel: float
+    wavelength: float
+    L1: float
+    L2: float
+    xcoh: float = 0.0
+    ycoh: float = 0.0
+    gamma: float = 1.0
+    alpha: complex = 0.1 + 0.01j
+    eta: float = 1.0
+
+
+# ----------------------------------------------------------------------------
+# Spatial frequencies and the filters of Algorithm S1's input list
+# ----------------------------------------------------------------------------
+def frequencies(geom: Geometry):
+    """(u, v) grids in cycles/m, u along x (columns), v along y (rows)."""
+    u = np.fft.fftfreq(geom.nx, d=geom.pixel)[None, :]
+    v = np.fft.fftfreq(geom.ny, d=geom.pixel)[:, None]
+    return u, v
+
+
+def transfer_function(geom: Geometry, L: float) -> np.ndarray:
+    """Q_k of FreePropagation (Algorithm S2), piston removed (reading R1).
+
+    w = sqrt(lambda^-2 - u^2 - v^2); Q = exp(i 2 pi (w - 1/lambda) L) with
+    w - 1/lambda = -rho^2 / (1/lambda + w), an exact identity.
+    """
+    u, v = frequencies(geom)
+    inv_lam = 1.0 / geom.wavelength
+    rho2 = u * u + v * v
+    arg = inv_lam * inv_lam - rho2
+    prop = arg > 0
+    w = np.sqrt(np.where(prop, arg, 0.0))
+    w_minus = -rho2 / (inv_lam + w)
+    Q = np.exp(1j * 2.0 * np.pi * w_minus * L)
+    return np.where(prop, Q, 0.0)          # reading R2
+
+
+def transfer_function_literal(geom: Geometry, L: float) -> np.ndarray:
+    """Q = exp(i 2 pi w L) exactly as printed, piston included (for the R1 pin)."""
+    u, v = frequencies(geom)
+    w = np.sqrt(1.0 / geom.wavelength ** 2 - u * u - v * v)
+    return np.exp(1j * 2.0 * np.pi * w * L)
+
+
+def iotf(geom: Geometry) -> np.ndarray:
+    """IOTF_k = exp[-pi/2 (u^2 x_coh^2 + v^2 y_coh^2)], Eq. (5)."""
+    u, v = frequencies(geom)
+    return np.exp(-0.5 * np.pi * (u * u * geom.xcoh ** 2 + v * v * geom.ycoh ** 2))
+
+
+def precond_filter(geom: Geometry) -> np.ndarray:
+    """P^-1_k = 1/(u^2 + v^2), zero at u = v = 0, Eq. (11); cycles/pixel (R3)."""
+    u = np.fft.fftfreq(geom.nx)[None, :]
+    v = np.fft.fftfreq(geom.ny)[:, None]
+    rho2 = u * u + v * v
+    out = np.zeros((geom.ny, geom.nx))
+    nz = rho2 > 0
+    out[nz] = 1.0 / rho2[nz]
+    return out
+
+
+def stf(geom: Geometry) -> np.ndarray:
+    """STF_k = exp[-pi gamma (u^2 x_coh^2 + v^2 y_coh^2)], Eq. (14)."""
+    u, v = frequencies(geom)
+    return np.exp(-np.pi * geom.gamma * (u * u * geom.xcoh ** 2 + v * v * geom.ycoh ** 2))
+
+
+def reg_window(geom: Geometry) -> np.ndarray:
+    """Gamma^2_k = 1 - STF_k, Eq. (15)."""
+    return 1.0 - stf(geom)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm S2
+# ----------------------------------------------------------------------------
+def Filter(x: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """x <- F^-1{ F{x} W } (Algorithm S2, Filter)."""
+    return np.fft.ifft2(np.fft.fft2(x) * W)
+
+
+def FreePropagation(x: np.ndarray, geom: Geometry, L: float) -> np.ndarray:
+    """Angular-spectrum propagation over distance L (Algorithm S2)."""
+    return Filter(x, transfer_function(geom, L))
+
+
+def PhysicalModel(psi: np.ndarray, t: np.ndarray, geom: Geometry):
+    """f(x), x, v of Algorithm S2 / Eq. (1)."""
+    x = np.exp(psi)
+    v = FreePropagation(x, geom, geom.L1)          # sample to diffuser
+    v = FreePropagation(t * v, geom, geom.L2)      # diffuser to detector
+    f = Filter(np.abs(v) ** 2, iotf(geom)).real    # IPSF convolution (R5)
+    return f, x, v
+
+
+def WirtingerDerivative(e, x, v, t, geom: Geometry) -> np.ndarray:
+    """g of Algorithm S2: Filter(-e, IOTF), times v, back over L2, times t*,
+    back over L1, times x*, divided by max |t|^2."""
+    g = Filter(-e, iotf(geom)).real                # R5
+    g = FreePropagation(v * g, geom, -geom.L2)
+    g = FreePropagation(np.conj(t) * g, geom, -geom.L1)
+    g = np.conj(x) * g
+    g = g / np.max(np.abs(t) ** 2)
+    return g
+
+
+def Preconditioner(g: np.ndarray, Pinv: np.ndarray) -> np.ndarray:
+    """Filter Im g with P^-1; keep Re g (Algorithm S2, Eq. (11))."""
+    g2 = g.imag
+    g2 = Filter(g2, Pinv).real                     # R5
+    return g.real + 1j * g2
+
+
+def Regularizer(psi: np.ndarray, Gamma2: np.ndarray, alpha: complex) -> np.ndarray:
+    """rho = Filter(psi, Gamma^2); Re(alpha) Re(rho) + i Im(alpha) Im(rho)."""
+    rho = Filter(psi, Gamma2)
+    return alpha.real * rho.real + 1j * alpha.imag * rho.imag
+
+
+def loss(y: np.ndarray, f: np.ndarray) -> float:
+    """Sum_r (y_r - f_r)^2, Eq. (2)."""
+    return float(np.sum((y - f) ** 2))
+
+
+def correlation(x_new: np.ndarray, x_old: np.ndarray) -> float:
+    """Normalised correlation of successive fields (reading R6)."""
+    num = np.abs(np.vdot(x_old, x_new))
+    den = np.sqrt(np.vdot(x_new, x_new).real * np.vdot(x_old, x_old).real)
+    return float(num / den)
+
+
+def nesterov_mu(mu: float) -> float:
+    """mu <- (1 + sqrt(1 + 4 mu^2)) / 2 (Algorithm S1)."""
+    return (1.0 + np.sqrt(1.0 + 4.0 * mu * mu)) / 2.0
+
+
+# ----------------------------------------------------------------------------
+# Algorithm S1
+# ----------------------------------------------------------------------------
+@dataclass
+class PWFResult:
+    psi: np.ndarray
+    iterations: int
+    losses: list          # loss of the model at the start of each iteration
+    correlations: list    # correlation after each iteration
+
+
+def pwf_iteration(psi, phi, mu, y, t, geom: Geometry, Pinv=None, Gamma2=None):
+    """One pass of the while-loop body of Algorithm S1.
+
+    Returns (psi_new, phi_new, mu_new, loss_before).
+    """
+    if Pinv is None:
+        Pinv = precond_filter(geom)
+    if Gamma2 is None:
+        Gamma2 = reg_window(geom)
+    phi_prev = phi
+    mu_prev = mu
+    f, x, v = PhysicalModel(psi, t, geom)
+    e = y - f
+    g = WirtingerDerivative(e, x, v, t, geom)
+    g = Preconditioner(g, Pinv) + Regularizer(psi, Gamma2, geom.alpha)
+    phi = psi - geom.eta * g
+    mu = nesterov_mu(mu)
+    psi_new = phi + ((mu_prev - 1.0) / mu) * (phi - phi_prev)
+    return psi_new, phi, mu, loss(y, f)
+
+
+def pwf(y: np.ndarray, t: np.ndarray, geom: Geometry, max_iter: int,
+        corr_tol: float | None = None, psi0: np.ndarray | None = None) -> PWFResult:
+    """Algorithm S1. ``corr_tol`` None runs exactly ``max_iter`` iterations;
+    otherwise the loop also stops once the correlation exceeds ``corr_tol``."""
+    psi = np.zeros((geom.ny, geom.nx), np.complex128) if psi0 is None else psi0.astype(np.complex128)
+    phi = np.zeros_like(psi)
+    mu = 1.0
+    Pinv, Gamma2 = precond_filter(geom), reg_window(geom)
+    losses, corrs = [], []
+    it = 0
+    while it < max_iter:
+        x_old = np.exp(psi)
+        psi, phi, mu, L = pwf_iteration(psi, phi, mu, y, t, geom, Pinv, Gamma2)
+        it += 1
+        losses.append(L)
+        c = correlation(np.exp(psi), x_old)
+        corrs.append(c)
+        if corr_tol is not None and c > corr_tol:
+            break
+    return PWFResult(psi, it, losses, corrs)
+
+
+# ----------------------------------------------------------------------------
+# Gradient and vector-Jacobian products in PyTorch's convention
+# ----------------------------------------------------------------------------
+def gradient(psi, t, y, geom: Geometry):
+    """(g, loss) with g the raw WirtingerDerivative output of Algorithm S2."""
+    f, x, v = PhysicalModel(psi, t, geom)
+    e = y - f
+    return WirtingerDerivative(e, x, v, t, geom), loss(y, f)
+
+
+def loss_gradient_real(psi, t, y, geom: Geometry):
+    """dL/dRe(psi) + i dL/dIm(psi) of Eq. (2).
+
+    Algorithm S2 drops the factor 2 of the Wirtinger calculus (Preconditioning
+    filter section) and divides by max|t|^2, so the true gradient of the loss
+    is 4 max|t|^2 g.
+    """
+    g, L = gradient(psi, t, y, geom)
+    return 4.0 * np.max(np.abs(t) ** 2) * g, L
+
+
+def forward_vjp(psi, t, grad_f, geom: Geometry):
+    """Vector-Jacobian product of f = PhysicalModel(psi, t) for a real cotangent.
+
+    Returns (grad_psi, grad_t) in the convention dL/dRe + i dL/dIm, for a
+    scalar L with dL/df = grad_f. grad_psi reuses WirtingerDerivative with
+    e = -grad_f / 2 (then scaled by 4 max|t|^2). grad_t (reading R7):
+    f depends on t through v = P2{t u1}, u1 = P1{x}; dL = 2 Re<v G, P2{dt u1}>
+    with G = Filter(grad_f, IOTF), so grad_t = 2 conj(u1) P2^H{v G}.
+    """
+    f, x, v = PhysicalModel(psi, t, geom)
+    m = np.max(np.abs(t) ** 2)
+    grad_psi = 4.0 * m * WirtingerDerivative(-0.5 * grad_f, x, v, t, geom)
+    u1 = FreePropagation(x, geom, geom.L1)
+    G = Filter(grad_f, iotf(geom)).real
+    g2 = FreePropagation(v * G, geom, -geom.L2)
+    grad_t = 2.0 * np.conj(u1) * g2
+    return grad_psi, grad_t
+
+
+# ----------------------------------------------------------------------------
+# Batched helpers (independent projections, shared diffuser)
+# ----------------------------------------------------------------------------
+def physical_model_batch(psi_b, t, geom: Geometry) -> np.ndarray:
+    return np.stack([PhysicalModel(p, t, geom)[0] for p in psi_b])
+
+
+def gradient_batch(psi_b, t, y_b, geom: Geometry):
+    gs, Ls = zip(*[gradient(p, t, y, geom) for p, y in zip(psi_b, y_b)])
+    return np.stack(gs), np.array(Ls)
+
+
+def forward_vjp_batch(psi_b, t, grad_f_b, geom: Geometry):
+    """grad_t is summed over the batch: the diffuser is shared."""
+    gp, gt = zip(*[forward_vjp(p, t, gf, geom) for p, gf in zip(psi_b, grad_f_b)])
+    return np.stack(gp), np.sum(np.stack(gt), axis=0)
+
+
+def pwf_batch(y_b, t, geom: Geometry, max_iter: int, corr_tol=None):
+    return [pwf(y, t, geom, max_iter, corr_tol) for y in y_b]
