@@ -1,0 +1,160 @@
+/*
+ * pwf.h — C ABI of the GB300 (sm_103a) preconditioned Wirtinger flow library.
+ *
+ * Method: K. Lee, H. Hugonnet, J.-H. Lim, Y. Park, "Speckle-based X-ray
+ * microtomography via preconditioned Wirtinger flow", arXiv 2503.20146.
+ * Algorithm S1 (PWF) and Algorithm S2 (PhysicalModel, WirtingerDerivative,
+ * Preconditioner, Regularizer, FreePropagation, Filter); forward model Eq. (1);
+ * loss Eq. (2); IOTF Eq. (5); preconditioning filter Eq. (11); sample transfer
+ * function and regularization window Eqs. (14)-(15).
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are caller-owned DEVICE memory unless a parameter says "host".
+ *    Complex arrays are interleaved complex64 (float re, float im), row-major
+ *    [batch][ny][nx], 8-byte aligned at least (16-byte recommended). Real
+ *    arrays are float32 [batch][ny][nx]. The diffuser t is one complex64
+ *    [ny][nx] field shared by every projection of the batch.
+ *  - ny and nx are each one of 16, 32, 64, 96, 128, 256, 512, 768, 1024, 1536,
+ *    2048 (other sizes return PWF_ERR_UNSUPPORTED).
+ *  - Work is enqueued on the plan's stream (pwf_plan_desc.stream, a
+ *    cudaStream_t; NULL means the legacy default stream) and runs
+ *    asynchronously, except where a parameter is a host output: then the call
+ *    synchronises the stream before returning.
+ *  - No entry point throws. Errors are returned as pwf_status; the first CUDA
+ *    error seen by a plan is sticky and returned by every later call on it.
+ *  - A plan owns its workspace (a few complex fields per projection) and its
+ *    1-D filter tables. Plans are not thread-safe; use one per host thread.
+ */
+#ifndef PWF_H
+#define PWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PWF_OK = 0,
+  PWF_ERR_INVALID_ARG = 1,  /* null pointer, non-positive size, bad flag value */
+  PWF_ERR_UNSUPPORTED = 2,  /* transform length not built, or geometry outside the
+                               separable-propagator bound (see pwf_plan_create) */
+  PWF_ERR_NOMEM = 3,        /* device allocation failed */
+  PWF_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  PWF_ERR_NONFINITE = 5,    /* a non-finite loss was produced */
+  PWF_ERR_STATE = 6         /* state / plan mismatch or bad checkpoint buffer */
+} pwf_status;
+
+typedef struct pwf_plan pwf_plan;
+typedef struct pwf_state pwf_state;
+
+/* plan flags (ablations of Figs. S3-S5 and the unfused baseline) */
+#define PWF_FLAG_NO_PRECOND 0x1u /* P^-1 := 1 (Preconditioner off, Fig. S3)        */
+#define PWF_FLAG_NO_REG 0x2u     /* alpha := 0 (Regularizer off)                   */
+#define PWF_FLAG_PLAIN 0x4u      /* unfused per-operation kernels, one projection at
+                                    a time: Algorithm S2 executed step by step     */
+
+/* Inputs of Algorithm S1 other than y and t. All lengths in metres. */
+typedef struct {
+  int32_t batch;     /* number of independent projections B >= 1 */
+  int32_t ny, nx;    /* detector grid */
+  double pixel_m;    /* detector pixel pitch p */
+  double wavelength_m;
+  double L1_m;       /* sample -> diffuser */
+  double L2_m;       /* diffuser -> detector */
+  double xcoh_m, ycoh_m; /* coherence lengths of Eqs. (4), (5), (14); both 0 = fully
+                            coherent: IOTF = 1 and Gamma^2 = 0 */
+  double gamma;      /* oversampling ratio of Eq. (14) (paper: 1) */
+  double alpha_re, alpha_im; /* regularization parameter (paper: 0.1 + 0.01i) */
+  double eta;        /* step size of Algorithm S1 */
+  uint32_t flags;    /* PWF_FLAG_* */
+  void* stream;      /* cudaStream_t */
+} pwf_plan_desc;
+
+/* Creates a plan. Builds the 1-D frequency tables of Q_k = exp(i 2 pi (w - 1/lambda) L)
+ * (FreePropagation of Algorithm S2, constant piston dropped), IOTF (Eq. (5)),
+ * P^-1 = 1/(u^2 + v^2) in cycles per pixel with P^-1(0) = 0 (Eq. (11)) and
+ * Gamma^2 = 1 - STF (Eqs. (14)-(15)). The propagator phase is applied as the sum
+ * of its two axis restrictions; the plan checks, in double precision, that the
+ * neglected cross term is below 1e-6 rad over the grid (it is ~1e-8 rad for
+ * hard X-rays on micron pixels) and returns PWF_ERR_UNSUPPORTED otherwise.
+ * Returns PWF_ERR_UNSUPPORTED also for evanescent bins (rho^2 >= lambda^-2).
+ * *out receives the plan; it must be released with pwf_plan_destroy. */
+pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out);
+pwf_status pwf_plan_destroy(pwf_plan* plan);
+/* Replaces the stream used by later calls on this plan. */
+pwf_status pwf_plan_set_stream(pwf_plan* plan, void* stream);
+/* Bytes of device workspace the plan holds. */
+size_t pwf_plan_workspace_bytes(const pwf_plan* plan);
+
+/* f = PhysicalModel(psi, t) of Algorithm S2 / Eq. (1):
+ *   x = exp(psi); v = P2{ t P1{x} }; f = Re Filter(|v|^2, IOTF).
+ * psi: complex64 [B][ny][nx]; t: complex64 [ny][nx]; f: float32 [B][ny][nx]. */
+pwf_status pwf_forward(pwf_plan* plan, const void* psi, const void* t, float* f);
+
+/* g = WirtingerDerivative(y - f(psi), x, v, t) of Algorithm S2 (the raw,
+ * unpreconditioned gradient, divided by max |t|^2) and the loss of Eq. (2).
+ * g: complex64 [B][ny][nx]; loss: device float64 [B] (may be NULL).
+ * The gradient of the loss w.r.t. Re psi and Im psi is 4 max|t|^2 (Re g, Im g). */
+pwf_status pwf_gradient(pwf_plan* plan, const void* psi, const void* t, const float* y,
+                        void* g, double* loss);
+
+/* Vector-Jacobian product of f = PhysicalModel(psi, t) for a real cotangent
+ * grad_f = dL/df (float32 [B][ny][nx]), in the convention dL/dRe + i dL/dIm:
+ *   grad_psi = 2 conj(x) P1^H{ conj(t) P2^H{ v Filter(grad_f, IOTF) } }
+ *   grad_t   = sum over the batch of 2 conj(P1{x}) P2^H{ v Filter(grad_f, IOTF) }
+ * (the second is the diffuser gradient of the simultaneous retrieval of
+ * Methods / Fig. S12). grad_psi: complex64 [B][ny][nx] (may be NULL);
+ * grad_t: complex64 [ny][nx] (may be NULL). Intermediate fields are recomputed
+ * from psi and t, not taken from an earlier pwf_forward. */
+pwf_status pwf_forward_vjp(pwf_plan* plan, const void* psi, const void* t, const float* grad_f,
+                           void* grad_psi, void* grad_t);
+
+/* Solver state of Algorithm S1: phi (the previous Nesterov point), mu, the
+ * iteration count, per-projection convergence flags and the last loss and
+ * correlation. */
+pwf_status pwf_state_create(pwf_plan* plan, pwf_state** out);
+pwf_status pwf_state_destroy(pwf_state* state);
+/* phi := 0, mu := 1, iteration := 0, every projection active (Algorithm S1 set-up). */
+pwf_status pwf_state_reset(pwf_plan* plan, pwf_state* state);
+
+/* One iteration of the while-loop of Algorithm S1 on every still-active
+ * projection, updating psi (complex64 [B][ny][nx], in place) and the state.
+ * corr_tol > 0 enables the stopping rule of Methods ("Reconstruction
+ * procedure"): a projection whose normalized correlation between exp(psi) of
+ * this and the previous iteration exceeds corr_tol stops (its psi is left
+ * as the converged value). corr_tol <= 0 never stops. */
+pwf_status pwf_step(pwf_plan* plan, pwf_state* state, const float* y, const void* t, void* psi,
+                    double corr_tol);
+
+/* Reads per-projection results of the last iteration into HOST arrays of
+ * length B (any may be NULL): loss of Eq. (2) before the update, correlation,
+ * iterations done, and 1/0 active flags. Synchronises the stream. */
+pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_host,
+                          double* corr_host, int32_t* iters_host, int32_t* active_host);
+
+/* Algorithm S1 from the caller's psi (Algorithm S1 starts from psi = 0; the
+ * caller zeroes psi for that): up to max_iter iterations, with the stopping
+ * rule when corr_tol > 0. Fused, batched kernels replayed from a CUDA graph.
+ * iters_host / loss_host: HOST arrays of length B (may be NULL); when either is
+ * given the call synchronises. psi is updated in place. */
+pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
+                     double corr_tol, int32_t* iters_host, double* loss_host);
+
+/* Checkpoint: pwf_state_bytes gives the size of a host buffer that holds the
+ * state (phi and the counters); save/load copy it. Loading into a state of a
+ * plan with other sizes returns PWF_ERR_STATE. Both synchronise. */
+size_t pwf_state_bytes(const pwf_state* state);
+pwf_status pwf_state_save(pwf_plan* plan, const pwf_state* state, void* host_buf, size_t bytes);
+pwf_status pwf_state_load(pwf_plan* plan, pwf_state* state, const void* host_buf, size_t bytes);
+
+/* Human-readable name of a status code (static storage). */
+const char* pwf_status_string(pwf_status s);
+/* Last error message recorded on the plan (static per plan; never NULL). */
+const char* pwf_plan_last_error(const pwf_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWF_H */

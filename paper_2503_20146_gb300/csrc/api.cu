@@ -1,0 +1,1033 @@
+// C ABI of the PWF library: plans, filter tables, the pass schedules of
+// Algorithms S1/S2, the solver state, CUDA-graph replay of the fused iteration,
+// and the unfused per-operation baseline.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pwf.h"
+#include "passes.cuh"
+
+namespace pwf {
+const LengthKernels* length_kernels_16();
+const LengthKernels* length_kernels_32();
+const LengthKernels* length_kernels_64();
+const LengthKernels* length_kernels_96();
+const LengthKernels* length_kernels_128();
+const LengthKernels* length_kernels_256();
+const LengthKernels* length_kernels_512();
+const LengthKernels* length_kernels_768();
+const LengthKernels* length_kernels_1024();
+const LengthKernels* length_kernels_1536();
+const LengthKernels* length_kernels_2048();
+
+const LengthKernels* kernels_for_length(int n) {
+  switch (n) {
+    case 16: return length_kernels_16();
+    case 32: return length_kernels_32();
+    case 64: return length_kernels_64();
+    case 96: return length_kernels_96();
+    case 128: return length_kernels_128();
+    case 256: return length_kernels_256();
+    case 512: return length_kernels_512();
+    case 768: return length_kernels_768();
+    case 1024: return length_kernels_1024();
+    case 1536: return length_kernels_1536();
+    case 2048: return length_kernels_2048();
+    default: return nullptr;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+// max over the diffuser of |t|^2 (Algorithm S2, WirtingerDerivative). Values
+// are non-negative floats, whose bit patterns order like integers.
+__global__ void k_max_abs2(const float2* __restrict__ t, size_t n, float* out) {
+  float m = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, cabs2(t[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
+struct DevIter {
+  double mu;       // mu of Algorithm S1 after the last completed iteration
+  float beta;      // (mu_prev - 1)/mu for the next iteration
+  int iter;        // completed iterations
+  int n_active;    // projections still iterating
+  int nonfinite;   // a non-finite loss was seen
+};
+
+// End of one iteration: per-projection loss / correlation / stopping rule,
+// accumulator reset, and the Nesterov coefficients of the next iteration.
+__global__ void k_finalize(double* acc, int B, int* active, int* iters, double* loss, double* corr,
+                           DevIter* it, double corr_tol) {
+  __shared__ int s_active;
+  if (threadIdx.x == 0) s_active = 0;
+  __syncthreads();
+  int na = 0, nf = 0;
+  for (int p = threadIdx.x; p < B; p += blockDim.x) {
+    double* a = acc + (size_t)p * NACC;
+    if (active[p]) {
+      const double L = a[ACC_LOSS];
+      const double c = sqrt(a[ACC_XR] * a[ACC_XR] + a[ACC_XI] * a[ACC_XI]) / sqrt(a[ACC_XNEW] * a[ACC_XOLD]);
+      loss[p] = L;
+      corr[p] = c;
+      iters[p] += 1;
+      if (!isfinite(L)) nf = 1;
+      if (corr_tol > 0.0 && c > corr_tol) active[p] = 0;
+      else na += 1;
+    }
+    for (int k = 0; k < NACC; k++) a[k] = 0.0;
+  }
+  atomicAdd(&s_active, na);
+  if (nf) it->nonfinite = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double mu_prev = it->mu;
+    const double mu = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu_prev * mu_prev));
+    const double mu_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu * mu));
+    it->mu = mu;
+    it->beta = (float)((mu - 1.0) / mu_next);
+    it->iter += 1;
+    it->n_active = s_active;
+  }
+}
+
+__global__ void k_state_reset(DevIter* it, int* active, int* iters, double* loss, double* corr, int B) {
+  for (int p = threadIdx.x; p < B; p += blockDim.x) {
+    active[p] = 1;
+    iters[p] = 0;
+    loss[p] = 0.0;
+    corr[p] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    it->mu = 1.0;
+    it->beta = 0.0f;
+    it->iter = 0;
+    it->n_active = B;
+    it->nonfinite = 0;
+  }
+}
+
+__global__ void k_gather_loss(const double* acc, double* loss, int B) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < B) loss[p] = acc[(size_t)p * NACC + ACC_LOSS];
+}
+
+// grad_t = sum over the batch of the per-projection terms
+__global__ void k_batch_sum(const float2* __restrict__ s, float2* __restrict__ out, int B, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int b = 0; b < B; b++) a = cadd(a, s[(size_t)b * n + i]);
+    out[i] = a;
+  }
+}
+
+// ---- unfused per-operation kernels (the plain baseline) ----
+enum PlainFilter : int { PF_Q = 0, PF_IOTF = 1, PF_PINV = 2, PF_GAMMA2 = 3 };
+
+__global__ void k_exp(const float2* __restrict__ psi, float2* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = cexpf2(psi[i]);
+}
+__global__ void k_filter(float2* X, int ny, int nx, int which, const float2* qx, const float2* qy, int conj,
+                         const float* ix, const float* iy, const float* u2x, const float* u2y, const float* ex,
+                         const float* ey, int no_precond) {
+  const size_t n = (size_t)ny * nx;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nx), ky = (int)(i / nx);
+    float2 v = X[i];
+    if (which == PF_Q) {
+      float2 q = cmul(qx[kx], qy[ky]);
+      if (conj) q = cconj(q);
+      v = cmul(v, q);
+    } else if (which == PF_IOTF) {
+      v = cscale(v, ix[kx] * iy[ky]);
+    } else if (which == PF_PINV) {
+      const float r2 = u2x[kx] + u2y[ky];
+      v = cscale(v, no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f));
+    } else {
+      v = cscale(v, -expm1f(-(ex[kx] + ey[ky])));
+    }
+    X[i] = v;
+  }
+}
+__global__ void k_mul_t(float2* X, const float2* __restrict__ t, size_t n, int conj) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = conj ? cmulc(X[i], t[i]) : cmul(X[i], t[i]);
+}
+// V = v; X = |v|^2
+__global__ void k_abs2_keep(float2* X, float2* V, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = X[i];
+    V[i] = v;
+    X[i] = make_float2(cabs2(v), 0.f);
+  }
+}
+// X = -(y - Re X), loss += (y - Re X)^2
+__global__ void k_resid(float2* X, const float* __restrict__ y, size_t n, double* loss) {
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float e = y[i] - X[i].x;
+    s = fmaf(e, e, s);
+    X[i] = make_float2(-e, 0.f);
+  }
+  double d = s;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, d);
+}
+// X = V * Re X
+__global__ void k_mul_v_real(float2* X, const float2* __restrict__ V, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = cscale(V[i], X[i].x);
+}
+// X = conj(exp psi) X / max|t|^2
+__global__ void k_grad(float2* X, const float2* __restrict__ psi, size_t n, const float* maxt2) {
+  const float s = 1.0f / *maxt2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = cscale(cmulc(X[i], cexpf2(psi[i])), s);
+}
+// REG = Re X; S = Im X (as a complex field with zero imaginary part)
+__global__ void k_split(const float2* __restrict__ X, float* reg, float2* S, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 g = X[i];
+    reg[i] = g.x;
+    S[i] = make_float2(g.y, 0.f);
+  }
+}
+__global__ void k_copy(const float2* __restrict__ a, float2* b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+// g = (Re g + i Re Filter(Im g, P^-1)) + (Re a Re rho + i Im a Im rho); Nesterov.
+__global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __restrict__ S,
+                                 const float2* __restrict__ H, float2* psi, float2* phi, size_t n, float eta,
+                                 float are, float aim, const float* beta_p, double* acc) {
+  const float beta = *beta_p;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 rho = H[i];
+    const float2 g = make_float2(reg[i] + are * rho.x, S[i].x + aim * rho.y);
+    const float2 p = psi[i], fp = phi[i];
+    const float2 f = make_float2(p.x - eta * g.x, p.y - eta * g.y);
+    const float2 pn = make_float2(f.x + beta * (f.x - fp.x), f.y + beta * (f.y - fp.y));
+    phi[i] = f;
+    psi[i] = pn;
+    const float2 xo = cexpf2(p), xn = cexpf2(pn);
+    const float2 c = cmulc(xn, xo);
+    p0 += c.x;
+    p1 += c.y;
+    p2 += cabs2(xn);
+    p3 += cabs2(xo);
+  }
+  double d[4] = {p0, p1, p2, p3};
+  for (int k = 0; k < 4; k++) {
+    for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[ACC_XR + k], d[k]);
+  }
+}
+
+}  // namespace pwf
+
+using namespace pwf;
+
+// ---------------------------------------------------------------------------
+// plan and state
+// ---------------------------------------------------------------------------
+struct AxisTables {
+  int n = 0;
+  float2* tw_fwd = nullptr;
+  float2* tw_inv = nullptr;
+  float2* q1 = nullptr;  // exp(i phi_{L1}) restricted to this axis
+  float2* q2 = nullptr;
+  float* iotf = nullptr;
+  float* u2 = nullptr;   // squared frequency, cycles per pixel
+  float* stf = nullptr;  // pi gamma u^2 coh^2
+};
+
+struct pwf_state {
+  int B = 0, ny = 0, nx = 0;
+  float2* phi = nullptr;
+  int* active = nullptr;
+  int* iters = nullptr;
+  double* loss = nullptr;
+  double* corr = nullptr;
+  DevIter* it = nullptr;
+};
+
+struct pwf_plan {
+  pwf_plan_desc d{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  const LengthKernels* krow = nullptr;  // length nx
+  const LengthKernels* kcol = nullptr;  // length ny
+  AxisTables ax, ay;
+  bool coherent = false;
+  // workspace
+  float2* X = nullptr;
+  float2* V = nullptr;
+  float2* S = nullptr;
+  float* REG = nullptr;
+  float2* YH = nullptr;
+  double* acc = nullptr;
+  float* maxt2 = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+  // solver
+  pwf_state* solve_state = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  double graph_tol = 0.0;
+  pwf_status sticky = PWF_OK;
+  char err[256] = "";
+};
+
+namespace {
+
+pwf_status fail(pwf_plan* p, pwf_status s, const char* msg) {
+  if (p) {
+    std::snprintf(p->err, sizeof(p->err), "%s", msg);
+    if (s == PWF_ERR_CUDA && p->sticky == PWF_OK) p->sticky = s;
+  }
+  return s;
+}
+
+pwf_status cuda_fail(pwf_plan* p, cudaError_t e, const char* where) {
+  if (p) {
+    std::snprintf(p->err, sizeof(p->err), "%s: %s", where, cudaGetErrorString(e));
+    if (p->sticky == PWF_OK) p->sticky = PWF_ERR_CUDA;
+  }
+  return PWF_ERR_CUDA;
+}
+
+#define PWF_CUDA(p, call)                                   \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return cuda_fail((p), e__, #call); \
+  } while (0)
+
+template <class T>
+pwf_status dalloc(pwf_plan* p, T** ptr, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, PWF_ERR_NOMEM, "device allocation failed");
+  }
+  p->allocs.push_back(q);
+  p->ws_bytes += count * sizeof(T);
+  *ptr = static_cast<T*>(q);
+  return PWF_OK;
+}
+
+double fftfreq(int k, int n) { return (double)(k < (n + 1) / 2 ? k : k - n) / (double)n; }  // cycles per sample
+
+// 2 pi L (w - 1/lambda), w = sqrt(lambda^-2 - rho2), in the cancellation-free form
+double prop_phase(double rho2, double lambda, double L) {
+  const double il = 1.0 / lambda;
+  const double w = std::sqrt(il * il - rho2);
+  return 2.0 * M_PI * L * (-rho2 / (il + w));
+}
+
+pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double coh) {
+  A.n = n;
+  const pwf_plan_desc& d = p->d;
+  // the inverse runs the radices in reverse order, so its table length differs
+  const int tlf = twiddle_len(n, FWD) > 0 ? twiddle_len(n, FWD) : 1;
+  const int tli = twiddle_len(n, INV) > 0 ? twiddle_len(n, INV) : 1;
+  std::vector<float2> twf(tlf, make_float2(1.f, 0.f)), twi(tli, make_float2(1.f, 0.f));
+  const Sched s = sched_for(n);
+  for (int dir = 0; dir < 2; dir++) {
+    const int D = dir == 0 ? FWD : INV;
+    for (int k = 1; k < s.s; k++) {
+      const int R = stage_radix(n, D, k), NS = stage_ns(n, D, k), off = stage_twoff(n, D, k);
+      std::vector<float2>& tab = dir == 0 ? twf : twi;
+      for (int r = 1; r < R; r++)
+        for (int j = 0; j < NS; j++) {
+          const long m = ((long)r * j) % ((long)NS * R);
+          const double ang = 2.0 * M_PI * (double)m / (double)(NS * R);
+          const size_t idx = (size_t)off + (size_t)(r - 1) * NS + j;
+          if (idx >= tab.size()) return fail(p, PWF_ERR_UNSUPPORTED, "twiddle table layout");
+          tab[idx] = make_float2((float)std::cos(ang), (float)(D * std::sin(ang)));
+        }
+    }
+  }
+  std::vector<float2> q1(n), q2(n);
+  std::vector<float> io(n), u2(n), st(n);
+  for (int k = 0; k < n; k++) {
+    const double f = fftfreq(k, n);  // cycles per pixel
+    const double u = f / pixel;      // cycles per metre
+    const double a1 = prop_phase(u * u, d.wavelength_m, d.L1_m);
+    const double a2 = prop_phase(u * u, d.wavelength_m, d.L2_m);
+    q1[k] = make_float2((float)std::cos(a1), (float)std::sin(a1));
+    q2[k] = make_float2((float)std::cos(a2), (float)std::sin(a2));
+    io[k] = (float)std::exp(-0.5 * M_PI * u * u * coh * coh);
+    u2[k] = (float)(f * f);
+    st[k] = (float)(M_PI * d.gamma * u * u * coh * coh);
+  }
+  pwf_status r;
+  if ((r = dalloc(p, &A.tw_fwd, tlf)) || (r = dalloc(p, &A.tw_inv, tli)) || (r = dalloc(p, &A.q1, n)) ||
+      (r = dalloc(p, &A.q2, n)) || (r = dalloc(p, &A.iotf, n)) || (r = dalloc(p, &A.u2, n)) ||
+      (r = dalloc(p, &A.stf, n)))
+    return r;
+  PWF_CUDA(p, cudaMemcpy(A.tw_fwd, twf.data(), tlf * sizeof(float2), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.tw_inv, twi.data(), tli * sizeof(float2), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.q1, q1.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.q2, q2.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.iotf, io.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.u2, u2.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  PWF_CUDA(p, cudaMemcpy(A.stf, st.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  return PWF_OK;
+}
+
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  return (int)(g > 152 * 16 ? 152 * 16 : (g == 0 ? 1 : g));
+}
+
+PassArgs base_args(pwf_plan* p) {
+  PassArgs a{};
+  a.B = p->d.batch;
+  a.ny = p->d.ny;
+  a.nx = p->d.nx;
+  a.maxt2 = p->maxt2;
+  a.acc = p->acc;
+  a.scale = (float)(1.0 / ((double)p->d.nx * p->d.ny));
+  a.eta = (float)p->d.eta;
+  const bool no_reg = (p->d.flags & PWF_FLAG_NO_REG) != 0;
+  a.alpha_re = no_reg ? 0.f : (float)p->d.alpha_re;
+  a.alpha_im = no_reg ? 0.f : (float)p->d.alpha_im;
+  a.no_precond = (p->d.flags & PWF_FLAG_NO_PRECOND) ? 1 : 0;
+  a.gscale = 1.0f;
+  return a;
+}
+
+// row pass on axis x, column pass on axis y
+cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
+  a.tw_fwd = p->ax.tw_fwd;
+  a.tw_inv = p->ax.tw_inv;
+  return p->krow->row[op](a, nproj, p->stream);
+}
+cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
+  a.tw_fwd = p->ay.tw_fwd;
+  a.tw_inv = p->ay.tw_inv;
+  a.qx = nullptr;
+  a.ix = p->ax.iotf;
+  a.iy = p->ay.iotf;
+  a.u2x = p->ax.u2;
+  a.u2y = p->ay.u2;
+  a.ex = p->ax.stf;
+  a.ey = p->ay.stf;
+  return p->kcol->col[op](a, nproj, p->stream);
+}
+cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
+  a.tw_fwd = p->ay.tw_fwd;
+  a.tw_inv = p->ay.tw_inv;
+  a.qx = which == 1 ? p->ax.q1 : p->ax.q2;
+  a.qy = which == 1 ? p->ay.q1 : p->ay.q2;
+  a.conj_q = conj;
+  return p->kcol->col[COL_Q](a, nproj, p->stream);
+}
+
+#define LAUNCH(p, expr)                                    \
+  do {                                                     \
+    cudaError_t e__ = (expr);                              \
+    if (e__ != cudaSuccess) return cuda_fail((p), e__, #expr); \
+  } while (0)
+
+pwf_status compute_maxt2(pwf_plan* p, const float2* t) {
+  const size_t n = (size_t)p->d.ny * p->d.nx;
+  PWF_CUDA(p, cudaMemsetAsync(p->maxt2, 0, sizeof(float), p->stream));
+  k_max_abs2<<<grid_for(n), 256, 0, p->stream>>>(t, n, p->maxt2);
+  PWF_CUDA(p, cudaGetLastError());
+  return PWF_OK;
+}
+
+// psi -> X = F_row{exp psi} -> ... -> X = F_row{ P2{t P1{x}} } (row spectrum of v)
+pwf_status fused_to_detector(pwf_plan* p, PassArgs a, const float2* psi, const float2* t, float2* u1,
+                             bool start_from_psi, int nproj) {
+  a.in = p->X;
+  a.out = p->X;
+  if (start_from_psi) {
+    a.psi = psi;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, nproj));
+  }
+  LAUNCH(p, col_q(p, a, 1, 0, nproj));          // P1: multiply by Q1
+  a.t = t;
+  a.conj_t = 0;
+  a.u1 = u1;
+  LAUNCH(p, row(p, ROW_MUL_T, a, nproj));       // t * P1{x}
+  a.u1 = nullptr;
+  LAUNCH(p, col_q(p, a, 2, 0, nproj));          // P2: multiply by Q2
+  return PWF_OK;
+}
+
+// X holds the row spectrum of w = v G; back-propagate: P2^H, conj(t), P1^H.
+pwf_status fused_backprop(pwf_plan* p, PassArgs a, const float2* t, bool gradt, int nproj) {
+  a.in = p->X;
+  a.out = p->X;
+  a.t = t;
+  LAUNCH(p, col_q(p, a, 2, 1, nproj));
+  if (gradt) {
+    a.u1 = p->S;
+    a.gt_scratch = p->YH;
+    LAUNCH(p, row(p, ROW_GRADT, a, nproj));
+    a.u1 = nullptr;
+  } else {
+    a.conj_t = 1;
+    LAUNCH(p, row(p, ROW_MUL_T, a, nproj));
+  }
+  LAUNCH(p, col_q(p, a, 1, 1, nproj));
+  return PWF_OK;
+}
+
+// one fused iteration (or the body of pwf_step): X must hold F_row{exp psi}
+pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
+                           bool next_fft, double corr_tol) {
+  PassArgs a = base_args(p);
+  a.active = st->active;
+  a.beta = &st->it->beta;
+  pwf_status r = fused_to_detector(p, a, psi, t, nullptr, false, a.B);
+  if (r) return r;
+  a.in = p->X;
+  a.out = p->X;
+  a.y = y;
+  if (p->coherent) {
+    LAUNCH(p, row(p, ROW_COH_RESID, a, a.B));   // e = y - |v|^2; loss; v (-e)
+  } else {
+    a.v = p->V;
+    LAUNCH(p, row(p, ROW_INTENSITY, a, a.B));   // v stored; F_row{|v|^2}
+    a.yhat = p->YH;
+    LAUNCH(p, col(p, COL_RESID_IOTF2, a, a.B)); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
+    LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v Filter(-e, IOTF)
+  }
+  if ((r = fused_backprop(p, a, t, false, a.B))) return r;
+  a.psi = psi;
+  a.reg = p->REG;
+  a.aux = p->S;
+  LAUNCH(p, row(p, ROW_GRAD_PACK, a, a.B));     // Re g; F_row{alpha o psi}; F_row{Im g}
+  a.aux_in = p->S;
+  LAUNCH(p, col(p, COL_PRECOND_REG, a, a.B));   // Gamma^2 H + i P^-1 S
+  a.psi_out = psi;
+  a.phi = st->phi;
+  LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, a.B));
+  k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
+  PWF_CUDA(p, cudaGetLastError());
+  return PWF_OK;
+}
+
+// F{y} for every projection (used by the Parseval form of the residual)
+pwf_status compute_yhat(pwf_plan* p, const float* y, const int* active) {
+  PassArgs a = base_args(p);
+  a.active = active;
+  a.y = y;
+  a.out = p->YH;
+  LAUNCH(p, row(p, ROW_REAL_FFT, a, a.B));
+  a.in = p->YH;
+  LAUNCH(p, col(p, COL_FFT, a, a.B));
+  return PWF_OK;
+}
+
+// ---- unfused baseline: Algorithm S2 one operation per launch, one projection at a time ----
+pwf_status plain_fft2(pwf_plan* p, float2* X, int proj, bool inverse) {
+  PassArgs a = base_args(p);
+  a.proj0 = proj;
+  a.in = X;
+  a.out = X;
+  if (!inverse) {
+    LAUNCH(p, row(p, ROW_FFT, a, 1));
+    LAUNCH(p, col(p, COL_FFT, a, 1));
+  } else {
+    LAUNCH(p, col(p, COL_IFFT, a, 1));
+    LAUNCH(p, row(p, ROW_IFFT, a, 1));
+  }
+  return PWF_OK;
+}
+
+pwf_status plain_filter(pwf_plan* p, float2* X, int proj, int which, int L, int conj) {
+  pwf_status r;
+  if ((r = plain_fft2(p, X, proj, false))) return r;
+  const size_t n = (size_t)p->d.ny * p->d.nx;
+  float2* Xp = X + (size_t)proj * n;
+  k_filter<<<grid_for(n), 256, 0, p->stream>>>(Xp, p->d.ny, p->d.nx, which, L == 1 ? p->ax.q1 : p->ax.q2,
+                                                L == 1 ? p->ay.q1 : p->ay.q2, conj, p->ax.iotf, p->ay.iotf,
+                                                p->ax.u2, p->ay.u2, p->ax.stf, p->ay.stf,
+                                                (p->d.flags & PWF_FLAG_NO_PRECOND) ? 1 : 0);
+  PWF_CUDA(p, cudaGetLastError());
+  return plain_fft2(p, X, proj, true);
+}
+
+pwf_status plain_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi, int proj) {
+  const size_t n = (size_t)p->d.ny * p->d.nx;
+  const size_t o = (size_t)proj * n;
+  const int G = grid_for(n);
+  cudaStream_t s = p->stream;
+  float2 *X = p->X, *V = p->V, *S = p->S, *H = p->YH;
+  pwf_status r;
+  // PhysicalModel
+  k_exp<<<G, 256, 0, s>>>(psi + o, X + o, n);
+  if ((r = plain_filter(p, X, proj, PF_Q, 1, 0))) return r;
+  k_mul_t<<<G, 256, 0, s>>>(X + o, t, n, 0);
+  if ((r = plain_filter(p, X, proj, PF_Q, 2, 0))) return r;
+  k_abs2_keep<<<G, 256, 0, s>>>(X + o, V + o, n);
+  if ((r = plain_filter(p, X, proj, PF_IOTF, 0, 0))) return r;
+  // e = y - f
+  k_resid<<<G, 256, 0, s>>>(X + o, y + o, n, p->acc + (size_t)proj * NACC + ACC_LOSS);
+  // WirtingerDerivative
+  if ((r = plain_filter(p, X, proj, PF_IOTF, 0, 0))) return r;
+  k_mul_v_real<<<G, 256, 0, s>>>(X + o, V + o, n);
+  if ((r = plain_filter(p, X, proj, PF_Q, 2, 1))) return r;
+  k_mul_t<<<G, 256, 0, s>>>(X + o, t, n, 1);
+  if ((r = plain_filter(p, X, proj, PF_Q, 1, 1))) return r;
+  k_grad<<<G, 256, 0, s>>>(X + o, psi + o, n, p->maxt2);
+  // Preconditioner
+  k_split<<<G, 256, 0, s>>>(X + o, p->REG + o, S + o, n);
+  if ((r = plain_filter(p, S, proj, PF_PINV, 0, 0))) return r;
+  // Regularizer
+  k_copy<<<G, 256, 0, s>>>(psi + o, H + o, n);
+  if ((r = plain_filter(p, H, proj, PF_GAMMA2, 0, 0))) return r;
+  // Nesterov
+  const bool no_reg = (p->d.flags & PWF_FLAG_NO_REG) != 0;
+  k_nesterov_plain<<<G, 256, 0, s>>>(p->REG + o, S + o, H + o, psi + o, st->phi + o, n, (float)p->d.eta,
+                                     no_reg ? 0.f : (float)p->d.alpha_re, no_reg ? 0.f : (float)p->d.alpha_im,
+                                     &st->it->beta, p->acc + (size_t)proj * NACC);
+  PWF_CUDA(p, cudaGetLastError());
+  return PWF_OK;
+}
+
+bool size_ok(int n) { return kernels_for_length(n) != nullptr; }
+
+pwf_status check_plan(pwf_plan* p) {
+  if (!p) return PWF_ERR_INVALID_ARG;
+  if (p->sticky != PWF_OK) return p->sticky;
+  return PWF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* pwf_status_string(pwf_status s) {
+  switch (s) {
+    case PWF_OK: return "PWF_OK";
+    case PWF_ERR_INVALID_ARG: return "PWF_ERR_INVALID_ARG";
+    case PWF_ERR_UNSUPPORTED: return "PWF_ERR_UNSUPPORTED";
+    case PWF_ERR_NOMEM: return "PWF_ERR_NOMEM";
+    case PWF_ERR_CUDA: return "PWF_ERR_CUDA";
+    case PWF_ERR_NONFINITE: return "PWF_ERR_NONFINITE";
+    case PWF_ERR_STATE: return "PWF_ERR_STATE";
+  }
+  return "PWF_ERR_UNKNOWN";
+}
+
+const char* pwf_plan_last_error(const pwf_plan* plan) { return plan ? plan->err : "null plan"; }
+
+pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
+  if (!desc || !out) return PWF_ERR_INVALID_ARG;
+  *out = nullptr;
+  const pwf_plan_desc& d = *desc;
+  if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
+      d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
+      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN)))
+    return PWF_ERR_INVALID_ARG;
+  if (!size_ok(d.ny) || !size_ok(d.nx)) return PWF_ERR_UNSUPPORTED;
+  // evanescent bins and the separable-propagator bound, in double precision
+  {
+    const double umax = 0.5 / d.pixel_m, il = 1.0 / d.wavelength_m;
+    if (2.0 * umax * umax >= il * il) return PWF_ERR_UNSUPPORTED;
+    for (double L : {d.L1_m, d.L2_m}) {
+      const double cross = prop_phase(2 * umax * umax, d.wavelength_m, L) - 2 * prop_phase(umax * umax, d.wavelength_m, L);
+      if (std::fabs(cross) > 1e-6) return PWF_ERR_UNSUPPORTED;
+    }
+  }
+  pwf_plan* p = new (std::nothrow) pwf_plan();
+  if (!p) return PWF_ERR_NOMEM;
+  p->d = d;
+  p->stream = static_cast<cudaStream_t>(d.stream);
+  p->krow = kernels_for_length(d.nx);
+  p->kcol = kernels_for_length(d.ny);
+  p->coherent = (d.xcoh_m == 0.0 && d.ycoh_m == 0.0);
+  const size_t n = (size_t)d.batch * d.ny * d.nx;
+  pwf_status r;
+  if ((r = build_axis(p, p->ax, d.nx, d.pixel_m, d.xcoh_m)) || (r = build_axis(p, p->ay, d.ny, d.pixel_m, d.ycoh_m)) ||
+      (r = dalloc(p, &p->X, n)) || (r = dalloc(p, &p->S, n)) || (r = dalloc(p, &p->REG, n)) ||
+      (r = dalloc(p, &p->V, n)) || (r = dalloc(p, &p->YH, n)) ||
+      (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1))) {
+    pwf_plan_destroy(p);
+    return r;
+  }
+  for (int op = 0; op < NUM_ROW_OPS; op++)
+    if (p->krow->row_prep[op]() != cudaSuccess) {
+      cudaGetLastError();
+      pwf_plan_destroy(p);
+      return PWF_ERR_CUDA;
+    }
+  for (int op = 0; op < NUM_COL_OPS; op++)
+    if (p->kcol->col_prep[op]() != cudaSuccess) {
+      cudaGetLastError();
+      pwf_plan_destroy(p);
+      return PWF_ERR_CUDA;
+    }
+  if (cudaMemset(p->acc, 0, (size_t)d.batch * NACC * sizeof(double)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    pwf_plan_destroy(p);
+    return PWF_ERR_CUDA;
+  }
+  *out = p;
+  return PWF_OK;
+}
+
+pwf_status pwf_plan_destroy(pwf_plan* p) {
+  if (!p) return PWF_ERR_INVALID_ARG;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->solve_state) pwf_state_destroy(p->solve_state);
+  for (void* q : p->allocs) cudaFree(q);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  delete p;
+  return PWF_OK;
+}
+
+pwf_status pwf_plan_set_stream(pwf_plan* p, void* stream) {
+  if (!p) return PWF_ERR_INVALID_ARG;
+  p->stream = static_cast<cudaStream_t>(stream);
+  return PWF_OK;
+}
+
+size_t pwf_plan_workspace_bytes(const pwf_plan* p) { return p ? p->ws_bytes : 0; }
+
+pwf_status pwf_forward(pwf_plan* p, const void* psi, const void* t, float* f) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!psi || !t || !f) return PWF_ERR_INVALID_ARG;
+  PassArgs a = base_args(p);
+  if ((r = fused_to_detector(p, a, (const float2*)psi, (const float2*)t, nullptr, true, a.B))) return r;
+  a.in = p->X;
+  a.out = p->X;
+  a.f_out = f;
+  if (p->coherent) {
+    LAUNCH(p, row(p, ROW_INTENSITY_OUT, a, a.B));
+  } else {
+    a.v = nullptr;
+    LAUNCH(p, row(p, ROW_INTENSITY, a, a.B));
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));
+    LAUNCH(p, row(p, ROW_REAL_OUT, a, a.B));
+  }
+  return PWF_OK;
+}
+
+pwf_status pwf_gradient(pwf_plan* p, const void* psi, const void* t, const float* y, void* g, double* loss) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!psi || !t || !y || !g) return PWF_ERR_INVALID_ARG;
+  const float2* P = (const float2*)psi;
+  if ((r = compute_maxt2(p, (const float2*)t))) return r;
+  PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
+  PassArgs a = base_args(p);
+  if ((r = fused_to_detector(p, a, P, (const float2*)t, nullptr, true, a.B))) return r;
+  a.in = p->X;
+  a.out = p->X;
+  a.y = y;
+  if (p->coherent) {
+    LAUNCH(p, row(p, ROW_COH_RESID, a, a.B));
+  } else {
+    a.v = p->V;
+    LAUNCH(p, row(p, ROW_INTENSITY, a, a.B));   // |v|^2, v kept
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // f = Filter(|v|^2, IOTF)
+    LAUNCH(p, row(p, ROW_RESID, a, a.B));       // e = y - f; loss; -e
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // Filter(-e, IOTF)
+    LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v g
+  }
+  if ((r = fused_backprop(p, a, (const float2*)t, false, a.B))) return r;
+  a.psi = P;
+  a.g_out = (float2*)g;
+  a.div_maxt2 = 1;
+  a.gscale = 1.0f;
+  LAUNCH(p, row(p, ROW_GRAD_OUT, a, a.B));
+  if (loss) {
+    k_gather_loss<<<(a.B + 255) / 256, 256, 0, p->stream>>>(p->acc, loss, a.B);
+    PWF_CUDA(p, cudaGetLastError());
+  }
+  return PWF_OK;
+}
+
+pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const float* grad_f, void* grad_psi,
+                           void* grad_t) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!psi || !t || !grad_f) return PWF_ERR_INVALID_ARG;
+  if (!grad_psi && !grad_t) return PWF_OK;
+  const float2* P = (const float2*)psi;
+  PassArgs a = base_args(p);
+  if ((r = fused_to_detector(p, a, P, (const float2*)t, grad_t ? p->S : nullptr, true, a.B))) return r;
+  a.in = p->X;
+  a.out = p->X;
+  if (p->coherent) {
+    a.y = grad_f;
+    LAUNCH(p, row(p, ROW_COH_VJP, a, a.B));     // v grad_f
+  } else {
+    a.out = p->V;
+    LAUNCH(p, row(p, ROW_IFFT, a, a.B));        // v
+    a.out = p->X;
+    a.y = grad_f;
+    LAUNCH(p, row(p, ROW_REAL_FFT, a, a.B));    // F_row{grad_f}
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // Filter(grad_f, IOTF)
+    a.v = p->V;
+    LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v G
+  }
+  if ((r = fused_backprop(p, a, (const float2*)t, grad_t != nullptr, a.B))) return r;
+  if (grad_t) {
+    const size_t n = (size_t)p->d.ny * p->d.nx;
+    k_batch_sum<<<grid_for(n), 256, 0, p->stream>>>(p->YH, (float2*)grad_t, a.B, n);
+    PWF_CUDA(p, cudaGetLastError());
+  }
+  if (grad_psi) {
+    a.psi = P;
+    a.g_out = (float2*)grad_psi;
+    a.div_maxt2 = 0;
+    a.gscale = 2.0f;
+    LAUNCH(p, row(p, ROW_GRAD_OUT, a, a.B));
+  }
+  return PWF_OK;
+}
+
+pwf_status pwf_state_create(pwf_plan* p, pwf_state** out) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!out) return PWF_ERR_INVALID_ARG;
+  pwf_state* s = new (std::nothrow) pwf_state();
+  if (!s) return PWF_ERR_NOMEM;
+  s->B = p->d.batch;
+  s->ny = p->d.ny;
+  s->nx = p->d.nx;
+  const size_t n = (size_t)s->B * s->ny * s->nx;
+  bool ok = cudaMalloc(&s->phi, n * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&s->active, s->B * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&s->iters, s->B * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&s->loss, s->B * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&s->corr, s->B * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&s->it, sizeof(DevIter)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pwf_state_destroy(s);
+    return PWF_ERR_NOMEM;
+  }
+  if ((r = pwf_state_reset(p, s))) {
+    pwf_state_destroy(s);
+    return r;
+  }
+  *out = s;
+  return PWF_OK;
+}
+
+pwf_status pwf_state_destroy(pwf_state* s) {
+  if (!s) return PWF_ERR_INVALID_ARG;
+  cudaFree(s->phi);
+  cudaFree(s->active);
+  cudaFree(s->iters);
+  cudaFree(s->loss);
+  cudaFree(s->corr);
+  cudaFree(s->it);
+  delete s;
+  return PWF_OK;
+}
+
+pwf_status pwf_state_reset(pwf_plan* p, pwf_state* s) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!s) return PWF_ERR_INVALID_ARG;
+  if (s->B != p->d.batch || s->ny != p->d.ny || s->nx != p->d.nx) return PWF_ERR_STATE;
+  PWF_CUDA(p, cudaMemsetAsync(s->phi, 0, (size_t)s->B * s->ny * s->nx * sizeof(float2), p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)s->B * NACC * sizeof(double), p->stream));
+  k_state_reset<<<1, 256, 0, p->stream>>>(s->it, s->active, s->iters, s->loss, s->corr, s->B);
+  PWF_CUDA(p, cudaGetLastError());
+  return PWF_OK;
+}
+
+pwf_status pwf_step(pwf_plan* p, pwf_state* st, const float* y, const void* t, void* psi, double corr_tol) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!st || !y || !t || !psi) return PWF_ERR_INVALID_ARG;
+  if (st->B != p->d.batch || st->ny != p->d.ny || st->nx != p->d.nx) return PWF_ERR_STATE;
+  float2* P = (float2*)psi;
+  if ((r = compute_maxt2(p, (const float2*)t))) return r;
+  PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
+  if (p->d.flags & PWF_FLAG_PLAIN) {
+    // host-driven: read the convergence flags, then one projection at a time
+    std::vector<int> act(p->d.batch);
+    PWF_CUDA(p, cudaMemcpyAsync(act.data(), st->active, p->d.batch * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+    for (int b = 0; b < p->d.batch; b++)
+      if (act[b] && (r = plain_iteration(p, st, y, (const float2*)t, P, b))) return r;
+    k_finalize<<<1, 256, 0, p->stream>>>(p->acc, p->d.batch, st->active, st->iters, st->loss, st->corr, st->it,
+                                         corr_tol);
+    PWF_CUDA(p, cudaGetLastError());
+    return PWF_OK;
+  }
+  if (!p->coherent && (r = compute_yhat(p, y, st->active))) return r;
+  PassArgs a = base_args(p);
+  a.active = st->active;
+  a.psi = P;
+  a.out = p->X;
+  LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+  return fused_iteration(p, st, y, (const float2*)t, P, false, corr_tol);
+}
+
+pwf_status pwf_state_read(pwf_plan* p, const pwf_state* s, double* loss_host, double* corr_host,
+                          int32_t* iters_host, int32_t* active_host) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!s) return PWF_ERR_INVALID_ARG;
+  if (loss_host) PWF_CUDA(p, cudaMemcpyAsync(loss_host, s->loss, s->B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  if (corr_host) PWF_CUDA(p, cudaMemcpyAsync(corr_host, s->corr, s->B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  if (iters_host) PWF_CUDA(p, cudaMemcpyAsync(iters_host, s->iters, s->B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  if (active_host) PWF_CUDA(p, cudaMemcpyAsync(active_host, s->active, s->B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  DevIter it;
+  PWF_CUDA(p, cudaMemcpy(&it, s->it, sizeof(DevIter), cudaMemcpyDeviceToHost));
+  if (it.nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss");
+  return PWF_OK;
+}
+
+pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int32_t max_iter, double corr_tol,
+                     int32_t* iters_host, double* loss_host) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
+  if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
+  pwf_state* st = p->solve_state;
+  if ((r = pwf_state_reset(p, st))) return r;
+  float2* P = (float2*)psi;
+  if (p->d.flags & PWF_FLAG_PLAIN) {
+    for (int k = 0; k < max_iter; k++)
+      if ((r = pwf_step(p, st, y, t, psi, corr_tol))) return r;
+  } else if (max_iter > 0) {
+    if ((r = compute_maxt2(p, (const float2*)t))) return r;
+    if (!p->coherent && (r = compute_yhat(p, y, st->active))) return r;
+    PassArgs a = base_args(p);
+    a.active = st->active;
+    a.psi = P;
+    a.out = p->X;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    // capture one fused iteration into a graph (re-captured when the operands change)
+    const void* key[4] = {y, t, psi, p->stream};
+    if (!p->graph || std::memcmp(key, p->graph_key, sizeof(key)) != 0 || p->graph_tol != corr_tol) {
+      if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+      }
+      cudaStream_t user = p->stream;
+      p->stream = p->capture_stream;
+      cudaGraph_t g = nullptr;
+      PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+      r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
+      cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
+      p->stream = user;
+      if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&p->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaGraphInstantiate");
+      std::memcpy(p->graph_key, key, sizeof(key));
+      p->graph_tol = corr_tol;
+    }
+    const int check_every = 16;
+    for (int k = 0; k < max_iter; k++) {
+      PWF_CUDA(p, cudaGraphLaunch(p->graph, p->stream));
+      if (corr_tol > 0.0 && (k + 1) % check_every == 0 && k + 1 < max_iter) {
+        DevIter it;
+        PWF_CUDA(p, cudaMemcpyAsync(&it, st->it, sizeof(DevIter), cudaMemcpyDeviceToHost, p->stream));
+        PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+        if (it.n_active == 0) break;
+      }
+    }
+  }
+  if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
+  return PWF_OK;
+}
+
+size_t pwf_state_bytes(const pwf_state* s) {
+  if (!s) return 0;
+  return 64 + (size_t)s->B * s->ny * s->nx * sizeof(float2) + s->B * (2 * sizeof(int) + 2 * sizeof(double)) +
+         sizeof(DevIter);
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t B, ny, nx, version;
+  char pad[40];
+};
+}  // namespace
+
+pwf_status pwf_state_save(pwf_plan* p, const pwf_state* s, void* host_buf, size_t bytes) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!s || !host_buf) return PWF_ERR_INVALID_ARG;
+  if (bytes < pwf_state_bytes(s)) return PWF_ERR_STATE;
+  char* b = static_cast<char*>(host_buf);
+  CkptHeader h{};
+  std::memcpy(h.magic, "PWFSTAT1", 8);
+  h.B = s->B;
+  h.ny = s->ny;
+  h.nx = s->nx;
+  h.version = 1;
+  std::memcpy(b, &h, sizeof(h));
+  b += 64;
+  const size_t nf = (size_t)s->B * s->ny * s->nx * sizeof(float2);
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->phi, nf, cudaMemcpyDeviceToHost, p->stream));
+  b += nf;
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->active, s->B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  b += s->B * sizeof(int);
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->iters, s->B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  b += s->B * sizeof(int);
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->loss, s->B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  b += s->B * sizeof(double);
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->corr, s->B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  b += s->B * sizeof(double);
+  PWF_CUDA(p, cudaMemcpyAsync(b, s->it, sizeof(DevIter), cudaMemcpyDeviceToHost, p->stream));
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PWF_OK;
+}
+
+pwf_status pwf_state_load(pwf_plan* p, pwf_state* s, const void* host_buf, size_t bytes) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!s || !host_buf) return PWF_ERR_INVALID_ARG;
+  if (bytes < pwf_state_bytes(s)) return PWF_ERR_STATE;
+  const char* b = static_cast<const char*>(host_buf);
+  CkptHeader h;
+  std::memcpy(&h, b, sizeof(h));
+  if (std::memcmp(h.magic, "PWFSTAT1", 8) != 0 || h.version != 1 || h.B != s->B || h.ny != s->ny || h.nx != s->nx)
+    return PWF_ERR_STATE;
+  b += 64;
+  const size_t nf = (size_t)s->B * s->ny * s->nx * sizeof(float2);
+  PWF_CUDA(p, cudaMemcpyAsync(s->phi, b, nf, cudaMemcpyHostToDevice, p->stream));
+  b += nf;
+  PWF_CUDA(p, cudaMemcpyAsync(s->active, b, s->B * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  b += s->B * sizeof(int);
+  PWF_CUDA(p, cudaMemcpyAsync(s->iters, b, s->B * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  b += s->B * sizeof(int);
+  PWF_CUDA(p, cudaMemcpyAsync(s->loss, b, s->B * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  b += s->B * sizeof(double);
+  PWF_CUDA(p, cudaMemcpyAsync(s->corr, b, s->B * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  b += s->B * sizeof(double);
+  PWF_CUDA(p, cudaMemcpyAsync(s->it, b, sizeof(DevIter), cudaMemcpyHostToDevice, p->stream));
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  return PWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+// Register/shared-memory Stockham FFT building blocks for the PWF passes.
+//
+// Every Filter of Algorithm S2 (F^-1{F{x} W}) is evaluated as a row transform
+// and a column transform of a complex64 field. This header holds the pieces
+// shared by the row and column kernels:
+//   * complex helpers and radix-2/3/4/8/16 DFT butterflies (written from the
+//     DFT definition X_k = sum_j x_j exp(s 2 pi i j k / R), s = -1 forward);
+//   * a compile-time radix schedule per transform length N (N = 2^a 3^b);
+//   * a self-sorting (Stockham) stage runner: stage 0 takes its inputs from
+//     registers, middle stages exchange through shared memory, and the last
+//     stage leaves its outputs in registers. The inverse transform uses the
+//     reversed radix order, so the slot layout at the end of a forward
+//     transform equals the one at the start of an inverse transform and vice
+//     versa; that is what lets point-wise work run in registers between two
+//     transforms of the same pass.
+//
+// Slot convention: with R the radix of the first (or last) stage, EPT values
+// per thread and TPF threads per transform, slot (i, r) of thread t holds
+// element  t + i*TPF + r*(N/R),  stored at v[i*R + r].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pwf {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+constexpr int FWD = -1;  // exponent sign of the forward DFT
+constexpr int INV = +1;
+
+// (s i) * a, s = DIR
+template <int DIR>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  if constexpr (DIR == FWD) return make_float2(a.y, -a.x);   // -i a
+  else return make_float2(-a.y, a.x);                        // +i a
+}
+
+// exp(s 2 pi i m / 16) for the compile-time exponent m
+template <int DIR, int M>
+__device__ __forceinline__ float2 w16() {
+  constexpr int m = M & 15;
+  // cos and sin of m*pi/8 for m = 0..15
+  constexpr float C[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                           0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                           -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                           0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  constexpr float S[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                           1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                           0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                           -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+  return make_float2(C[m], DIR == FWD ? -S[m] : S[m]);
+}
+
+template <int DIR, int M>
+__device__ __forceinline__ float2 twm16(float2 a) {
+  constexpr int m = M & 15;
+  if constexpr (m == 0) return a;
+  else if constexpr (m == 4) return mul_si<DIR>(a);
+  else if constexpr (m == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (m == 12) return mul_si<-DIR>(a);
+  else return cmul(a, w16<DIR, m>());
+}
+
+// ---------------------------------------------------------------------------
+// radix butterflies (in place on x[0..R))
+// ---------------------------------------------------------------------------
+template <int DIR>
+__device__ __forceinline__ void dft2(float2* x) {
+  float2 a = x[0], b = x[1];
+  x[0] = cadd(a, b);
+  x[1] = csub(a, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft3(float2* x) {
+  constexpr float H = 0.86602540378443865f;  // sqrt(3)/2
+  float2 s = cadd(x[1], x[2]);
+  float2 d = csub(x[1], x[2]);
+  float2 m = make_float2(fmaf(-0.5f, s.x, x[0].x), fmaf(-0.5f, s.y, x[0].y));
+  float2 r = mul_si<DIR>(cscale(d, H));
+  x[0] = cadd(x[0], s);
+  x[1] = cadd(m, r);
+  x[2] = csub(m, r);
+}
+
+// 4-point DFT on elements x[0], x[S], x[2S], x[3S]
+template <int DIR, int S = 1>
+__device__ __forceinline__ void dft4s(float2* x) {
+  float2 t0 = cadd(x[0], x[2 * S]);
+  float2 t1 = csub(x[0], x[2 * S]);
+  float2 t2 = cadd(x[S], x[3 * S]);
+  float2 t3 = mul_si<DIR>(csub(x[S], x[3 * S]));
+  x[0] = cadd(t0, t2);
+  x[2 * S] = csub(t0, t2);
+  x[S] = cadd(t1, t3);
+  x[3 * S] = csub(t1, t3);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2* x) { dft4s<DIR, 1>(x); }
+
+// 8-point: radix-2 split into even/odd 4-point DFTs.
+template <int DIR>
+__device__ __forceinline__ void dft8(float2* x) {
+  float2 e[4] = {x[0], x[2], x[4], x[6]};
+  float2 o[4] = {x[1], x[3], x[5], x[7]};
+  dft4<DIR>(e);
+  dft4<DIR>(o);
+  o[1] = twm16<DIR, 2>(o[1]);
+  o[2] = twm16<DIR, 4>(o[2]);
+  o[3] = twm16<DIR, 6>(o[3]);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    x[k] = cadd(e[k], o[k]);
+    x[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+// 16-point: 4 x 4. Inner 4-point DFTs over j = q + 4m (stride 4), twiddle
+// W16^(q k1), outer 4-point DFTs over q; output index k1 + 4 k2.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* x) {
+  float2 y[16];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float2 a[4] = {x[q], x[q + 4], x[q + 8], x[q + 12]};
+    dft4<DIR>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) y[q * 4 + k1] = a[k1];
+  }
+  // y[q*4 + k1] *= W16^(q k1)
+  y[1 * 4 + 1] = twm16<DIR, 1>(y[5]);
+  y[1 * 4 + 2] = twm16<DIR, 2>(y[6]);
+  y[1 * 4 + 3] = twm16<DIR, 3>(y[7]);
+  y[2 * 4 + 1] = twm16<DIR, 2>(y[9]);
+  y[2 * 4 + 2] = twm16<DIR, 4>(y[10]);
+  y[2 * 4 + 3] = twm16<DIR, 6>(y[11]);
+  y[3 * 4 + 1] = twm16<DIR, 3>(y[13]);
+  y[3 * 4 + 2] = twm16<DIR, 6>(y[14]);
+  y[3 * 4 + 3] = twm16<DIR, 9>(y[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++) {
+    float2 a[4] = {y[k1], y[4 + k1], y[8 + k1], y[12 + k1]};
+    dft4<DIR>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; k2++) x[k1 + 4 * k2] = a[k2];
+  }
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2* x) {
+  if constexpr (R == 2) dft2<DIR>(x);
+  else if constexpr (R == 3) dft3<DIR>(x);
+  else if constexpr (R == 4) dft4<DIR>(x);
+  else if constexpr (R == 8) dft8<DIR>(x);
+  else if constexpr (R == 16) dft16<DIR>(x);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ---------------------------------------------------------------------------
+// compile-time radix schedules (forward order; the inverse runs them reversed)
+// ---------------------------------------------------------------------------
+struct Sched {
+  int n, s, r0, r1, r2, r3;
+  __host__ __device__ constexpr int r(int i) const { return i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : r3; }
+};
+
+__host__ __device__ constexpr Sched sched_for(int n) {
+  switch (n) {
+    case 16: return {16, 1, 16, 1, 1, 1};
+    case 32: return {32, 2, 8, 4, 1, 1};
+    case 64: return {64, 2, 8, 8, 1, 1};
+    case 96: return {96, 3, 8, 4, 3, 1};
+    case 128: return {128, 2, 16, 8, 1, 1};
+    case 192: return {192, 3, 8, 8, 3, 1};
+    case 256: return {256, 2, 16, 16, 1, 1};
+    case 384: return {384, 4, 8, 8, 2, 3};
+    case 512: return {512, 3, 16, 8, 4, 1};
+    case 768: return {768, 4, 8, 8, 4, 3};
+    case 1024: return {1024, 3, 16, 8, 8, 1};
+    case 1536: return {1536, 4, 8, 8, 8, 3};
+    case 2048: return {2048, 3, 16, 16, 8, 1};
+    default: return {0, 0, 1, 1, 1, 1};
+  }
+}
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
+
+// elements per thread: lcm of the radices
+__host__ __device__ constexpr int ept_for(int n) {
+  Sched s = sched_for(n);
+  int e = 1;
+  for (int i = 0; i < s.s; i++) e = lcm_c(e, s.r(i));
+  return e;
+}
+__host__ __device__ constexpr int tpf_for(int n) { return n / ept_for(n); }
+
+// radix of stage k of the transform with direction DIR
+__host__ __device__ constexpr int stage_radix(int n, int dir, int k) {
+  Sched s = sched_for(n);
+  return dir == FWD ? s.r(k) : s.r(s.s - 1 - k);
+}
+// product of the radices before stage k
+__host__ __device__ constexpr int stage_ns(int n, int dir, int k) {
+  int p = 1;
+  for (int i = 0; i < k; i++) p *= stage_radix(n, dir, i);
+  return p;
+}
+// twiddle-table offset of stage k (stage 0 needs none)
+__host__ __device__ constexpr int stage_twoff(int n, int dir, int k) {
+  int off = 0;
+  for (int i = 1; i < k; i++) off += (stage_radix(n, dir, i) - 1) * stage_ns(n, dir, i);
+  return off;
+}
+__host__ __device__ constexpr int twiddle_len(int n, int dir) { return stage_twoff(n, dir, sched_for(n).s); }
+
+// ---------------------------------------------------------------------------
+// shared-memory layouts
+// ---------------------------------------------------------------------------
+// one transform per row; one padding slot per 16 (breaks the stride-R
+// bank pattern of the first stage's writes)
+struct RowLayout {
+  float2* base;
+  __device__ __forceinline__ float2& operator[](int p) const { return base[p + (p >> 4)]; }
+};
+__host__ __device__ constexpr int row_smem_len(int n) { return n + n / 16; }
+
+// C transforms interleaved: element p of column c at p*C + c
+template <int C>
+struct ColLayout {
+  float2* base;  // already offset by c
+  __device__ __forceinline__ float2& operator[](int p) const { return base[p * C]; }
+};
+
+// ---------------------------------------------------------------------------
+// Stockham stages
+// ---------------------------------------------------------------------------
+// Runs stages [K, S) of the length-N transform with direction DIR on the slot
+// registers v. Before the call, v holds the inputs of stage K in slot order of
+// its radix (for K = 0, the transform's input). After it, v holds the outputs
+// of the last stage in slot order of the last radix. A __syncthreads() is
+// issued before the first shared-memory write and after every write phase, so
+// the caller needs no barrier around it.
+template <int N, int DIR, int K, class L>
+__device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm, int t,
+                                           const float2* __restrict__ tw) {
+  constexpr Sched S = sched_for(N);
+  constexpr int EPT = ept_for(N);
+  constexpr int TPF = tpf_for(N);
+  constexpr int R = stage_radix(N, DIR, K);
+  constexpr int NS = stage_ns(N, DIR, K);
+  constexpr int NB = EPT / R;
+  constexpr bool LAST = (K + 1 == S.s);
+  static_assert(EPT % R == 0, "radix must divide the per-thread count");
+
+  if constexpr (K > 0) {
+    constexpr int OFF = stage_twoff(N, DIR, K);
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+#pragma unroll
+      for (int r = 0; r < R; r++) v[i * R + r] = sm[b + r * (N / R)];
+    }
+    if constexpr (!LAST) __syncthreads();  // reads of this stage precede its writes
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+      const int k = b % NS;
+#pragma unroll
+      for (int r = 1; r < R; r++) v[i * R + r] = cmul(v[i * R + r], __ldg(&tw[OFF + (r - 1) * NS + k]));
+      dft<R, DIR>(&v[i * R]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; i++) dft<R, DIR>(&v[i * R]);
+  }
+
+  if constexpr (!LAST) {
+    if constexpr (K == 0) __syncthreads();  // earlier readers of the buffer are done
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+      const int k = b % NS;
+      const int base = (b / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; r++) sm[base + r * NS] = v[i * R + r];
+    }
+    __syncthreads();
+    fft_stages<N, DIR, K + 1, L>(v, sm, t, tw);
+  }
+}
+
+template <int N, int DIR, class L>
+__device__ __forceinline__ void fft_run(float2 (&v)[ept_for(N)], const L& sm, int t,
+                                        const float2* __restrict__ tw) {
+  fft_stages<N, DIR, 0, L>(v, sm, t, tw);
+}
+
+// radix of the slot layout at the start / end of a transform
+template <int N, int DIR>
+__host__ __device__ constexpr int first_radix() { return stage_radix(N, DIR, 0); }
+template <int N, int DIR>
+__host__ __device__ constexpr int last_radix() { return stage_radix(N, DIR, sched_for(N).s - 1); }
+
+// element index of slot j (= i*R + r) for radix R
+template <int N, int R>
+__device__ __forceinline__ int slot_index(int t, int j) {
+  constexpr int TPF = tpf_for(N);
+  return t + (j / R) * TPF + (j % R) * (N / R);
+}
+
+}  // namespace pwf

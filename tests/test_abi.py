@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every entry point include/pwf.h declares.
+
+Runs on CPU: no compute call is made. Only argument validation that returns
+before any CUDA call is exercised (null descriptors, unsupported sizes).
+"""
+import ctypes
+
+import pytest
+
+from paper_2503_20146_gb300 import _build, pwf
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return pwf.load()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = pwf.header_functions()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for code, name in pwf.STATUS.items():
+        assert pwf.pwf_status_string(code) == name
+
+
+def _desc(**kw):
+    base = dict(batch=1, ny=128, nx=128, pixel_m=1e-6, wavelength_m=6.2e-11, L1_m=0.1, L2_m=0.4,
+                xcoh_m=0.0, ycoh_m=0.0, gamma=1.0, alpha_re=0.1, alpha_im=0.01, eta=1e-3, flags=0,
+                stream=None)
+    base.update(kw)
+    return pwf.pwf_plan_desc(**base)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(ny=100), 2),            # not a built transform length
+    (dict(nx=4096), 2),
+    (dict(batch=0), 1),
+    (dict(eta=0.0), 1),
+    (dict(pixel_m=-1.0), 1),
+    (dict(flags=0x80), 1),
+    (dict(wavelength_m=2e-6), 2),  # evanescent bins at this pixel pitch
+    (dict(L2_m=5e3), 2),           # separable-propagator bound exceeded
+])
+def test_plan_validation_before_any_cuda_call(lib, kw, status):
+    plan = ctypes.c_void_p()
+    d = _desc(**kw)
+    assert lib.pwf_plan_create(ctypes.byref(d), ctypes.byref(plan)) == status
+    assert not plan.value
+
+
+def test_null_arguments(lib):
+    plan = ctypes.c_void_p()
+    assert lib.pwf_plan_create(None, ctypes.byref(plan)) == 1
+    assert lib.pwf_forward(None, None, None, None) == 1
+    assert lib.pwf_plan_destroy(None) == 1
+    assert lib.pwf_state_bytes(None) == 0
