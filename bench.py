@@ -1,0 +1,430 @@
+"""Throughput benchmark of the fused, batched PWF iteration on GB300.
+
+Workload (default): a tomographic series of 180 projections of 1024 x 1024
+pixels (angles 0..179 degrees of a seeded 40-ellipsoid phantom, 20 keV, 1 um
+pixels, L1 = 0.1 m, L2 = 0.4 m), shared diffuser, partial coherence in the
+paper's IOTF form (Gaussian blur of sigma = 2 px), gamma = 1, alpha = 0.1 +
+0.01i. One step = one PWF iteration (Algorithm S1 body: forward model,
+residual, Wirtinger derivative, preconditioner + regularizer, Nesterov) over
+all 180 projections. Metric: megapixel-projection iterations per second.
+
+Arms:
+  default            fused batched CUDA path (libpwf, pwf_solve), plus the
+                     unfused per-projection baseline (PWF_FLAG_PLAIN) on a
+                     sample, the roofline of the dominant kernel, the FP64
+                     oracle on the host cores (cpu_baseline) and an
+                     end-to-end number through host buffers.
+  --impl reference   the FP64 oracle on the host cores, timed per step on a
+                     bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs its own 180-projection series (weak
+scaling, no collective on the data path); the timed region is bracketed by a
+barrier and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "megapixel-projection PWF iterations/s at 1 GB300 (fused batched vs plain); % HBM roofline"
+UNIT = "Mpx*it/s"
+
+# Algorithmic DRAM bytes per pixel of each pass of the fused iteration (reads +
+# writes of the fields the pass must touch; complex64 = 8 B, float32 = 4 B).
+PASS_BYTES_PER_PX = {
+    "col_q": 16,            # field in, field out
+    "row_mul_t": 24,        # field in, t in, field out
+    "row_intensity": 24,    # field in, v out, F_row{|v|^2} out
+    "col_resid_iotf2": 24,  # field in, F{y} in, field out
+    "row_mul_v": 24,        # field in, v in, field out
+    "row_grad_pack": 36,    # field in, psi in, Re g out, two fields out
+    "col_precond_reg": 24,  # two fields in, one out
+    "row_nesterov_fft": 52, # field, psi, phi, Re g in; phi, psi, field out
+    "row_coh_resid": 20,    # field in, y in, field out
+    "finalize": 0,
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tomo180x1024_iotf")
+    ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing
+# ----------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# workload synthesis (seeded; on the GPU for speed)
+# ----------------------------------------------------------------------------
+def make_workload(P, S, w, batch, device):
+    import numpy as np
+    import torch
+    n = w.ny
+    if w.name.startswith("tomo"):
+        ph = S.ellipsoid_phantom(S.rng_for(w.config, 0), size=n)
+        xd, yd = S.detector_grid(n, n, xp=torch)
+        xd, yd = xd.to(device), yd.to(device)
+        psi_true = torch.empty((batch, n, n), dtype=torch.complex64, device=device)
+        for i, ang in enumerate(S.tomo_angles(batch)):
+            re, im = S.ellipsoid_projection(ph, float(ang), xd, yd, w.wavelength_m)
+            psi_true[i] = torch.complex(re, im).to(torch.complex64)
+    else:
+        psi_true = torch.stack([torch.from_numpy(S.complex_phase_from(
+            S.blob_phase(w.ny, w.nx, S.rng_for(w.config, b))).astype(np.complex64)) for b in range(batch)]).to(device)
+    t = torch.from_numpy(S.diffuser(w.ny, w.nx, S.rng_for(w.config, 99)).astype(np.complex64)).to(device)
+    return psi_true, t
+
+
+def plan_desc(P, w, batch, flags=0):
+    return P.PlanDesc(batch, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
+                      w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2503_20146_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the summary was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_full")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# oracle timing on the host (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(w, n_proj, seed_iters):
+    """Times the FP64 oracle on n_proj projections of the workload's size
+    (blob objects stand in for the phantom: the oracle's cost does not depend
+    on the values) for `seed_iters` iterations; returns (seconds, Mpx*it)."""
+    import numpy as np
+    from oracle import pwf_oracle as O
+    from paper_2503_20146_gb300 import synth as S
+    geom = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m, w.gamma,
+                      w.alpha, w.eta)
+    t = S.diffuser(w.ny, w.nx, S.rng_for(w.config, 99))
+    ys = [np.clip(1.0 + 0.1 * S.rng_for(w.config, 200 + b).standard_normal((w.ny, w.nx)), 0, None)
+          for b in range(n_proj)]
+    t0 = time.perf_counter()
+    for y in ys:
+        O.pwf(y, t, geom, seed_iters)
+    dt = time.perf_counter() - t0
+    return dt, n_proj * w.ny * w.nx * seed_iters / 1e6
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    # one step = one oracle iteration over one projection of the workload
+    for _ in range(args.warmup):
+        oracle_sample(w, 1, 1)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = oracle_sample(w, 1, 1)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * w.ny * w.nx / 1e6 / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: oracle on 1 of {w.batch} projections per step",
+                   "ny": w.ny, "nx": w.nx, "batch": w.batch},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"1 projection of {w.ny}x{w.nx}, 1 iteration per step, numpy FP64 (single thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------
+# main arm
+# ----------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    from paper_2503_20146_gb300 import synth as S
+    w = S.WORKLOADS[args.workload]
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import numpy as np
+    import torch
+
+    from paper_2503_20146_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    from paper_2503_20146_gb300 import pwf as P
+    P.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    batch = args.batch or w.batch
+    mpx_iter = batch * w.ny * w.nx / 1e6
+
+    psi_true, t = make_workload(P, S, w, batch, dev)
+    plan = P.Plan(plan_desc(P, w, batch))
+    f = plan.forward(psi_true, t)
+    gen = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config + rank)
+    y = (torch.poisson(f.clamp_min(0) * w.photons, generator=gen) / w.photons).contiguous()
+    del f, psi_true
+    psi = torch.zeros((batch, w.ny, w.nx), dtype=torch.complex64, device=dev)
+
+    # warm-up (captures the iteration graph)
+    plan.solve(y, t, psi, args.warmup, read_back=False)
+    torch.cuda.synchronize()
+
+    # timed region: K iterations of Algorithm S1 (one pwf_solve call)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = P.pwf_plan_launch_count(plan.handle)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        psi.zero_()
+        plan.solve(y, t, psi, args.steps, read_back=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = P.pwf_plan_launch_count(plan.handle) - launches0
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    value = world * mpx_iter * args.steps / (ms / 1e3)
+
+    # per-pass timing (eager, CUDA events around each kernel) -> roofline
+    psi.zero_()
+    passes = P.pwf_profile_iteration(plan.handle, y, t, psi, 3)
+    hbm, peak_kind = peaks()
+    tot = {}
+    for name, pms in passes:
+        tot[name] = tot.get(name, 0.0) + pms
+    dom = max(tot, key=tot.get)
+    dom_ms = [pms for name, pms in passes if name == dom]
+    dom_avg = sum(dom_ms) / len(dom_ms)
+    dom_bytes = PASS_BYTES_PER_PX.get(dom, 0) * batch * w.ny * w.nx
+    achieved = dom_bytes / (dom_avg / 1e3) / 1e9
+    iter_ms = sum(p for _, p in passes)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": measured_traffic(dom), "peak_kind": peak_kind,
+                "bytes_per_px": PASS_BYTES_PER_PX.get(dom, 0), "launch_ms": dom_avg,
+                "share_of_iteration": sum(dom_ms) / iter_ms}
+    model_bytes = sum(PASS_BYTES_PER_PX.get(n, 0) for n, _ in passes) * batch * w.ny * w.nx
+    iteration = {"passes": [[n, round(p, 4)] for n, p in passes],
+                 "eager_iteration_ms": iter_ms,
+                 "model_bytes_per_px": sum(PASS_BYTES_PER_PX.get(n, 0) for n, _ in passes),
+                 "model_gbs_timed": model_bytes / (ms / args.steps / 1e3) / 1e9,
+                 "model_frac_timed": model_bytes / (ms / args.steps / 1e3) / 1e9 / hbm}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # plain per-projection baseline (unfused, Algorithm S2 step by step) on a sample
+        nplain, iplain = 4, 2
+        plain = P.Plan(plan_desc(P, w, nplain, P.FLAG_PLAIN))
+        yp = y[:nplain].contiguous()
+        pp = torch.zeros((nplain, w.ny, w.nx), dtype=torch.complex64, device=dev)
+        plain.solve(yp, t, pp, 1, read_back=False)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        pp.zero_()
+        plain.solve(yp, t, pp, iplain, read_back=False)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pv = nplain * w.ny * w.nx * iplain / 1e6 / (a0.elapsed_time(a1) / 1e3)
+        extras["plain_gpu"] = {"value": pv, "unit": UNIT, "sample": f"{nplain} projections x {iplain} iterations",
+                               "fused_over_plain": value / world / pv}
+        plain.close()
+        del yp, pp
+
+        # end to end through host buffers: H2D (y, t) + solve + D2H psi per call
+        e2e_iters = 10
+        y_h = y.cpu().pin_memory()
+        t_h = t.cpu().pin_memory()
+        psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
+        y_d = torch.empty_like(y)
+        t_d = torch.empty_like(t)
+        times = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            y_d.copy_(y_h, non_blocking=True)
+            t_d.copy_(t_h, non_blocking=True)
+            psi.zero_()
+            plan.solve(y_d, t_d, psi, e2e_iters, read_back=False)
+            psi_h.copy_(psi, non_blocking=True)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(b0.elapsed_time(b1))
+        ems = sum(times) / len(times)
+        extras["e2e"] = {"value": mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(y.numel() * 4 + t.numel() * 8),
+                         "d2h_bytes_per_step": int(psi.numel() * 8),
+                         "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers"}
+        del y_h, psi_h
+
+        # FP64 oracle on the host cores, bounded sample
+        dt, work = oracle_sample(w, 1, 3)
+        extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"1 projection of {w.ny}x{w.nx}, 3 iterations, numpy FP64 (single thread)",
+                                  "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "projections_per_gpu": batch, "ny": w.ny, "nx": w.nx,
+                       "coherence": "IOTF, Gaussian sigma = 2 px" if w.xcoh_m > 0 else "coherent",
+                       "eta": w.eta, "l2_flush": "inputs larger than L2 (state ~1.5 GB per field)",
+                       "step": "one PWF iteration over all projections"},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "iteration": iteration,
+            "clocks": clk.summary(),
+        }
+        line.update(extras)
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,21 @@ size_t pwf_state_bytes(const pwf_state* state);
 pwf_status pwf_state_save(pwf_plan* plan, const pwf_state* state, void* host_buf, size_t bytes);
 pwf_status pwf_state_load(pwf_plan* plan, pwf_state* state, const void* host_buf, size_t bytes);
 
+/* Instrumentation.
+ * pwf_plan_launch_count: number of kernels this plan has enqueued so far
+ * (kernels replayed from the solver's CUDA graph included); -1 for NULL.
+ * pwf_profile_iteration: runs Algorithm S1 from the caller's psi for `iters`
+ * fused iterations WITHOUT the graph, with a CUDA event pair recorded on the
+ * plan's stream around every kernel, and returns for each kernel position of
+ * one iteration its mean duration in milliseconds (pass_ms, HOST float array
+ * of PWF_MAX_PASSES) and its static name (pass_names, HOST array of
+ * PWF_MAX_PASSES pointers); *n_passes receives the count. psi is updated as by
+ * pwf_solve. Synchronises. PWF_ERR_UNSUPPORTED for PWF_FLAG_PLAIN plans. */
+#define PWF_MAX_PASSES 32
+long long pwf_plan_launch_count(const pwf_plan* plan);
+pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t iters,
+                                 float* pass_ms, const char** pass_names, int32_t* n_passes);
+
 /* Human-readable name of a status code (static storage). */
 const char* pwf_status_string(pwf_status s);
 /* Last error message recorded on the plan (static per plan; never NULL). */

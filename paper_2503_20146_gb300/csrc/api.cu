@@ -286,6 +286,13 @@ struct pwf_plan {
   double graph_tol = 0.0;
   pwf_status sticky = PWF_OK;
   char err[256] = "";
+  // instrumentation: kernels enqueued, and per-pass event timing
+  long long launches = 0;
+  long long graph_kernels = 0;  // kernels in the captured iteration graph
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<const char*> prof_names;
+  size_t prof_n = 0;
 };
 
 namespace {
@@ -409,11 +416,44 @@ PassArgs base_args(pwf_plan* p) {
   return a;
 }
 
+const char* const kRowNames[NUM_ROW_OPS] = {
+    "row_exp_fft", "row_real_fft", "row_fft", "row_ifft", "row_mul_t", "row_intensity", "row_intensity_out",
+    "row_real_out", "row_resid", "row_coh_resid", "row_coh_vjp", "row_mul_v", "row_grad_out", "row_grad_pack",
+    "row_nesterov_fft", "row_nesterov", "row_gradt"};
+const char* const kColNames[NUM_COL_OPS] = {"col_q", "col_iotf", "col_resid_iotf2", "col_precond_reg", "col_fft",
+                                            "col_ifft"};
+
+// Enqueues one kernel; under pwf_profile_iteration it is bracketed by events.
+template <class F>
+cudaError_t enqueue(pwf_plan* p, const char* name, F&& launch) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p->prof) {
+    if (p->prof_n + 2 > p->ev_pool.size()) {
+      for (int k = 0; k < 64; k++) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return cudaErrorMemoryAllocation;
+        p->ev_pool.push_back(e);
+      }
+    }
+    e0 = p->ev_pool[p->prof_n];
+    e1 = p->ev_pool[p->prof_n + 1];
+    cudaEventRecord(e0, p->stream);
+  }
+  cudaError_t e = launch();
+  p->launches++;
+  if (p->prof) {
+    cudaEventRecord(e1, p->stream);
+    p->prof_names.push_back(name);
+    p->prof_n += 2;
+  }
+  return e;
+}
+
 // row pass on axis x, column pass on axis y
 cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
   a.tw_fwd = p->ax.tw_fwd;
   a.tw_inv = p->ax.tw_inv;
-  return p->krow->row[op](a, nproj, p->stream);
+  return enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
 }
 cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a.tw_fwd = p->ay.tw_fwd;
@@ -425,7 +465,7 @@ cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a.u2y = p->ay.u2;
   a.ex = p->ax.stf;
   a.ey = p->ay.stf;
-  return p->kcol->col[op](a, nproj, p->stream);
+  return enqueue(p, kColNames[op], [&] { return p->kcol->col[op](a, nproj, p->stream); });
 }
 cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
   a.tw_fwd = p->ay.tw_fwd;
@@ -433,7 +473,7 @@ cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
   a.qx = which == 1 ? p->ax.q1 : p->ax.q2;
   a.qy = which == 1 ? p->ay.q1 : p->ay.q2;
   a.conj_q = conj;
-  return p->kcol->col[COL_Q](a, nproj, p->stream);
+  return enqueue(p, kColNames[COL_Q], [&] { return p->kcol->col[COL_Q](a, nproj, p->stream); });
 }
 
 #define LAUNCH(p, expr)                                    \
@@ -446,6 +486,7 @@ pwf_status compute_maxt2(pwf_plan* p, const float2* t) {
   const size_t n = (size_t)p->d.ny * p->d.nx;
   PWF_CUDA(p, cudaMemsetAsync(p->maxt2, 0, sizeof(float), p->stream));
   k_max_abs2<<<grid_for(n), 256, 0, p->stream>>>(t, n, p->maxt2);
+  p->launches++;
   PWF_CUDA(p, cudaGetLastError());
   return PWF_OK;
 }
@@ -518,8 +559,10 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   a.psi_out = psi;
   a.phi = st->phi;
   LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, a.B));
-  k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
-  PWF_CUDA(p, cudaGetLastError());
+  LAUNCH(p, enqueue(p, "finalize", [&] {
+    k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
+    return cudaGetLastError();
+  }));
   return PWF_OK;
 }
 
@@ -692,6 +735,7 @@ pwf_status pwf_plan_destroy(pwf_plan* p) {
   if (!p) return PWF_ERR_INVALID_ARG;
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->solve_state) pwf_state_destroy(p->solve_state);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (void* q : p->allocs) cudaFree(q);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   delete p;
@@ -850,6 +894,7 @@ pwf_status pwf_state_reset(pwf_plan* p, pwf_state* s) {
   PWF_CUDA(p, cudaMemsetAsync(s->phi, 0, (size_t)s->B * s->ny * s->nx * sizeof(float2), p->stream));
   PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)s->B * NACC * sizeof(double), p->stream));
   k_state_reset<<<1, 256, 0, p->stream>>>(s->it, s->active, s->iters, s->loss, s->corr, s->B);
+  p->launches++;
   PWF_CUDA(p, cudaGetLastError());
   return PWF_OK;
 }
@@ -930,7 +975,10 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
       p->stream = p->capture_stream;
       cudaGraph_t g = nullptr;
       PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+      const long long before = p->launches;
       r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
+      p->graph_kernels = p->launches - before;
+      p->launches = before;
       cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
       p->stream = user;
       if (r) {
@@ -947,6 +995,7 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
     const int check_every = 16;
     for (int k = 0; k < max_iter; k++) {
       PWF_CUDA(p, cudaGraphLaunch(p->graph, p->stream));
+      p->launches += p->graph_kernels;
       if (corr_tol > 0.0 && (k + 1) % check_every == 0 && k + 1 < max_iter) {
         DevIter it;
         PWF_CUDA(p, cudaMemcpyAsync(&it, st->it, sizeof(DevIter), cudaMemcpyDeviceToHost, p->stream));
@@ -956,6 +1005,48 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
     }
   }
   if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
+  return PWF_OK;
+}
+
+long long pwf_plan_launch_count(const pwf_plan* p) { return p ? p->launches : -1; }
+
+pwf_status pwf_profile_iteration(pwf_plan* p, const float* y, const void* t, void* psi, int32_t iters,
+                                 float* pass_ms, const char** pass_names, int32_t* n_passes) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!y || !t || !psi || iters < 1 || !pass_ms || !pass_names || !n_passes) return PWF_ERR_INVALID_ARG;
+  if (p->d.flags & PWF_FLAG_PLAIN) return PWF_ERR_UNSUPPORTED;
+  if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
+  pwf_state* st = p->solve_state;
+  if ((r = pwf_state_reset(p, st)) || (r = compute_maxt2(p, (const float2*)t))) return r;
+  if (!p->coherent && (r = compute_yhat(p, y, st->active))) return r;
+  PassArgs a = base_args(p);
+  a.active = st->active;
+  a.psi = (const float2*)psi;
+  a.out = p->X;
+  LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+  p->prof_names.clear();
+  p->prof_n = 0;
+  p->prof = true;
+  for (int k = 0; k < iters && r == PWF_OK; k++) r = fused_iteration(p, st, y, (const float2*)t, (float2*)psi, true, 0.0);
+  p->prof = false;
+  if (r) return r;
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  const size_t total = p->prof_names.size();
+  const size_t per = total / (size_t)iters;
+  if (per == 0 || per > PWF_MAX_PASSES) return fail(p, PWF_ERR_STATE, "unexpected pass count");
+  for (size_t i = 0; i < per; i++) {
+    double acc_ms = 0.0;
+    for (int k = 0; k < iters; k++) {
+      float ms = 0.f;
+      const size_t j = (size_t)k * per + i;
+      PWF_CUDA(p, cudaEventElapsedTime(&ms, p->ev_pool[2 * j], p->ev_pool[2 * j + 1]));
+      acc_ms += ms;
+    }
+    pass_ms[i] = (float)(acc_ms / iters);
+    pass_names[i] = p->prof_names[i];
+  }
+  *n_passes = (int32_t)per;
   return PWF_OK;
 }
 

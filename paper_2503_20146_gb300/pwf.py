@@ -89,6 +89,8 @@ def load(path: str | None = None):
         "pwf_state_load": ([_P, _P, _P, sz], i32),
         "pwf_status_string": ([i32], ctypes.c_char_p),
         "pwf_plan_last_error": ([_P], ctypes.c_char_p),
+        "pwf_plan_launch_count": ([_P], ctypes.c_longlong),
+        "pwf_profile_iteration": ([_P, _P, _P, _P, i32, _P, _P, _P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -251,6 +253,24 @@ def pwf_state_load(plan, state, data: bytes):
     buf = ctypes.create_string_buffer(data, len(data))
     _on_current_stream(plan)
     _check(load().pwf_state_load(plan, state, buf, len(data)), "pwf_state_load", plan)
+
+
+MAX_PASSES = 32
+
+
+def pwf_plan_launch_count(plan) -> int:
+    return int(load().pwf_plan_launch_count(plan))
+
+
+def pwf_profile_iteration(plan, y, t, psi, iters: int):
+    """Returns [(pass name, mean milliseconds)] for one fused iteration."""
+    ms = (ctypes.c_float * MAX_PASSES)()
+    names = (ctypes.c_char_p * MAX_PASSES)()
+    n = ctypes.c_int32()
+    _on_current_stream(plan)
+    _check(load().pwf_profile_iteration(plan, _ptr(y), _ptr(t), _ptr(psi), int(iters), ms, names,
+                                        ctypes.byref(n)), "pwf_profile_iteration", plan)
+    return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
 
 def pwf_status_string(status: int) -> str:

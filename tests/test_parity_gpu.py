@@ -287,5 +287,7 @@ def test_full_size_tomo_iterations_sampled(pwf, tomo):
     assert list(iters) == [3] * psi.shape[0]
     for b in (5, 150):
         ref = O.pwf(y[b].cpu().numpy().astype(np.float64), t32.astype(np.complex128), geom, 3)
-        assert phase_rms(psi[b].cpu().numpy(), ref.psi) <= PHASE_TOL
-        assert rel_l2(psi[b].cpu().numpy(), ref.psi) <= 1e-4
+        got = psi[b].cpu().numpy()
+        assert phase_rms(got, ref.psi) <= PHASE_TOL
+        # attenuation (Re psi) to the same absolute bound
+        assert float(np.sqrt(np.mean((got.real - ref.psi.real) ** 2))) <= PHASE_TOL
