@@ -1,0 +1,41 @@
+"""torch.autograd.Function over the PWF forward model (Eq. (1)).
+
+forward:  f = PhysicalModel(psi, t)                      -> pwf_forward
+backward: (dL/dpsi, dL/dt) for a real cotangent dL/df    -> pwf_forward_vjp
+
+Only psi and t are saved for the backward pass; the propagated fields (P1{x},
+the detector field v) are recomputed inside pwf_forward_vjp rather than
+stored, which keeps the memory of a batch at a few fields per projection.
+Gradients follow PyTorch's convention for complex inputs of a real loss:
+dL/dRe + i dL/dIm.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import pwf as _pwf
+
+
+class PWFForward(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, psi: torch.Tensor, t: torch.Tensor, plan: "_pwf.Plan"):
+        if psi.dtype != torch.complex64 or t.dtype != torch.complex64:
+            raise TypeError("psi and t must be complex64")
+        psi = psi.contiguous()
+        t = t.contiguous()
+        f = plan.forward(psi, t)
+        ctx.save_for_backward(psi, t)
+        ctx.plan = plan
+        return f
+
+    @staticmethod
+    def backward(ctx, grad_f: torch.Tensor):
+        psi, t = ctx.saved_tensors
+        want_psi, want_t = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gp, gt = ctx.plan.vjp(psi, t, grad_f.to(torch.float32).contiguous(), want_psi=want_psi, want_t=want_t)
+        return gp, gt, None
+
+
+def physical_model(psi: torch.Tensor, t: torch.Tensor, plan: "_pwf.Plan") -> torch.Tensor:
+    """Differentiable f = PhysicalModel(psi, t) on the CUDA path."""
+    return PWFForward.apply(psi, t, plan)
