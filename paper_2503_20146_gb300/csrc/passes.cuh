@@ -398,6 +398,130 @@ __global__ void __launch_bounds__(col_threads(N)) col_kernel(const PassArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// column pass, persistent and software-pipelined
+// ---------------------------------------------------------------------------
+// One CTA per SM walks over column tiles (proj, c0). While tile k is being
+// transformed in one shared-memory buffer, tile k+1 is copied into the other
+// with cp.async (16-byte chunks, one commit group per tile); results leave
+// from registers with plain stores, which drain while the next tile computes.
+// Same arithmetic as col_kernel. Not used for COL_PRECOND_REG (two inputs).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+__host__ __device__ constexpr size_t colp_smem_bytes(int n) { return 2 * col_smem_bytes(n); }
+// the double-buffered tile must fit the per-CTA shared memory (227 KB)
+__host__ __device__ constexpr bool colp_fits(int n) { return colp_smem_bytes(n) <= 200 * 1024; }
+
+template <int N, int OP>
+__global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassArgs a, int nproj) {
+  constexpr int EPT = ept_for(N), TPF = tpf_for(N), C = cols_for(N);
+  constexpr int NT = col_threads(N);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  constexpr int CHUNKS = N * C / 2;  // 16-byte chunks per tile
+  static_assert(CHUNKS % NT == 0, "tile chunks must divide evenly");
+  static_assert(OP != COL_PRECOND_REG, "two-input pass uses col_kernel");
+  extern __shared__ float2 smem[];
+
+  const int tid = threadIdx.x;
+  const int c = tid % C, t = tid / C;
+  const int tiles_per_proj = a.nx / C;
+  const int ntiles = nproj * tiles_per_proj;
+  const size_t ld = (size_t)a.nx;
+
+  auto tile_base = [&](int tile, int& proj, int& col0) -> size_t {
+    proj = a.proj0 + tile / tiles_per_proj;
+    col0 = (tile % tiles_per_proj) * C;
+    return (size_t)proj * a.ny * a.nx + col0;
+  };
+  auto prefetch = [&](int tile, float2* buf) {
+    int proj, col0;
+    const size_t b = tile_base(tile, proj, col0);
+    if (a.active != nullptr && a.active[proj] == 0) return;
+#pragma unroll
+    for (int k = 0; k < CHUNKS / NT; k++) {
+      const int q = tid + k * NT;           // chunk index: row q / (C/2), pair q % (C/2)
+      const int row = q / (C / 2), pr = q % (C / 2);
+      cp_async16(buf + row * C + 2 * pr, a.in + b + (size_t)row * ld + 2 * pr);
+    }
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, smem);
+  cp_async_commit();
+  for (int k = 0; tile < ntiles; k++, tile += gridDim.x) {
+    float2* cur = smem + (k & 1) * (C * N);
+    float2* nxt = smem + ((k + 1) & 1) * (C * N);
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    int proj, col0;
+    const size_t base = tile_base(tile, proj, col0) + c;
+    const int col = col0 + c;
+    if (a.active != nullptr && a.active[proj] == 0) {
+      __syncthreads();
+      continue;
+    }
+    const ColLayout<C> sm{cur + c};
+    float2 v[EPT];
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+
+    if constexpr (OP == COL_IFFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) v[j] = cscale(sm[slot_index<N, RK>(t, j)], a.scale);
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) v[j] = sm[slot_index<N, RS>(t, j)];
+      fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+      if constexpr (OP == COL_Q) {
+        const float2 qx = __ldg(&a.qx[col]);
+#pragma unroll
+        for (int j = 0; j < EPT; j++) {
+          float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
+          if (a.conj_q) q = cconj(q);
+          v[j] = cscale(cmul(v[j], q), a.scale);
+        }
+      } else if constexpr (OP == COL_IOTF) {
+        const float ixv = __ldg(&a.ix[col]) * a.scale;
+#pragma unroll
+        for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], ixv * __ldg(&a.iy[slot_index<N, RK>(t, j)]));
+      } else if constexpr (OP == COL_RESID_IOTF2) {
+        const float ixv = __ldg(&a.ix[col]);
+#pragma unroll
+        for (int j = 0; j < EPT; j++) {
+          const int ky = slot_index<N, RK>(t, j);
+          const float w = ixv * __ldg(&a.iy[ky]);
+          const float2 yh = a.yhat[base + (size_t)ky * ld];
+          const float2 r = make_float2(fmaf(w, v[j].x, -yh.x), fmaf(w, v[j].y, -yh.y));
+          part[0] = fmaf(r.x, r.x, fmaf(r.y, r.y, part[0]));
+          v[j] = cscale(r, w * a.scale);
+        }
+        part[0] *= a.scale;
+      }
+    }
+    if constexpr (OP == COL_FFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RK>(t, j) * ld] = v[j];
+    } else {
+      fft_run<N, INV>(v, sm, t, a.tw_inv);
+#pragma unroll
+      for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
+    }
+    if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, cur);
+    __syncthreads();  // cur is refilled by the prefetch of the next-but-one tile
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch for one transform length
 // ---------------------------------------------------------------------------
 using PassFn = cudaError_t (*)(const PassArgs&, int nproj, cudaStream_t);
@@ -411,7 +535,25 @@ cudaError_t prep_row() {
 }
 template <int N, int OP>
 cudaError_t prep_col() {
-  return cudaFuncSetAttribute(col_kernel<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem_bytes(N));
+  cudaError_t e = cudaFuncSetAttribute(col_kernel<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)col_smem_bytes(N));
+  if constexpr (OP != COL_PRECOND_REG && colp_fits(N)) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(col_kernel_pipe<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)colp_smem_bytes(N));
+  }
+  return e;
+}
+
+// number of SMs of the current device (persistent grids)
+inline int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return sms;
 }
 
 // row pass over the ny rows of nproj projections starting at a.proj0
@@ -427,6 +569,14 @@ cudaError_t launch_row(const PassArgs& a, int nproj, cudaStream_t s) {
 template <int N, int OP>
 cudaError_t launch_col(const PassArgs& a, int nproj, cudaStream_t s) {
   constexpr int C = cols_for(N);
+  const long long ntiles = (long long)nproj * (a.nx / C);
+  if constexpr (OP != COL_PRECOND_REG && colp_fits(N)) {
+    if (ntiles >= 2 * device_sms()) {
+      const int grid = (int)(ntiles < device_sms() ? ntiles : device_sms());
+      col_kernel_pipe<N, OP><<<grid, col_threads(N), colp_smem_bytes(N), s>>>(a, nproj);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
   col_kernel<N, OP><<<grid, col_threads(N), col_smem_bytes(N), s>>>(a);
   return cudaGetLastError();

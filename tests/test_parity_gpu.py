@@ -240,6 +240,38 @@ def test_nonfinite_measurement_reported(pwf):
 
 
 # ----------------------------------------------------------------------------
+# batches large enough for the persistent, pipelined column kernel
+# (used once a pass has at least two column tiles per SM)
+# ----------------------------------------------------------------------------
+BIG = [("b64_128_iotf", 64, 128, 128), ("b40_512_iotf", 40, 512, 512), ("b24_768x256_iotf", 24, 768, 256),
+       ("b20_256x1536_iotf", 20, 256, 1536)]
+
+
+@pytest.mark.parametrize("name,batch,ny,nx", BIG, ids=[c[0] for c in BIG])
+def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
+    w = W2
+    geom = geometry(w, ny, nx)
+    psi, t = blob_batch(w, batch, ny, nx)
+    psi, t = to_c64(psi), to_c64(t)
+    y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(5).standard_normal((batch, ny, nx)), 0, None))
+    with plan_for(pwf, geom, batch) as plan:
+        f = plan.forward(dev(psi), dev(t)).cpu().numpy()
+        g, L = plan.gradient(dev(psi), dev(t), dev(y))
+        g, L = g.cpu().numpy(), L.cpu().numpy()
+        p = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+        plan.solve(dev(y), dev(t), p, 3)
+        p = p.cpu().numpy()
+    for b in (0, batch // 2, batch - 1):
+        P64, T64 = psi[b].astype(np.complex128), t.astype(np.complex128)
+        assert rel_l2(f[b], O.PhysicalModel(P64, T64, geom)[0]) <= FWD_TOL
+        ge, le = O.gradient(P64, T64, y[b].astype(np.float64), geom)
+        assert rel_l2(g[b], ge) <= GRAD_TOL
+        assert abs(L[b] - le) <= 1e-5 * le
+        ref = O.pwf(y[b].astype(np.float64), T64, geom, 3)
+        assert phase_rms(p[b], ref.psi) <= PHASE_TOL
+
+
+# ----------------------------------------------------------------------------
 # full-size tomographic series (180 x 1024^2), sampled projections
 # ----------------------------------------------------------------------------
 def tomo_inputs(n_angles=180, n=1024):
