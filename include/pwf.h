@@ -164,6 +164,30 @@ long long pwf_plan_launch_count(const pwf_plan* plan);
 pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t iters,
                                  float* pass_ms, const char** pass_names, int32_t* n_passes);
 
+/* Forward model for callers that cannot allocate device memory. The paper has
+ * no counterpart: this is an interface choice, not part of the method.
+ * pwf_forward needs a plan, and creating a plan allocates device memory. Some
+ * callers cannot allow that: processes whose device memory is owned by another
+ * allocator or reserved up front (a framework's caching pool, a fixed budget of
+ * an acquisition pipeline), and code that cannot take the device-wide
+ * synchronisation cudaMalloc/cudaFree imply. This call computes the same f as
+ * pwf_forward (x = exp(psi); v = P2{t P1{x}}; f = Re Filter(|v|^2, IOTF)) with
+ * the same kernels, but keeps its scratch field and 1-D tables in fixed
+ * file-scope device arrays of the library (about 16.2 MiB on every GPU where
+ * the library's code is loaded, held until the process exits). It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   desc: as for pwf_plan_create (eta, gamma, alpha and flags are not used);
+ *         the work is enqueued on desc->stream.
+ *   psi, t, f: as for pwf_forward (caller-owned device memory).
+ * Limit: batch * ny * nx <= 2097152 (2^21) complex elements; larger problems
+ * return PWF_ERR_UNSUPPORTED before any work. Other errors as pwf_forward.
+ * The first call on a device does a one-time set-up on that device (resolves
+ * the device addresses of the arrays, raises kernel shared-memory limits);
+ * make that first call before any stream capture. Every call rewrites and
+ * shares the same arrays, which keep the last call's contents; calls that
+ * overlap on the GPU (for example on two streams at once) race on them. */
+pwf_status pwf_forward_noalloc(const pwf_plan_desc* desc, const void* psi, const void* t, float* f);
+
 /* Human-readable name of a status code (static storage). */
 const char* pwf_status_string(pwf_status s);
 /* Last error message recorded on the plan (static per plan; never NULL). */

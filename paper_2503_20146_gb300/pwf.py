@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "pwf_plan_last_error": ([_P], ctypes.c_char_p),
         "pwf_plan_launch_count": ([_P], ctypes.c_longlong),
         "pwf_profile_iteration": ([_P, _P, _P, _P, i32, _P, _P, _P], i32),
+        "pwf_forward_noalloc": ([ctypes.POINTER(pwf_plan_desc), _P, _P, _P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +176,16 @@ def _on_current_stream(plan):
 def pwf_forward(plan, psi, t, f):
     _on_current_stream(plan)
     _check(load().pwf_forward(plan, _ptr(psi), _ptr(t), _ptr(f)), "pwf_forward", plan)
+
+
+def pwf_forward_noalloc(desc: "PlanDesc", psi, t, f):
+    """Forward model without any device allocation by the library (scratch in
+    fixed device arrays); for callers that cannot allocate. Runs on the current
+    torch stream."""
+    d = pwf_plan_desc(desc.batch, desc.ny, desc.nx, desc.pixel_m, desc.wavelength_m, desc.L1_m, desc.L2_m,
+                      desc.xcoh_m, desc.ycoh_m, desc.gamma, desc.alpha_re, desc.alpha_im, desc.eta,
+                      desc.flags, _stream_ptr())
+    _check(load().pwf_forward_noalloc(ctypes.byref(d), _ptr(psi), _ptr(t), _ptr(f)), "pwf_forward_noalloc")
 
 
 def pwf_gradient(plan, psi, t, y, g, loss=None):
