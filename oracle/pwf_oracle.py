@@ -38,6 +38,12 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
   R7  The gradient w.r.t. the diffuser (simultaneous retrieval, Methods and
       Fig. S12) is not printed; it is derived here from Eq. (1) in the same
       Wirtinger convention as the sample gradient.
+  R13 K-mode variant (not the paper's form; a workload option): mutually
+      incoherent tilted plane-wave modes of a Gaussian source replace the IPSF
+      convolution. Nodes and weights are the tensor Gauss-Hermite rule of the
+      standard normal (k1 = 1, 3, 5 per axis, K = k1^2); a node n walks the
+      pattern by sigma n pixels at the detector, i.e. a tilt of
+      sigma n p / (lambda (L1 + L2)) cycles/m, rounded to whole bins.
 """
 from __future__ import annotations
 
@@ -307,3 +313,124 @@ def forward_vjp_batch(psi_b, t, grad_f_b, geom: Geometry):
 
 def pwf_batch(y_b, t, geom: Geometry, max_iter: int, corr_tol=None):
     return [pwf(y, t, geom, max_iter, corr_tol) for y in y_b]
+
+
+# ----------------------------------------------------------------------------
+# K-mode partial-coherence variant (a workload option, not the paper's form)
+# ----------------------------------------------------------------------------
+# The paper models partial coherence by the IPSF convolution of Eq. (1). The
+# variant below instead sums the intensities of K mutually incoherent source
+# modes: tilted plane waves s_j(r) = exp(i 2 pi q_j . r) with weights w_j,
+#   f = sum_j w_j |P2{ t P1{ x s_j } }|^2,
+# the tilts on a tensor Gauss-Hermite grid of a Gaussian source whose walk-off
+# over L1 + L2 has standard deviation sigma pixels at the detector (reading
+# R13). Tilts are rounded to whole frequency bins so that s_j is periodic on
+# the grid. The gradient follows by the same Wirtinger calculus as Algorithm
+# S2's WirtingerDerivative, with the IOTF filter replaced by the mode sum:
+#   g = sum_j w_j conj(x s_j) P1^H{ conj(t) P2^H{ v_j (-e) } } / max|t|^2.
+def gauss_hermite(k1: int):
+    """Nodes and weights (summing to 1) of the k1-point Gauss-Hermite rule for
+    the standard normal density (probabilists' Hermite polynomials)."""
+    if k1 == 1:
+        return np.array([0.0]), np.array([1.0])
+    if k1 == 3:
+        r3 = np.sqrt(3.0)
+        return np.array([-r3, 0.0, r3]), np.array([1.0 / 6, 2.0 / 3, 1.0 / 6])
+    if k1 == 5:
+        a, b = np.sqrt(5.0 - np.sqrt(10.0)), np.sqrt(5.0 + np.sqrt(10.0))
+        wa, wb = (7.0 + 2.0 * np.sqrt(10.0)) / 60.0, (7.0 - 2.0 * np.sqrt(10.0)) / 60.0
+        return np.array([-b, -a, 0.0, a, b]), np.array([wb, wa, 8.0 / 15, wa, wb])
+    raise ValueError("k1 must be 1, 3 or 5")
+
+
+def source_modes(geom: Geometry, n_modes: int, sigma_px: float):
+    """[(mx, my, w)] for K = n_modes = k1^2 modes: integer tilt bins along x and
+    y and the weight. A detector walk-off of s metres needs the tilt
+    q = s / (lambda (L1 + L2)) cycles/m, i.e. q N p bins."""
+    k1 = int(round(np.sqrt(n_modes)))
+    if k1 * k1 != n_modes:
+        raise ValueError("n_modes must be a square (1, 9, 25)")
+    nodes, weights = gauss_hermite(k1)
+    z = geom.wavelength * (geom.L1 + geom.L2)
+    modes = []
+    for ny_i, wy in zip(nodes, weights):
+        for nx_i, wx in zip(nodes, weights):
+            sx, sy = sigma_px * nx_i * geom.pixel, sigma_px * ny_i * geom.pixel
+            mx = int(np.rint(sx / z * geom.nx * geom.pixel)) if z > 0 else 0
+            my = int(np.rint(sy / z * geom.ny * geom.pixel)) if z > 0 else 0
+            modes.append((mx, my, wx * wy))
+    return modes
+
+
+def mode_wave(geom: Geometry, mx: int, my: int) -> np.ndarray:
+    """s(r) = exp(i 2 pi (mx x / nx + my y / ny)) on the pixel grid."""
+    y = np.arange(geom.ny)[:, None]
+    x = np.arange(geom.nx)[None, :]
+    return np.exp(2j * np.pi * (mx * x / geom.nx + my * y / geom.ny))
+
+
+def ModalPhysicalModel(psi, t, geom: Geometry, modes):
+    """f = sum_j w_j |P2{t P1{x s_j}}|^2; returns f, x and the fields v_j."""
+    x = np.exp(psi)
+    f = np.zeros(psi.shape)
+    vs = []
+    for mx, my, w in modes:
+        v = FreePropagation(x * mode_wave(geom, mx, my), geom, geom.L1)
+        v = FreePropagation(t * v, geom, geom.L2)
+        f += w * np.abs(v) ** 2
+        vs.append(v)
+    return f, x, vs
+
+
+def ModalWirtingerDerivative(e, x, vs, t, geom: Geometry, modes):
+    """g = sum_j w_j conj(x s_j) P1^H{conj(t) P2^H{v_j (-e)}} / max|t|^2."""
+    g = np.zeros(x.shape, complex)
+    for (mx, my, w), v in zip(modes, vs):
+        gj = FreePropagation(v * (-e), geom, -geom.L2)
+        gj = FreePropagation(np.conj(t) * gj, geom, -geom.L1)
+        g += w * np.conj(x * mode_wave(geom, mx, my)) * gj
+    return g / np.max(np.abs(t) ** 2)
+
+
+def modal_gradient(psi, t, y, geom: Geometry, modes):
+    f, x, vs = ModalPhysicalModel(psi, t, geom, modes)
+    e = y - f
+    return ModalWirtingerDerivative(e, x, vs, t, geom, modes), loss(y, f)
+
+
+def modal_pwf_iteration(psi, phi, mu, y, t, geom: Geometry, modes, Pinv=None, Gamma2=None):
+    """Algorithm S1's loop body with the modal model in place of PhysicalModel /
+    WirtingerDerivative (the preconditioner, regularizer and Nesterov steps are
+    unchanged; Gamma^2 uses x_coh, y_coh of geom)."""
+    if Pinv is None:
+        Pinv = precond_filter(geom)
+    if Gamma2 is None:
+        Gamma2 = reg_window(geom)
+    phi_prev, mu_prev = phi, mu
+    f, x, vs = ModalPhysicalModel(psi, t, geom, modes)
+    e = y - f
+    g = ModalWirtingerDerivative(e, x, vs, t, geom, modes)
+    g = Preconditioner(g, Pinv) + Regularizer(psi, Gamma2, geom.alpha)
+    phi = psi - geom.eta * g
+    mu = nesterov_mu(mu)
+    psi_new = phi + ((mu_prev - 1.0) / mu) * (phi - phi_prev)
+    return psi_new, phi, mu, loss(y, f)
+
+
+def modal_pwf(y, t, geom: Geometry, modes, max_iter: int, corr_tol=None) -> PWFResult:
+    psi = np.zeros((geom.ny, geom.nx), np.complex128)
+    phi = np.zeros_like(psi)
+    mu = 1.0
+    Pinv, Gamma2 = precond_filter(geom), reg_window(geom)
+    losses, corrs = [], []
+    it = 0
+    while it < max_iter:
+        x_old = np.exp(psi)
+        psi, phi, mu, L = modal_pwf_iteration(psi, phi, mu, y, t, geom, modes, Pinv, Gamma2)
+        it += 1
+        losses.append(L)
+        c = correlation(np.exp(psi), x_old)
+        corrs.append(c)
+        if corr_tol is not None and c > corr_tol:
+            break
+    return PWFResult(psi, it, losses, corrs)

@@ -299,3 +299,67 @@ def test_paper_constants_golden():
     assert O.STOP_CORRELATION == 10.0 ** c["stop_exponent"]["value"]
     lam_10kev = 1.23984198e-6 / 1.0e4
     assert abs(lam_10kev - c["wavelength_10keV_nm"]["value"] * 1e-9) < 0.001e-9
+
+
+# ----------------------------------------------------------------------------
+# K-mode variant (reading R13)
+# ----------------------------------------------------------------------------
+def test_gauss_hermite_rules_integrate_normal_moments():
+    for k1, exact_to in ((3, 5), (5, 9)):
+        x, w = O.gauss_hermite(k1)
+        for m in range(exact_to + 1):
+            moment = 0.0 if m % 2 else float(np.prod(np.arange(m - 1, 0, -2))) if m else 1.0
+            assert abs(np.sum(w * x ** m) - moment) < 1e-12
+
+
+def test_single_mode_is_the_coherent_model():
+    rng = np.random.default_rng(12)
+    g = geom(32, 48)
+    psi = 0.3 * crandn(rng, (32, 48))
+    t = np.exp(1j * rng.standard_normal((32, 48)))
+    f1 = O.ModalPhysicalModel(psi, t, g, [(0, 0, 1.0)])[0]
+    assert np.max(np.abs(f1 - O.PhysicalModel(psi, t, g)[0])) < 1e-13
+
+
+def test_tilted_modes_shift_the_field_by_lambda_L2_q():
+    """With L1 = 0, a mode tilted by m bins propagates to
+    v_m(r) = s_m(r) exp(-i pi lambda L2 |q|^2) v_0(r - lambda L2 q), q = m/(N p)
+    (the Fresnel shift theorem; exact on the grid for the paraxial kernel up to
+    spectral content that wraps past Nyquist, here on periodic smooth inputs;
+    the angular-spectrum correction is ~1e-8 rad)."""
+    n = 64
+    g = O.Geometry(n, n, 1e-6, S.WAVELENGTH_20KEV_M, 0.0, 0.4)
+    rng = S.rng_for(1, 5)
+    psi = 0.4j * np.angle(S.diffuser(n, n, rng, corr_px=6.0, std_rad=1.0)) - 0.02
+    t = S.diffuser(n, n, rng, corr_px=6.0, std_rad=0.5)
+    v0 = O.ModalPhysicalModel(psi, t, g, [(0, 0, 1.0)])[2][0]
+    V0 = np.fft.fft2(v0)
+    kx = np.fft.fftfreq(n)[None, :]
+    ky = np.fft.fftfreq(n)[:, None]
+    for mx, my in ((3, 0), (-2, 5)):
+        vm = O.ModalPhysicalModel(psi, t, g, [(mx, my, 1.0)])[2][0]
+        qx, qy = mx / (n * g.pixel), my / (n * g.pixel)
+        dx, dy = g.wavelength * g.L2 * qx / g.pixel, g.wavelength * g.L2 * qy / g.pixel   # pixels
+        shifted = np.fft.ifft2(V0 * np.exp(-2j * np.pi * (kx * dx + ky * dy)))
+        expect = O.mode_wave(g, mx, my) * np.exp(-1j * np.pi * g.wavelength * g.L2 * (qx * qx + qy * qy)) * shifted
+        assert np.max(np.abs(vm - expect)) < 1e-6 * np.max(np.abs(v0))     # 2-4e-7 seen; a sign error gives > 0.3
+        assert np.max(np.abs(np.abs(vm) - np.abs(v0))) > 1e-2 * np.max(np.abs(v0))   # the pattern moved
+
+
+def test_modal_gradient_matches_central_differences():
+    rng = np.random.default_rng(13)
+    g = geom(32, 32, xcoh=4e-6, ycoh=4e-6)
+    modes = O.source_modes(O.Geometry(32, 32, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4), 9, 1.5)
+    assert len({(mx, my) for mx, my, _ in modes}) == 9
+    psi = 0.3 * crandn(rng, (32, 32))
+    t = np.exp(1j * rng.standard_normal((32, 32))) * (1 + 0.2 * rng.standard_normal((32, 32)))
+    y = rng.uniform(0.5, 1.5, (32, 32))
+    gr, L = O.modal_gradient(psi, t, y, g, modes)
+    G = 4.0 * np.max(np.abs(t) ** 2) * gr
+    for _ in range(2):
+        d = crandn(rng, psi.shape)
+        an = np.sum(G.real * d.real + G.imag * d.imag)
+        eps = 1e-6
+        Lp = O.loss(y, O.ModalPhysicalModel(psi + eps * d, t, g, modes)[0])
+        Lm = O.loss(y, O.ModalPhysicalModel(psi - eps * d, t, g, modes)[0])
+        assert abs((Lp - Lm) / (2 * eps) - an) <= 1e-7 * abs(an)
