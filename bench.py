@@ -302,6 +302,8 @@ def main():
     del f, psi_true
     psi = torch.zeros((batch, w.ny, w.nx), dtype=torch.complex64, device=dev)
 
+    tuned = P.pwf_plan_describe(plan.handle)
+
     # warm-up (captures the iteration graph)
     plan.solve(y, t, psi, args.warmup, read_back=False)
     torch.cuda.synchronize()
@@ -410,7 +412,8 @@ def main():
             "config": {"workload": w.name, "projections_per_gpu": batch, "ny": w.ny, "nx": w.nx,
                        "coherence": "IOTF, Gaussian sigma = 2 px" if w.xcoh_m > 0 else "coherent",
                        "eta": w.eta, "l2_flush": "inputs larger than L2 (state ~1.5 GB per field)",
-                       "step": "one PWF iteration over all projections"},
+                       "step": "one PWF iteration over all projections",
+                       "column_shapes": tuned},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "iteration": iteration,

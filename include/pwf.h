@@ -54,6 +54,7 @@ typedef struct pwf_state pwf_state;
 #define PWF_FLAG_NO_REG 0x2u     /* alpha := 0 (Regularizer off)                   */
 #define PWF_FLAG_PLAIN 0x4u      /* unfused per-operation kernels, one projection at
                                     a time: Algorithm S2 executed step by step     */
+#define PWF_FLAG_NO_TUNE 0x8u    /* skip the plan-time column-pass autotuning      */
 
 /* Inputs of Algorithm S1 other than y and t. All lengths in metres. */
 typedef struct {
@@ -72,7 +73,11 @@ typedef struct {
   void* stream;      /* cudaStream_t */
 } pwf_plan_desc;
 
-/* Creates a plan. Builds the 1-D frequency tables of Q_k = exp(i 2 pi (w - 1/lambda) L)
+/* Creates a plan. Unless PWF_FLAG_NO_TUNE is set, the plan also times every
+ * column-pass shape it was built with (columns per tile, pipelined or not) on
+ * its own zeroed workspace, on desc->stream, and keeps the fastest per pass
+ * (a few launches per shape; the call synchronises that stream).
+ * Builds the 1-D frequency tables of Q_k = exp(i 2 pi (w - 1/lambda) L)
  * (FreePropagation of Algorithm S2, constant piston dropped), IOTF (Eq. (5)),
  * P^-1 = 1/(u^2 + v^2) in cycles per pixel with P^-1(0) = 0 (Eq. (11)) and
  * Gamma^2 = 1 - STF (Eqs. (14)-(15)). The propagator phase is applied as the sum
@@ -161,6 +166,11 @@ pwf_status pwf_state_load(pwf_plan* plan, pwf_state* state, const void* host_buf
  * pwf_solve. Synchronises. PWF_ERR_UNSUPPORTED for PWF_FLAG_PLAIN plans. */
 #define PWF_MAX_PASSES 32
 long long pwf_plan_launch_count(const pwf_plan* plan);
+/* Writes a one-line description of the plan (sizes and the column-pass shape
+ * chosen per pass, e.g. "col_q=C8p" = 8 columns per tile, pipelined) into buf
+ * (NUL-terminated, truncated to len); returns the length needed including the
+ * NUL. buf may be NULL to query the length. */
+size_t pwf_plan_describe(const pwf_plan* plan, char* buf, size_t len);
 pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t iters,
                                  float* pass_ms, const char** pass_names, int32_t* n_passes);
 

@@ -267,6 +267,7 @@ struct pwf_plan {
   cudaStream_t capture_stream = nullptr;
   const LengthKernels* krow = nullptr;  // length nx
   const LengthKernels* kcol = nullptr;  // length ny
+  int colsel[NUM_COL_OPS] = {0, 0, 0, 0, 0, 0};  // chosen column-pass shape per op
   AxisTables ax, ay;
   bool coherent = false;
   // workspace
@@ -465,7 +466,7 @@ cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a.u2y = p->ay.u2;
   a.ex = p->ax.stf;
   a.ey = p->ay.stf;
-  return enqueue(p, kColNames[op], [&] { return p->kcol->col[op](a, nproj, p->stream); });
+  return enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
 }
 cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
   a.tw_fwd = p->ay.tw_fwd;
@@ -473,7 +474,8 @@ cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
   a.qx = which == 1 ? p->ax.q1 : p->ax.q2;
   a.qy = which == 1 ? p->ay.q1 : p->ay.q2;
   a.conj_q = conj;
-  return enqueue(p, kColNames[COL_Q], [&] { return p->kcol->col[COL_Q](a, nproj, p->stream); });
+  return enqueue(p, kColNames[COL_Q],
+                 [&] { return p->kcol->colv[COL_Q][p->colsel[COL_Q]].launch(a, nproj, p->stream); });
 }
 
 #define LAUNCH(p, expr)                                    \
@@ -645,6 +647,60 @@ pwf_status plain_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   return PWF_OK;
 }
 
+// Plan-time autotuning of the column passes: every shape variant of every
+// column op is run once to warm up and then timed over two launches on the
+// plan's own (zeroed) workspace, and the fastest is kept.
+pwf_status tune_columns(pwf_plan* p) {
+  const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
+  PWF_CUDA(p, cudaMemsetAsync(p->X, 0, n * sizeof(float2), p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->S, 0, n * sizeof(float2), p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->YH, 0, n * sizeof(float2), p->stream));
+  cudaEvent_t e0, e1;
+  PWF_CUDA(p, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(p, cudaGetLastError(), "cudaEventCreate");
+  }
+  PassArgs a = base_args(p);
+  a.in = p->X;
+  a.out = p->X;
+  a.aux_in = p->S;
+  a.yhat = p->YH;
+  a.tw_fwd = p->ay.tw_fwd;
+  a.tw_inv = p->ay.tw_inv;
+  a.qx = p->ax.q1;
+  a.qy = p->ay.q1;
+  a.ix = p->ax.iotf;
+  a.iy = p->ay.iotf;
+  a.u2x = p->ax.u2;
+  a.u2y = p->ay.u2;
+  a.ex = p->ax.stf;
+  a.ey = p->ay.stf;
+  cudaError_t err = cudaSuccess;
+  for (int op = 0; op < NUM_COL_OPS && err == cudaSuccess; op++) {
+    float best = 1e30f;
+    for (int v = 0; v < p->kcol->ncolv[op] && err == cudaSuccess; v++) {
+      const PassFn fn = p->kcol->colv[op][v].launch;
+      if ((err = fn(a, a.B, p->stream)) != cudaSuccess) break;
+      cudaEventRecord(e0, p->stream);
+      for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) err = fn(a, a.B, p->stream);
+      cudaEventRecord(e1, p->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        p->colsel[op] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(p, err, "column-pass tuning");
+  PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
+  return PWF_OK;
+}
+
 bool size_ok(int n) { return kernels_for_length(n) != nullptr; }
 
 pwf_status check_plan(pwf_plan* p) {
@@ -681,7 +737,7 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   const pwf_plan_desc& d = *desc;
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
-      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN)))
+      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE)))
     return PWF_ERR_INVALID_ARG;
   if (!size_ok(d.ny) || !size_ok(d.nx)) return PWF_ERR_UNSUPPORTED;
   // evanescent bins and the separable-propagator bound, in double precision
@@ -716,16 +772,21 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       return PWF_ERR_CUDA;
     }
   for (int op = 0; op < NUM_COL_OPS; op++)
-    if (p->kcol->col_prep[op]() != cudaSuccess) {
-      cudaGetLastError();
-      pwf_plan_destroy(p);
-      return PWF_ERR_CUDA;
-    }
+    for (int v = 0; v < p->kcol->ncolv[op]; v++)
+      if (p->kcol->colv[op][v].prep() != cudaSuccess) {
+        cudaGetLastError();
+        pwf_plan_destroy(p);
+        return PWF_ERR_CUDA;
+      }
   if (cudaMemset(p->acc, 0, (size_t)d.batch * NACC * sizeof(double)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     pwf_plan_destroy(p);
     return PWF_ERR_CUDA;
+  }
+  if (!(d.flags & PWF_FLAG_NO_TUNE) && (r = tune_columns(p)) != PWF_OK) {
+    pwf_plan_destroy(p);
+    return r;
   }
   *out = p;
   return PWF_OK;
@@ -1009,6 +1070,21 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
 }
 
 long long pwf_plan_launch_count(const pwf_plan* p) { return p ? p->launches : -1; }
+
+size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
+  if (!p) return 0;
+  char tmp[512];
+  size_t o = 0;
+  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
+  for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp); op++) {
+    const ColVariant& v = p->kcol->colv[op][p->colsel[op]];
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=C%d%s", kColNames[op], v.C, v.pipe ? "p" : "");
+  }
+  if (buf && len) {
+    std::snprintf(buf, len, "%s", tmp);
+  }
+  return std::strlen(tmp) + 1;
+}
 
 pwf_status pwf_profile_iteration(pwf_plan* p, const float* y, const void* t, void* psi, int32_t iters,
                                  float* pass_ms, const char** pass_names, int32_t* n_passes) {

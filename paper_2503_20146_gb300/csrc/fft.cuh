@@ -240,11 +240,19 @@ struct RowLayout {
 };
 __host__ __device__ constexpr int row_smem_len(int n) { return n + n / 16; }
 
-// C transforms interleaved: element p of column c at p*C + c
+// C transforms interleaved: element p of column c at row(p)*C + c. With 8 (4)
+// columns a row covers half (a quarter) of the banks, and the first stage of a
+// transform writes rows b*R0 + r, which for the consecutive b of a warp all
+// start on the same bank. One empty row after every 16 (row(p) = p + p/16)
+// spreads those rows evenly for R0 = 16 and R0 = 8, while the aligned groups
+// of consecutive rows of every other access stay contiguous.
+__host__ __device__ constexpr int col_pad_rows(int c) { return (c == 8 || c == 4) ? 1 : 0; }
+__host__ __device__ constexpr int col_row(int p, int c) { return col_pad_rows(c) ? p + (p >> 4) : p; }
+__host__ __device__ constexpr int col_tile_rows(int n, int c) { return col_pad_rows(c) ? n + n / 16 : n; }
 template <int C>
 struct ColLayout {
   float2* base;  // already offset by c
-  __device__ __forceinline__ float2& operator[](int p) const { return base[p * C]; }
+  __device__ __forceinline__ float2& operator[](int p) const { return base[col_row(p, C) * C]; }
 };
 
 // ---------------------------------------------------------------------------

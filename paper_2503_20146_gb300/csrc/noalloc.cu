@@ -131,7 +131,7 @@ pwf_status setup_device(DevPtrs** out) {
           return PWF_ERR_CUDA;
         }
       for (int op : {COL_Q, COL_IOTF})
-        if (k->col_prep[op]() != cudaSuccess) {
+        if (k->colv[op][0].prep() != cudaSuccess) {
           cudaGetLastError();
           return PWF_ERR_CUDA;
         }
@@ -203,7 +203,7 @@ extern "C" pwf_status pwf_forward_noalloc(const pwf_plan_desc* desc, const void*
     c.qy = dp->q + (L == 1 ? 2 : 3) * kMaxN;
     c.ix = dp->iotf;
     c.iy = dp->iotf + kMaxN;
-    return kcol->col[op](c, d.batch, s);
+    return kcol->colv[op][0].launch(c, d.batch, s);
   };
   const bool coherent = d.xcoh_m == 0.0 && d.ycoh_m == 0.0;
   cudaError_t e;

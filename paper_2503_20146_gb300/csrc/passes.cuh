@@ -23,14 +23,9 @@ __host__ __device__ constexpr int rows_for(int n) {
   int r = 256 / tpf_for(n);
   return r < 1 ? 1 : (r > 16 ? 16 : r);
 }
-__host__ __device__ constexpr int cols_for(int n) { return n >= 1024 ? 8 : 16; }
 __host__ __device__ constexpr int row_threads(int n) { return rows_for(n) * tpf_for(n); }
-__host__ __device__ constexpr int col_threads(int n) { return cols_for(n) * tpf_for(n); }
 __host__ __device__ constexpr size_t row_smem_bytes(int n) {
   return (size_t)rows_for(n) * row_smem_len(n) * sizeof(float2);
-}
-__host__ __device__ constexpr size_t col_smem_bytes(int n) {
-  return (size_t)cols_for(n) * n * sizeof(float2);
 }
 
 // per-projection accumulators (float64)
@@ -124,6 +119,11 @@ struct RowT {
                               : (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) ? 5 : 0;
 };
 
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ float2 cexpf2(float2 z) {
   float s, c;
   sincosf(z.y, &s, &c);
@@ -159,7 +159,7 @@ __device__ __forceinline__ void block_reduce_add(const float (&part)[5], double*
 // row pass
 // ---------------------------------------------------------------------------
 template <int N, int OP>
-__global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a) {
   constexpr int EPT = ept_for(N), TPF = tpf_for(N), ROWS = rows_for(N);
   constexpr int RS = first_radix<N, FWD>();  // slot radix of real-space data
   constexpr int RK = last_radix<N, FWD>();   // slot radix of spectra
@@ -176,6 +176,20 @@ __global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
   const RowLayout sm{smem + rr * row_smem_len(N)};
   float2 v[EPT];
   float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+
+  // Pull this row's side inputs into L2 while the first transform runs.
+  if (t == 0) {
+    if constexpr (OP == ROW_MUL_T || OP == ROW_GRADT) l2_prefetch(a.t + (size_t)yrow * N, N * sizeof(float2));
+    if constexpr (OP == ROW_GRADT) l2_prefetch(a.u1 + rb, N * sizeof(float2));
+    if constexpr (OP == ROW_MUL_V) l2_prefetch(a.v + rb, N * sizeof(float2));
+    if constexpr (OP == ROW_RESID || OP == ROW_COH_RESID || OP == ROW_COH_VJP) l2_prefetch(a.y + rb, N * sizeof(float));
+    if constexpr (OP == ROW_GRAD_PACK || OP == ROW_GRAD_OUT) l2_prefetch(a.psi + rb, N * sizeof(float2));
+    if constexpr (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) {
+      l2_prefetch(a.psi + rb, N * sizeof(float2));
+      l2_prefetch(a.phi + rb, N * sizeof(float2));
+      l2_prefetch(a.reg + rb, N * sizeof(float));
+    }
+  }
 
   // ---- input ----
   if constexpr (T::ifft_in) {
@@ -194,7 +208,6 @@ __global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
   }
 
   // ---- point-wise step in real space (slots of radix RS) ----
-  float2 w[(OP == ROW_GRAD_PACK) ? EPT : 1];
   if constexpr (OP == ROW_IFFT) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RS>(t, j)] = v[j];
@@ -249,15 +262,15 @@ __global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
       a.g_out[rb + x] = cscale(cmulc(v[j], xx), s);
     }
   } else if constexpr (OP == ROW_GRAD_PACK) {
+    // g = conj(exp psi) g1 / max|t|^2: Re g out, Im g stays in v for the
+    // first row FFT; alpha o psi is formed after it from a second read of psi
     const float s = 1.0f / *a.maxt2;
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int x = slot_index<N, RS>(t, j);
-      const float2 p = a.psi[rb + x];
-      const float2 g = cscale(cmulc(v[j], cexpf2(p)), s);
+      const float2 g = cscale(cmulc(v[j], cexpf2(a.psi[rb + x])), s);
       a.reg[rb + x] = g.x;
-      w[j] = make_float2(g.y, 0.f);
-      v[j] = make_float2(a.alpha_re * p.x, a.alpha_im * p.y);
+      v[j] = make_float2(g.y, 0.f);
     }
   } else if constexpr (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) {
     const float beta = *a.beta;
@@ -292,15 +305,22 @@ __global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
   }
 
   // ---- output ----
-  if constexpr (T::fft_out) {
+  if constexpr (OP == ROW_GRAD_PACK) {
+    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) a.aux[rb + slot_index<N, RK>(t, j)] = v[j];
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float2 p = a.psi[rb + slot_index<N, RS>(t, j)];
+      v[j] = make_float2(a.alpha_re * p.x, a.alpha_im * p.y);
+    }
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t, j)] = v[j];
-    if constexpr (OP == ROW_GRAD_PACK) {
-      fft_run<N, FWD>(w, sm, t, a.tw_fwd);
+  } else if constexpr (T::fft_out) {
+    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
-      for (int j = 0; j < EPT; j++) a.aux[rb + slot_index<N, RK>(t, j)] = w[j];
-    }
+    for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t, j)] = v[j];
   }
 
   // ---- reductions ----
@@ -314,9 +334,72 @@ __global__ void __launch_bounds__(row_threads(N)) row_kernel(const PassArgs a) {
 // ---------------------------------------------------------------------------
 // column pass
 // ---------------------------------------------------------------------------
-template <int N, int OP>
-__global__ void __launch_bounds__(col_threads(N)) col_kernel(const PassArgs a) {
-  constexpr int EPT = ept_for(N), TPF = tpf_for(N), C = cols_for(N);
+// C columns of one projection per tile; thread (t, c) = (tid / C, tid % C)
+// holds EPT elements of column c. The arithmetic lives in col_tile(); the two
+// kernels differ only in how a tile reaches it: col_kernel reads the first
+// stage's inputs straight from global memory (one tile per CTA), and
+// col_kernel_pipe is persistent and copies tile k+1 into a second shared
+// buffer with cp.async while tile k is transformed.
+__host__ __device__ constexpr int col_threads(int n, int c) { return c * tpf_for(n); }
+__host__ __device__ constexpr size_t col_smem_bytes(int n, int c) {
+  return (size_t)c * col_tile_rows(n, c) * sizeof(float2);
+}
+__host__ __device__ constexpr size_t colp_smem_bytes(int n, int c) { return 2 * col_smem_bytes(n, c); }
+__host__ __device__ constexpr int col_min_blocks(int threads) { return threads >= 512 ? 1 : threads >= 256 ? 3 : 4; }
+
+// the filter step and the inverse transform of one tile (v holds the forward
+// spectrum of the column in slots of the last forward radix)
+template <int N, int OP, int C, int S2N>
+__device__ __forceinline__ void col_tile_filter(const PassArgs& a, const ColLayout<C>& sm, int t, int col,
+                                                size_t base, float2 (&v)[ept_for(N)], float2 (&s2)[S2N],
+                                                float (&part)[5]) {
+  constexpr int EPT = ept_for(N);
+  constexpr int RK = last_radix<N, FWD>();
+  const size_t ld = (size_t)a.nx;
+  if constexpr (OP == COL_Q) {
+    const float2 qx = __ldg(&a.qx[col]);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
+      if (a.conj_q) q = cconj(q);
+      v[j] = cscale(cmul(v[j], q), a.scale);
+    }
+  } else if constexpr (OP == COL_IOTF) {
+    const float ixv = __ldg(&a.ix[col]) * a.scale;
+#pragma unroll
+    for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], ixv * __ldg(&a.iy[slot_index<N, RK>(t, j)]));
+  } else if constexpr (OP == COL_RESID_IOTF2) {
+    const float ixv = __ldg(&a.ix[col]);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int ky = slot_index<N, RK>(t, j);
+      const float w = ixv * __ldg(&a.iy[ky]);
+      const float2 yh = a.yhat[base + (size_t)ky * ld];
+      const float2 r = make_float2(fmaf(w, v[j].x, -yh.x), fmaf(w, v[j].y, -yh.y));
+      part[0] = fmaf(r.x, r.x, fmaf(r.y, r.y, part[0]));
+      v[j] = cscale(r, w * a.scale);
+    }
+    part[0] *= a.scale;
+  } else if constexpr (OP == COL_PRECOND_REG) {
+    fft_run<N, FWD>(s2, sm, t, a.tw_fwd);
+    const float exv = __ldg(&a.ex[col]);
+    const float u2 = __ldg(&a.u2x[col]);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int ky = slot_index<N, RK>(t, j);
+      const float g2 = -expm1f(-(exv + __ldg(&a.ey[ky])));  // Gamma^2 = 1 - STF
+      const float r2 = u2 + __ldg(&a.u2y[ky]);
+      const float pinv = a.no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f);
+      // Z = Gamma^2 H + i P^-1 S
+      v[j] = make_float2((g2 * v[j].x - pinv * s2[j].y) * a.scale, (g2 * v[j].y + pinv * s2[j].x) * a.scale);
+    }
+  }
+}
+
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+    col_kernel(const PassArgs a) {
+  constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
   extern __shared__ float2 smem[];
@@ -330,81 +413,33 @@ __global__ void __launch_bounds__(col_threads(N)) col_kernel(const PassArgs a) {
   const size_t ld = (size_t)a.nx;
   const ColLayout<C> sm{smem + c};
   float2 v[EPT];
+  float2 s2[(OP == COL_PRECOND_REG) ? EPT : 1];
   float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
   if constexpr (OP == COL_IFFT) {
 #pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = a.in[base + (size_t)slot_index<N, RK>(t, j) * ld];
-#pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], a.scale);
+    for (int j = 0; j < EPT; j++) v[j] = cscale(a.in[base + (size_t)slot_index<N, RK>(t, j) * ld], a.scale);
   } else {
+    if constexpr (OP == COL_PRECOND_REG) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) s2[j] = a.aux_in[base + (size_t)slot_index<N, RS>(t, j) * ld];
+    }
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = a.in[base + (size_t)slot_index<N, RS>(t, j) * ld];
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
-
-    // ---- multiply on the 2-D spectrum (slots of radix RK; ky = slot index) ----
     if constexpr (OP == COL_FFT) {
 #pragma unroll
       for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RK>(t, j) * ld] = v[j];
       return;
-    } else if constexpr (OP == COL_Q) {
-      const float2 qx = __ldg(&a.qx[col]);
-#pragma unroll
-      for (int j = 0; j < EPT; j++) {
-        float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
-        if (a.conj_q) q = cconj(q);
-        v[j] = cscale(cmul(v[j], q), a.scale);
-      }
-    } else if constexpr (OP == COL_IOTF) {
-      const float ixv = __ldg(&a.ix[col]) * a.scale;
-#pragma unroll
-      for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], ixv * __ldg(&a.iy[slot_index<N, RK>(t, j)]));
-    } else if constexpr (OP == COL_RESID_IOTF2) {
-      const float ixv = __ldg(&a.ix[col]);
-#pragma unroll
-      for (int j = 0; j < EPT; j++) {
-        const int ky = slot_index<N, RK>(t, j);
-        const float w = ixv * __ldg(&a.iy[ky]);
-        const float2 yh = a.yhat[base + (size_t)ky * ld];
-        const float2 r = make_float2(fmaf(w, v[j].x, -yh.x), fmaf(w, v[j].y, -yh.y));
-        part[0] = fmaf(r.x, r.x, fmaf(r.y, r.y, part[0]));
-        v[j] = cscale(r, w * a.scale);
-      }
-      part[0] *= a.scale;
-    } else if constexpr (OP == COL_PRECOND_REG) {
-      float2 s[EPT];
-#pragma unroll
-      for (int j = 0; j < EPT; j++) s[j] = a.aux_in[base + (size_t)slot_index<N, RS>(t, j) * ld];
-      fft_run<N, FWD>(s, sm, t, a.tw_fwd);
-      const float exv = __ldg(&a.ex[col]);
-      const float u2 = __ldg(&a.u2x[col]);
-#pragma unroll
-      for (int j = 0; j < EPT; j++) {
-        const int ky = slot_index<N, RK>(t, j);
-        const float g2 = -expm1f(-(exv + __ldg(&a.ey[ky])));  // Gamma^2 = 1 - STF
-        const float r2 = u2 + __ldg(&a.u2y[ky]);
-        const float pinv = a.no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f);
-        // Z = Gamma^2 H + i P^-1 S
-        v[j] = make_float2((g2 * v[j].x - pinv * s[j].y) * a.scale, (g2 * v[j].y + pinv * s[j].x) * a.scale);
-      }
     }
+    col_tile_filter<N, OP, C>(a, sm, t, col, base, v, s2, part);
   }
-
   fft_run<N, INV>(v, sm, t, a.tw_inv);
 #pragma unroll
   for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
-
   if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, smem);
 }
 
-// ---------------------------------------------------------------------------
-// column pass, persistent and software-pipelined
-// ---------------------------------------------------------------------------
-// One CTA per SM walks over column tiles (proj, c0). While tile k is being
-// transformed in one shared-memory buffer, tile k+1 is copied into the other
-// with cp.async (16-byte chunks, one commit group per tile); results leave
-// from registers with plain stores, which drain while the next tile computes.
-// Same arithmetic as col_kernel. Not used for COL_PRECOND_REG (two inputs).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -413,19 +448,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
-__host__ __device__ constexpr size_t colp_smem_bytes(int n) { return 2 * col_smem_bytes(n); }
-// the double-buffered tile must fit the per-CTA shared memory (227 KB)
-__host__ __device__ constexpr bool colp_fits(int n) { return colp_smem_bytes(n) <= 200 * 1024; }
-
-template <int N, int OP>
-__global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassArgs a, int nproj) {
-  constexpr int EPT = ept_for(N), TPF = tpf_for(N), C = cols_for(N);
-  constexpr int NT = col_threads(N);
+// Persistent, double-buffered: the CTA walks tiles blockIdx.x, +gridDim.x, ...
+// The copy of tile k+1 is one cp.async commit group (16-byte chunks); the wait
+// for tile k is cp.async.wait_group 1, which returns once that group landed.
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+    col_kernel_pipe(const PassArgs a, int nproj) {
+  constexpr int EPT = ept_for(N);
+  constexpr int NT = col_threads(N, C);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
   constexpr int CHUNKS = N * C / 2;  // 16-byte chunks per tile
+  constexpr int TILE = C * col_tile_rows(N, C);
   static_assert(CHUNKS % NT == 0, "tile chunks must divide evenly");
-  static_assert(OP != COL_PRECOND_REG, "two-input pass uses col_kernel");
   extern __shared__ float2 smem[];
 
   const int tid = threadIdx.x;
@@ -445,9 +480,9 @@ __global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassA
     if (a.active != nullptr && a.active[proj] == 0) return;
 #pragma unroll
     for (int k = 0; k < CHUNKS / NT; k++) {
-      const int q = tid + k * NT;           // chunk index: row q / (C/2), pair q % (C/2)
+      const int q = tid + k * NT;  // chunk q: row q / (C/2), column pair q % (C/2)
       const int row = q / (C / 2), pr = q % (C / 2);
-      cp_async16(buf + row * C + 2 * pr, a.in + b + (size_t)row * ld + 2 * pr);
+      cp_async16(buf + col_row(row, C) * C + 2 * pr, a.in + b + (size_t)row * ld + 2 * pr);
     }
   };
 
@@ -455,8 +490,8 @@ __global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassA
   if (tile < ntiles) prefetch(tile, smem);
   cp_async_commit();
   for (int k = 0; tile < ntiles; k++, tile += gridDim.x) {
-    float2* cur = smem + (k & 1) * (C * N);
-    float2* nxt = smem + ((k + 1) & 1) * (C * N);
+    float2* cur = smem + (k & 1) * TILE;
+    float2* nxt = smem + ((k + 1) & 1) * TILE;
     const int next = tile + gridDim.x;
     if (next < ntiles) prefetch(next, nxt);
     cp_async_commit();
@@ -472,40 +507,21 @@ __global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassA
     }
     const ColLayout<C> sm{cur + c};
     float2 v[EPT];
+    float2 s2[(OP == COL_PRECOND_REG) ? EPT : 1];
     float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
     if constexpr (OP == COL_IFFT) {
 #pragma unroll
       for (int j = 0; j < EPT; j++) v[j] = cscale(sm[slot_index<N, RK>(t, j)], a.scale);
     } else {
+      if constexpr (OP == COL_PRECOND_REG) {
+#pragma unroll
+        for (int j = 0; j < EPT; j++) s2[j] = a.aux_in[base + (size_t)slot_index<N, RS>(t, j) * ld];
+      }
 #pragma unroll
       for (int j = 0; j < EPT; j++) v[j] = sm[slot_index<N, RS>(t, j)];
       fft_run<N, FWD>(v, sm, t, a.tw_fwd);
-      if constexpr (OP == COL_Q) {
-        const float2 qx = __ldg(&a.qx[col]);
-#pragma unroll
-        for (int j = 0; j < EPT; j++) {
-          float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
-          if (a.conj_q) q = cconj(q);
-          v[j] = cscale(cmul(v[j], q), a.scale);
-        }
-      } else if constexpr (OP == COL_IOTF) {
-        const float ixv = __ldg(&a.ix[col]) * a.scale;
-#pragma unroll
-        for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], ixv * __ldg(&a.iy[slot_index<N, RK>(t, j)]));
-      } else if constexpr (OP == COL_RESID_IOTF2) {
-        const float ixv = __ldg(&a.ix[col]);
-#pragma unroll
-        for (int j = 0; j < EPT; j++) {
-          const int ky = slot_index<N, RK>(t, j);
-          const float w = ixv * __ldg(&a.iy[ky]);
-          const float2 yh = a.yhat[base + (size_t)ky * ld];
-          const float2 r = make_float2(fmaf(w, v[j].x, -yh.x), fmaf(w, v[j].y, -yh.y));
-          part[0] = fmaf(r.x, r.x, fmaf(r.y, r.y, part[0]));
-          v[j] = cscale(r, w * a.scale);
-        }
-        part[0] *= a.scale;
-      }
+      if constexpr (OP != COL_FFT) col_tile_filter<N, OP, C>(a, sm, t, col, base, v, s2, part);
     }
     if constexpr (OP == COL_FFT) {
 #pragma unroll
@@ -527,24 +543,6 @@ __global__ void __launch_bounds__(col_threads(N), 1) col_kernel_pipe(const PassA
 using PassFn = cudaError_t (*)(const PassArgs&, int nproj, cudaStream_t);
 using PrepFn = cudaError_t (*)();
 
-// Dynamic shared memory above 48 KB needs the attribute set once per kernel
-// (done at plan creation, outside any stream capture).
-template <int N, int OP>
-cudaError_t prep_row() {
-  return cudaFuncSetAttribute(row_kernel<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem_bytes(N));
-}
-template <int N, int OP>
-cudaError_t prep_col() {
-  cudaError_t e = cudaFuncSetAttribute(col_kernel<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)col_smem_bytes(N));
-  if constexpr (OP != COL_PRECOND_REG && colp_fits(N)) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(col_kernel_pipe<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)colp_smem_bytes(N));
-  }
-  return e;
-}
-
 // number of SMs of the current device (persistent grids)
 inline int device_sms() {
   static int sms = 0;
@@ -556,6 +554,13 @@ inline int device_sms() {
   return sms;
 }
 
+// Dynamic shared memory above 48 KB needs the attribute set once per kernel
+// (done at plan creation, outside any stream capture).
+template <int N, int OP>
+cudaError_t prep_row() {
+  return cudaFuncSetAttribute(row_kernel<N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem_bytes(N));
+}
+
 // row pass over the ny rows of nproj projections starting at a.proj0
 template <int N, int OP>
 cudaError_t launch_row(const PassArgs& a, int nproj, cudaStream_t s) {
@@ -565,82 +570,103 @@ cudaError_t launch_row(const PassArgs& a, int nproj, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// column pass over the nx columns of nproj projections starting at a.proj0
-template <int N, int OP>
-cudaError_t launch_col(const PassArgs& a, int nproj, cudaStream_t s) {
-  constexpr int C = cols_for(N);
-  const long long ntiles = (long long)nproj * (a.nx / C);
-  if constexpr (OP != COL_PRECOND_REG && colp_fits(N)) {
-    if (ntiles >= 2 * device_sms()) {
-      const int grid = (int)(ntiles < device_sms() ? ntiles : device_sms());
-      col_kernel_pipe<N, OP><<<grid, col_threads(N), colp_smem_bytes(N), s>>>(a, nproj);
-      return cudaGetLastError();
+// column-pass shape variants: tile width C, pipelined or not
+template <int N, int OP, int C, bool PIPE>
+struct ColShape {
+  static int resident;  // CTAs per SM of the pipelined kernel (set by prep)
+  static cudaError_t prep() {
+    if constexpr (PIPE) {
+      cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)colp_smem_bytes(N, C));
+      if (e != cudaSuccess) return e;
+      int r = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_pipe<N, OP, C>, col_threads(N, C),
+                                                        colp_smem_bytes(N, C));
+      resident = r > 0 ? r : 1;
+      return e;
+    } else {
+      return cudaFuncSetAttribute(col_kernel<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem_bytes(N, C));
     }
   }
-  dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
-  col_kernel<N, OP><<<grid, col_threads(N), col_smem_bytes(N), s>>>(a);
-  return cudaGetLastError();
-}
+  static cudaError_t launch(const PassArgs& a, int nproj, cudaStream_t s) {
+    if constexpr (PIPE) {
+      const long long ntiles = (long long)nproj * (a.nx / C);
+      const long long slots = (long long)device_sms() * resident;
+      const int grid = (int)(ntiles < slots ? ntiles : slots);
+      col_kernel_pipe<N, OP, C><<<grid, col_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+    } else {
+      dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
+      col_kernel<N, OP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+    }
+    return cudaGetLastError();
+  }
+};
+template <int N, int OP, int C, bool PIPE>
+int ColShape<N, OP, C, PIPE>::resident = 1;
+
+struct ColVariant {
+  PassFn launch;
+  PrepFn prep;
+  int C;
+  int pipe;
+};
+constexpr int MAX_COL_VARIANTS = 6;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
   int n;
   PassFn row[NUM_ROW_OPS];
-  PassFn col[NUM_COL_OPS];
   PrepFn row_prep[NUM_ROW_OPS];
-  PrepFn col_prep[NUM_COL_OPS];
+  ColVariant colv[NUM_COL_OPS][MAX_COL_VARIANTS];
+  int ncolv[NUM_COL_OPS];
 };
+
+// a shape is offered when its CTA has 64..512 threads and its buffers fit
+template <int N, int C, bool PIPE>
+constexpr bool col_shape_ok() {
+  constexpr int th = col_threads(N, C);
+  constexpr size_t sm = PIPE ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
+  return th >= 16 && th <= 512 && sm <= 200 * 1024 && (!PIPE || (N * C / 2) % th == 0);
+}
+
+template <int N, int OP, int C, bool PIPE>
+void add_col_variant(LengthKernels& k) {
+  if constexpr (col_shape_ok<N, C, PIPE>()) {
+    int& n = k.ncolv[OP];
+    if (n < MAX_COL_VARIANTS) k.colv[OP][n++] = {ColShape<N, OP, C, PIPE>::launch, ColShape<N, OP, C, PIPE>::prep, C, PIPE};
+  }
+}
+
+template <int N, int OP>
+void add_col_op(LengthKernels& k) {
+  // first entry = default before tuning
+  add_col_variant<N, OP, (N >= 1024 ? 8 : 16), true>(k);
+  add_col_variant<N, OP, 16, false>(k);
+  add_col_variant<N, OP, 8, false>(k);
+  add_col_variant<N, OP, 4, false>(k);
+  add_col_variant<N, OP, 4, true>(k);
+  if constexpr (N < 1024) add_col_variant<N, OP, 8, true>(k);
+}
 
 template <int N>
 LengthKernels make_length_kernels() {
   LengthKernels k{};
   k.n = N;
-  k.row[ROW_EXP_FFT] = launch_row<N, ROW_EXP_FFT>;
-  k.row_prep[ROW_EXP_FFT] = prep_row<N, ROW_EXP_FFT>;
-  k.row[ROW_REAL_FFT] = launch_row<N, ROW_REAL_FFT>;
-  k.row_prep[ROW_REAL_FFT] = prep_row<N, ROW_REAL_FFT>;
-  k.row[ROW_FFT] = launch_row<N, ROW_FFT>;
-  k.row_prep[ROW_FFT] = prep_row<N, ROW_FFT>;
-  k.row[ROW_IFFT] = launch_row<N, ROW_IFFT>;
-  k.row_prep[ROW_IFFT] = prep_row<N, ROW_IFFT>;
-  k.row[ROW_MUL_T] = launch_row<N, ROW_MUL_T>;
-  k.row_prep[ROW_MUL_T] = prep_row<N, ROW_MUL_T>;
-  k.row[ROW_INTENSITY] = launch_row<N, ROW_INTENSITY>;
-  k.row_prep[ROW_INTENSITY] = prep_row<N, ROW_INTENSITY>;
-  k.row[ROW_INTENSITY_OUT] = launch_row<N, ROW_INTENSITY_OUT>;
-  k.row_prep[ROW_INTENSITY_OUT] = prep_row<N, ROW_INTENSITY_OUT>;
-  k.row[ROW_REAL_OUT] = launch_row<N, ROW_REAL_OUT>;
-  k.row_prep[ROW_REAL_OUT] = prep_row<N, ROW_REAL_OUT>;
-  k.row[ROW_RESID] = launch_row<N, ROW_RESID>;
-  k.row_prep[ROW_RESID] = prep_row<N, ROW_RESID>;
-  k.row[ROW_COH_RESID] = launch_row<N, ROW_COH_RESID>;
-  k.row_prep[ROW_COH_RESID] = prep_row<N, ROW_COH_RESID>;
-  k.row[ROW_COH_VJP] = launch_row<N, ROW_COH_VJP>;
-  k.row_prep[ROW_COH_VJP] = prep_row<N, ROW_COH_VJP>;
-  k.row[ROW_MUL_V] = launch_row<N, ROW_MUL_V>;
-  k.row_prep[ROW_MUL_V] = prep_row<N, ROW_MUL_V>;
-  k.row[ROW_GRAD_OUT] = launch_row<N, ROW_GRAD_OUT>;
-  k.row_prep[ROW_GRAD_OUT] = prep_row<N, ROW_GRAD_OUT>;
-  k.row[ROW_GRAD_PACK] = launch_row<N, ROW_GRAD_PACK>;
-  k.row_prep[ROW_GRAD_PACK] = prep_row<N, ROW_GRAD_PACK>;
-  k.row[ROW_NESTEROV_FFT] = launch_row<N, ROW_NESTEROV_FFT>;
-  k.row_prep[ROW_NESTEROV_FFT] = prep_row<N, ROW_NESTEROV_FFT>;
-  k.row[ROW_NESTEROV] = launch_row<N, ROW_NESTEROV>;
-  k.row_prep[ROW_NESTEROV] = prep_row<N, ROW_NESTEROV>;
-  k.row[ROW_GRADT] = launch_row<N, ROW_GRADT>;
-  k.row_prep[ROW_GRADT] = prep_row<N, ROW_GRADT>;
-  k.col[COL_Q] = launch_col<N, COL_Q>;
-  k.col_prep[COL_Q] = prep_col<N, COL_Q>;
-  k.col[COL_IOTF] = launch_col<N, COL_IOTF>;
-  k.col_prep[COL_IOTF] = prep_col<N, COL_IOTF>;
-  k.col[COL_RESID_IOTF2] = launch_col<N, COL_RESID_IOTF2>;
-  k.col_prep[COL_RESID_IOTF2] = prep_col<N, COL_RESID_IOTF2>;
-  k.col[COL_PRECOND_REG] = launch_col<N, COL_PRECOND_REG>;
-  k.col_prep[COL_PRECOND_REG] = prep_col<N, COL_PRECOND_REG>;
-  k.col[COL_FFT] = launch_col<N, COL_FFT>;
-  k.col_prep[COL_FFT] = prep_col<N, COL_FFT>;
-  k.col[COL_IFFT] = launch_col<N, COL_IFFT>;
-  k.col_prep[COL_IFFT] = prep_col<N, COL_IFFT>;
+#define PWF_ROW(OP)                  \
+  k.row[OP] = launch_row<N, OP>;     \
+  k.row_prep[OP] = prep_row<N, OP>;
+  PWF_ROW(ROW_EXP_FFT) PWF_ROW(ROW_REAL_FFT) PWF_ROW(ROW_FFT) PWF_ROW(ROW_IFFT) PWF_ROW(ROW_MUL_T)
+  PWF_ROW(ROW_INTENSITY) PWF_ROW(ROW_INTENSITY_OUT) PWF_ROW(ROW_REAL_OUT) PWF_ROW(ROW_RESID)
+  PWF_ROW(ROW_COH_RESID) PWF_ROW(ROW_COH_VJP) PWF_ROW(ROW_MUL_V) PWF_ROW(ROW_GRAD_OUT) PWF_ROW(ROW_GRAD_PACK)
+  PWF_ROW(ROW_NESTEROV_FFT) PWF_ROW(ROW_NESTEROV) PWF_ROW(ROW_GRADT)
+#undef PWF_ROW
+  add_col_op<N, COL_Q>(k);
+  add_col_op<N, COL_IOTF>(k);
+  add_col_op<N, COL_RESID_IOTF2>(k);
+  add_col_op<N, COL_PRECOND_REG>(k);
+  add_col_op<N, COL_FFT>(k);
+  add_col_op<N, COL_IFFT>(k);
   return k;
 }
 

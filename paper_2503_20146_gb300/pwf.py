@@ -20,6 +20,7 @@ _HEADER = os.path.join(os.path.dirname(_PKG), "include", "pwf.h")
 FLAG_NO_PRECOND = 0x1
 FLAG_NO_REG = 0x2
 FLAG_PLAIN = 0x4
+FLAG_NO_TUNE = 0x8
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
           4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE"}
@@ -92,6 +93,7 @@ def load(path: str | None = None):
         "pwf_plan_launch_count": ([_P], ctypes.c_longlong),
         "pwf_profile_iteration": ([_P, _P, _P, _P, i32, _P, _P, _P], i32),
         "pwf_forward_noalloc": ([ctypes.POINTER(pwf_plan_desc), _P, _P, _P], i32),
+        "pwf_plan_describe": ([_P, ctypes.c_char_p, sz], sz),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -282,6 +284,13 @@ def pwf_profile_iteration(plan, y, t, psi, iters: int):
     _check(load().pwf_profile_iteration(plan, _ptr(y), _ptr(t), _ptr(psi), int(iters), ms, names,
                                         ctypes.byref(n)), "pwf_profile_iteration", plan)
     return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
+
+
+def pwf_plan_describe(plan) -> str:
+    n = int(load().pwf_plan_describe(plan, None, 0))
+    buf = ctypes.create_string_buffer(max(n, 1))
+    load().pwf_plan_describe(plan, buf, n)
+    return buf.value.decode()
 
 
 def pwf_status_string(status: int) -> str:
