@@ -233,10 +233,24 @@ __host__ __device__ constexpr int twiddle_len(int n, int dir) { return stage_two
 // shared-memory layouts
 // ---------------------------------------------------------------------------
 // one transform per row; one padding slot per 16 (breaks the stride-R
-// bank pattern of the first stage's writes)
+// bank pattern of the first stage's writes). The TPF threads of one row are
+// the only ones that touch it, so a stage barrier covers just them: a named
+// barrier (id 1 + row) when they span several warps, a warp barrier when the
+// row fits in one warp (NT = threads of the block).
+template <int TPF, int NT>
 struct RowLayout {
   float2* base;
+  int bar;
   __device__ __forceinline__ float2& operator[](int p) const { return base[p + (p >> 4)]; }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (TPF > 32) {
+      asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "n"(TPF) : "memory");
+    } else if constexpr (NT >= 32) {
+      __syncwarp();
+    } else {
+      __syncwarp((1u << NT) - 1u);
+    }
+  }
 };
 __host__ __device__ constexpr int row_smem_len(int n) { return n + n / 16; }
 
@@ -253,6 +267,7 @@ template <int C>
 struct ColLayout {
   float2* base;  // already offset by c
   __device__ __forceinline__ float2& operator[](int p) const { return base[col_row(p, C) * C]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -261,9 +276,10 @@ struct ColLayout {
 // Runs stages [K, S) of the length-N transform with direction DIR on the slot
 // registers v. Before the call, v holds the inputs of stage K in slot order of
 // its radix (for K = 0, the transform's input). After it, v holds the outputs
-// of the last stage in slot order of the last radix. A __syncthreads() is
-// issued before the first shared-memory write and after every write phase, so
-// the caller needs no barrier around it.
+// of the last stage in slot order of the last radix. The layout's barrier
+// (sm.sync(): every thread that shares the buffer) is issued before the first
+// shared-memory write and after every write phase, so the caller needs no
+// barrier around it.
 template <int N, int DIR, int K, class L>
 __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm, int t,
                                            const float2* __restrict__ tw) {
@@ -284,7 +300,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
 #pragma unroll
       for (int r = 0; r < R; r++) v[i * R + r] = sm[b + r * (N / R)];
     }
-    if constexpr (!LAST) __syncthreads();  // reads of this stage precede its writes
+    if constexpr (!LAST) sm.sync();  // reads of this stage precede its writes
 #pragma unroll
     for (int i = 0; i < NB; i++) {
       const int b = t + i * TPF;
@@ -299,7 +315,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
   }
 
   if constexpr (!LAST) {
-    if constexpr (K == 0) __syncthreads();  // earlier readers of the buffer are done
+    if constexpr (K == 0) sm.sync();  // earlier readers of the buffer are done
 #pragma unroll
     for (int i = 0; i < NB; i++) {
       const int b = t + i * TPF;
@@ -308,7 +324,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
 #pragma unroll
       for (int r = 0; r < R; r++) sm[base + r * NS] = v[i * R + r];
     }
-    __syncthreads();
+    sm.sync();
     fft_stages<N, DIR, K + 1, L>(v, sm, t, tw);
   }
 }
