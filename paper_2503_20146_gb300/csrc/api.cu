@@ -1071,6 +1071,21 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
 
 long long pwf_plan_launch_count(const pwf_plan* p) { return p ? p->launches : -1; }
 
+int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
+  if (!p || pass < 0 || pass >= NUM_COL_OPS) return -1;
+  return p->kcol->ncolv[pass];
+}
+
+pwf_status pwf_plan_set_column_shape(pwf_plan* p, int32_t pass, int32_t shape) {
+  if (!p || pass < 0 || pass >= NUM_COL_OPS || shape < 0 || shape >= p->kcol->ncolv[pass]) return PWF_ERR_INVALID_ARG;
+  p->colsel[pass] = shape;
+  if (p->graph) {  // the captured iteration used the previous shapes
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  return PWF_OK;
+}
+
 size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   if (!p) return 0;
   char tmp[512];
@@ -1078,7 +1093,7 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp); op++) {
     const ColVariant& v = p->kcol->colv[op][p->colsel[op]];
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=C%d%s", kColNames[op], v.C, v.pipe ? "p" : "");
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=C%d%s", kColNames[op], v.C, v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   }
   if (buf && len) {
     std::snprintf(buf, len, "%s", tmp);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a
   const int yrow = (int)(row - (long long)proj * a.ny);
   if (a.active != nullptr && a.active[proj] == 0) return;  // uniform per CTA (ny % ROWS == 0)
   const size_t rb = (size_t)row * N;
-  const RowLayout sm{smem + rr * row_smem_len(N)};
+  const RowLayout<TPF, ROWS * TPF> sm{smem + rr * row_smem_len(N), 1 + rr};
   float2 v[EPT];
   float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
@@ -349,8 +349,8 @@ __host__ __device__ constexpr int col_min_blocks(int threads) { return threads >
 
 // the filter step and the inverse transform of one tile (v holds the forward
 // spectrum of the column in slots of the last forward radix)
-template <int N, int OP, int C, int S2N>
-__device__ __forceinline__ void col_tile_filter(const PassArgs& a, const ColLayout<C>& sm, int t, int col,
+template <int N, int OP, int S2N, class L>
+__device__ __forceinline__ void col_tile_filter(const PassArgs& a, const L& sm, int t, int col,
                                                 size_t base, float2 (&v)[ept_for(N)], float2 (&s2)[S2N],
                                                 float (&part)[5]) {
   constexpr int EPT = ept_for(N);
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
       for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RK>(t, j) * ld] = v[j];
       return;
     }
-    col_tile_filter<N, OP, C>(a, sm, t, col, base, v, s2, part);
+    col_tile_filter<N, OP>(a, sm, t, col, base, v, s2, part);
   }
   fft_run<N, INV>(v, sm, t, a.tw_inv);
 #pragma unroll
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 #pragma unroll
       for (int j = 0; j < EPT; j++) v[j] = sm[slot_index<N, RS>(t, j)];
       fft_run<N, FWD>(v, sm, t, a.tw_fwd);
-      if constexpr (OP != COL_FFT) col_tile_filter<N, OP, C>(a, sm, t, col, base, v, s2, part);
+      if constexpr (OP != COL_FFT) col_tile_filter<N, OP>(a, sm, t, col, base, v, s2, part);
     }
     if constexpr (OP == COL_FFT) {
 #pragma unroll
@@ -530,6 +530,120 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
       fft_run<N, INV>(v, sm, t, a.tw_inv);
 #pragma unroll
       for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
+    }
+    if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, cur);
+    __syncthreads();  // cur is refilled by the prefetch of the next-but-one tile
+  }
+  cp_async_wait<0>();
+}
+
+// Transposed tile: the prefetch (8-byte cp.async) stores each of the C columns
+// contiguously in shared memory (column stride S, S = 4 mod 16 slots, so the
+// row-major copy pattern of a warp - C columns x 32/C rows - falls on every
+// bank pair exactly twice), the TPF threads of one column run its transforms
+// exactly like a row pass with a barrier of their own, and the results go
+// back through shared memory so that the global stores are row-major and
+// coalesced. Single-input ops only.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__host__ __device__ constexpr int colt_stride(int n) {
+  return row_smem_len(n) + ((4 - row_smem_len(n) % 16) + 16) % 16;
+}
+__host__ __device__ constexpr size_t colt_smem_bytes(int n, int c) {
+  return 2 * (size_t)c * colt_stride(n) * sizeof(float2);
+}
+
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+    col_kernel_t(const PassArgs a, int nproj) {
+  constexpr int EPT = ept_for(N), TPF = tpf_for(N);
+  constexpr int NT = col_threads(N, C);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  constexpr int S = colt_stride(N);
+  constexpr int TILE = C * S;
+  constexpr int ELEMS = N * C;
+  static_assert(ELEMS % NT == 0, "tile elements must divide evenly");
+  static_assert(OP != COL_PRECOND_REG, "two-input pass uses the other shapes");
+  extern __shared__ float2 smem[];
+
+  const int tid = threadIdx.x;
+  const int c = tid / TPF, t = tid % TPF;      // compute mapping: one column per TPF threads
+  const int tiles_per_proj = a.nx / C;
+  const int ntiles = nproj * tiles_per_proj;
+  const size_t ld = (size_t)a.nx;
+  auto at = [](float2* buf, int col, int p) -> float2& { return buf[col * S + p + (p >> 4)]; };
+
+  auto tile_base = [&](int tile, int& proj, int& col0) -> size_t {
+    proj = a.proj0 + tile / tiles_per_proj;
+    col0 = (tile % tiles_per_proj) * C;
+    return (size_t)proj * a.ny * a.nx + col0;
+  };
+  auto prefetch = [&](int tile, float2* buf) {
+    int proj, col0;
+    const size_t b = tile_base(tile, proj, col0);
+    if (a.active != nullptr && a.active[proj] == 0) return;
+#pragma unroll 8
+    for (int k = 0; k < ELEMS / NT; k++) {
+      const int q = tid + k * NT;  // row-major over the tile: row q / C, column q % C
+      const int row = q / C, cc = q % C;
+      cp_async8(&at(buf, cc, row), a.in + b + (size_t)row * ld + cc);
+    }
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, smem);
+  cp_async_commit();
+  for (int k = 0; tile < ntiles; k++, tile += gridDim.x) {
+    float2* cur = smem + (k & 1) * TILE;
+    float2* nxt = smem + ((k + 1) & 1) * TILE;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    int proj, col0;
+    const size_t tb = tile_base(tile, proj, col0);
+    if (a.active != nullptr && a.active[proj] == 0) {
+      __syncthreads();
+      continue;
+    }
+    const int col = col0 + c;
+    const size_t base = tb + c;
+    const RowLayout<TPF, NT> sm{cur + c * S, 1 + c};
+    float2 v[EPT];
+    float2 s2[1];
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int RO;  // slot radix of the results
+    if constexpr (OP == COL_IFFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) v[j] = cscale(sm[slot_index<N, RK>(t, j)], a.scale);
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) v[j] = sm[slot_index<N, RS>(t, j)];
+      fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+      if constexpr (OP != COL_FFT) col_tile_filter<N, OP>(a, sm, t, col, base, v, s2, part);
+    }
+    if constexpr (OP != COL_FFT) fft_run<N, INV>(v, sm, t, a.tw_inv);
+    // results back into this column's slots (natural order), then row-major stores
+    sm.sync();
+    if constexpr (OP == COL_FFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) sm[slot_index<N, RK>(t, j)] = v[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) sm[slot_index<N, RS>(t, j)] = v[j];
+    }
+    (void)RO;
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < ELEMS / NT; kk++) {
+      const int q = tid + kk * NT;
+      const int row = q / C, cc = q % C;
+      a.out[tb + (size_t)row * ld + cc] = at(cur, cc, row);
     }
     if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, cur);
     __syncthreads();  // cur is refilled by the prefetch of the next-but-one tile
@@ -571,11 +685,20 @@ cudaError_t launch_row(const PassArgs& a, int nproj, cudaStream_t s) {
 }
 
 // column-pass shape variants: tile width C, pipelined or not
-template <int N, int OP, int C, bool PIPE>
+template <int N, int OP, int C, int PIPE>
 struct ColShape {
-  static int resident;  // CTAs per SM of the pipelined kernel (set by prep)
+  static int resident;  // CTAs per SM of the persistent kernels (set by prep)
   static cudaError_t prep() {
-    if constexpr (PIPE) {
+    if constexpr (PIPE == 2) {
+      cudaError_t e = cudaFuncSetAttribute(col_kernel_t<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)colt_smem_bytes(N, C));
+      if (e != cudaSuccess) return e;
+      int r = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_t<N, OP, C>, col_threads(N, C),
+                                                        colt_smem_bytes(N, C));
+      resident = r > 0 ? r : 1;
+      return e;
+    } else if constexpr (PIPE == 1) {
       cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)colp_smem_bytes(N, C));
       if (e != cudaSuccess) return e;
@@ -594,7 +717,10 @@ struct ColShape {
       const long long ntiles = (long long)nproj * (a.nx / C);
       const long long slots = (long long)device_sms() * resident;
       const int grid = (int)(ntiles < slots ? ntiles : slots);
-      col_kernel_pipe<N, OP, C><<<grid, col_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+      if constexpr (PIPE == 2)
+        col_kernel_t<N, OP, C><<<grid, col_threads(N, C), colt_smem_bytes(N, C), s>>>(a, nproj);
+      else
+        col_kernel_pipe<N, OP, C><<<grid, col_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
     } else {
       dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
       col_kernel<N, OP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
@@ -602,7 +728,7 @@ struct ColShape {
     return cudaGetLastError();
   }
 };
-template <int N, int OP, int C, bool PIPE>
+template <int N, int OP, int C, int PIPE>
 int ColShape<N, OP, C, PIPE>::resident = 1;
 
 struct ColVariant {
@@ -611,7 +737,7 @@ struct ColVariant {
   int C;
   int pipe;
 };
-constexpr int MAX_COL_VARIANTS = 6;
+constexpr int MAX_COL_VARIANTS = 8;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
@@ -622,17 +748,18 @@ struct LengthKernels {
   int ncolv[NUM_COL_OPS];
 };
 
-// a shape is offered when its CTA has 64..512 threads and its buffers fit
-template <int N, int C, bool PIPE>
+// a shape is offered when its CTA has 16..512 threads and its buffers fit
+template <int N, int OP, int C, int PIPE>
 constexpr bool col_shape_ok() {
   constexpr int th = col_threads(N, C);
-  constexpr size_t sm = PIPE ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
-  return th >= 16 && th <= 512 && sm <= 200 * 1024 && (!PIPE || (N * C / 2) % th == 0);
+  constexpr size_t sm = PIPE == 2 ? colt_smem_bytes(N, C) : PIPE == 1 ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
+  return th >= 16 && th <= 512 && sm <= 200 * 1024 && (PIPE != 1 || (N * C / 2) % th == 0) &&
+         (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8));
 }
 
-template <int N, int OP, int C, bool PIPE>
+template <int N, int OP, int C, int PIPE>
 void add_col_variant(LengthKernels& k) {
-  if constexpr (col_shape_ok<N, C, PIPE>()) {
+  if constexpr (col_shape_ok<N, OP, C, PIPE>()) {
     int& n = k.ncolv[OP];
     if (n < MAX_COL_VARIANTS) k.colv[OP][n++] = {ColShape<N, OP, C, PIPE>::launch, ColShape<N, OP, C, PIPE>::prep, C, PIPE};
   }
@@ -641,12 +768,14 @@ void add_col_variant(LengthKernels& k) {
 template <int N, int OP>
 void add_col_op(LengthKernels& k) {
   // first entry = default before tuning
-  add_col_variant<N, OP, (N >= 1024 ? 8 : 16), true>(k);
-  add_col_variant<N, OP, 16, false>(k);
-  add_col_variant<N, OP, 8, false>(k);
-  add_col_variant<N, OP, 4, false>(k);
-  add_col_variant<N, OP, 4, true>(k);
-  if constexpr (N < 1024) add_col_variant<N, OP, 8, true>(k);
+  add_col_variant<N, OP, (N >= 1024 ? 8 : 16), 1>(k);
+  add_col_variant<N, OP, 16, 0>(k);
+  add_col_variant<N, OP, 8, 0>(k);
+  add_col_variant<N, OP, 4, 0>(k);
+  add_col_variant<N, OP, 4, 1>(k);
+  if constexpr (N < 1024) add_col_variant<N, OP, 8, 1>(k);
+  add_col_variant<N, OP, 8, 2>(k);
+  add_col_variant<N, OP, 4, 2>(k);
 }
 
 template <int N>

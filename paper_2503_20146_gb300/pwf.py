@@ -94,6 +94,8 @@ def load(path: str | None = None):
         "pwf_profile_iteration": ([_P, _P, _P, _P, i32, _P, _P, _P], i32),
         "pwf_forward_noalloc": ([ctypes.POINTER(pwf_plan_desc), _P, _P, _P], i32),
         "pwf_plan_describe": ([_P, ctypes.c_char_p, sz], sz),
+        "pwf_plan_column_shapes": ([_P, i32], i32),
+        "pwf_plan_set_column_shape": ([_P, i32, i32], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +293,14 @@ def pwf_plan_describe(plan) -> str:
     buf = ctypes.create_string_buffer(max(n, 1))
     load().pwf_plan_describe(plan, buf, n)
     return buf.value.decode()
+
+
+def pwf_plan_column_shapes(plan, pass_index: int) -> int:
+    return int(load().pwf_plan_column_shapes(plan, int(pass_index)))
+
+
+def pwf_plan_set_column_shape(plan, pass_index: int, shape: int):
+    _check(load().pwf_plan_set_column_shape(plan, int(pass_index), int(shape)), "pwf_plan_set_column_shape", plan)
 
 
 def pwf_status_string(status: int) -> str:

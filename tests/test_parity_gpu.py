@@ -272,6 +272,38 @@ def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
 
 
 # ----------------------------------------------------------------------------
+# every column-pass shape the tuner may choose, forced one at a time
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nx,batch", [(1024, 256, 6), (512, 128, 8), (128, 96, 4), (2048, 64, 2)],
+                         ids=["1024x256", "512x128", "128x96", "2048x64"])
+def test_every_column_shape_matches_oracle(pwf, ny, nx, batch):
+    w = W2
+    geom = geometry(w, ny, nx)
+    psi, t = blob_batch(w, batch, ny, nx)
+    psi, t = to_c64(psi), to_c64(t)
+    y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(6).standard_normal((batch, ny, nx)), 0, None))
+    P64, T64 = psi.astype(np.complex128), t.astype(np.complex128)
+    b = batch - 1
+    f_ref = O.PhysicalModel(P64[b], T64, geom)[0]
+    g_ref, _ = O.gradient(P64[b], T64, y[b].astype(np.float64), geom)
+    ref3 = O.pwf(y[b].astype(np.float64), T64, geom, 2)
+    with plan_for(pwf, geom, batch) as plan:
+        nshape = max(pwf.pwf_plan_column_shapes(plan.handle, op) for op in range(6))
+        assert nshape >= 3
+        for k in range(nshape):
+            for op in range(6):
+                n_op = pwf.pwf_plan_column_shapes(plan.handle, op)
+                pwf.pwf_plan_set_column_shape(plan.handle, op, min(k, n_op - 1))
+            f = plan.forward(dev(psi), dev(t)).cpu().numpy()
+            g, _ = plan.gradient(dev(psi), dev(t), dev(y))
+            p = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+            plan.solve(dev(y), dev(t), p, 2)
+            assert rel_l2(f[b], f_ref) <= FWD_TOL, (k, pwf.pwf_plan_describe(plan.handle))
+            assert rel_l2(g.cpu().numpy()[b], g_ref) <= GRAD_TOL, (k, pwf.pwf_plan_describe(plan.handle))
+            assert phase_rms(p.cpu().numpy()[b], ref3.psi) <= PHASE_TOL, (k, pwf.pwf_plan_describe(plan.handle))
+
+
+# ----------------------------------------------------------------------------
 # full-size tomographic series (180 x 1024^2), sampled projections
 # ----------------------------------------------------------------------------
 def tomo_inputs(n_angles=180, n=1024):
