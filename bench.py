@@ -158,7 +158,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload synthesis (seeded; on the GPU for speed)
 # ----------------------------------------------------------------------------
-def make_workload(P, S, w, batch, device):
+def make_workload(P, S, w, batch, device, rank=0, world=1):
+    """Rank r of `world` takes every world-th angle of a world*batch-angle series
+    (weak scaling: each rank solves its own batch of distinct projections)."""
     import numpy as np
     import torch
     n = w.ny
@@ -167,7 +169,7 @@ def make_workload(P, S, w, batch, device):
         xd, yd = S.detector_grid(n, n, xp=torch)
         xd, yd = xd.to(device), yd.to(device)
         psi_true = torch.empty((batch, n, n), dtype=torch.complex64, device=device)
-        for i, ang in enumerate(S.tomo_angles(batch)):
+        for i, ang in enumerate(S.tomo_angles(batch * world)[rank::world]):
             re, im = S.ellipsoid_projection(ph, float(ang), xd, yd, w.wavelength_m)
             psi_true[i] = torch.complex(re, im).to(torch.complex64)
     else:
@@ -177,9 +179,10 @@ def make_workload(P, S, w, batch, device):
     return psi_true, t
 
 
-def plan_desc(P, w, batch, flags=0):
+def plan_desc(P, w, batch, flags=0, n_modes=None):
     return P.PlanDesc(batch, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
-                      w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags)
+                      w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags,
+                      w.n_modes if n_modes is None else n_modes, w.mode_sigma_px)
 
 
 def source_hash():
@@ -294,7 +297,7 @@ def main():
     batch = args.batch or w.batch
     mpx_iter = batch * w.ny * w.nx / 1e6
 
-    psi_true, t = make_workload(P, S, w, batch, dev)
+    psi_true, t = make_workload(P, S, w, batch, dev, rank, world)
     plan = P.Plan(plan_desc(P, w, batch))
     f = plan.forward(psi_true, t)
     gen = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config + rank)
@@ -397,6 +400,26 @@ def main():
                          "d2h_bytes_per_step": int(psi.numel() * 8),
                          "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers"}
         del y_h, psi_h
+
+        # the same series with partial coherence as 9 tilted source modes
+        if w.name == "tomo180x1024_iotf":
+            wk = S.WORKLOADS["tomo180x1024_k9"]
+            mplan = P.Plan(plan_desc(P, wk, batch))
+            pm = torch.zeros_like(psi)
+            mplan.solve(y, t, pm, 3, read_back=False)
+            torch.cuda.synchronize()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            msteps = 5
+            m0.record(stream)
+            pm.zero_()
+            mplan.solve(y, t, pm, msteps, read_back=False)
+            m1.record(stream)
+            torch.cuda.synchronize()
+            mms = m0.elapsed_time(m1)
+            extras["modal_k9"] = {"value": mpx_iter * msteps / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / msteps,
+                                  "workload": wk.name, "steps": msteps}
+            mplan.close()
+            del pm
 
         # FP64 oracle on the host cores, bounded sample
         dt, work = oracle_sample(w, 1, 3)

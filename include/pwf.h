@@ -71,6 +71,17 @@ typedef struct {
   double eta;        /* step size of Algorithm S1 */
   uint32_t flags;    /* PWF_FLAG_* */
   void* stream;      /* cudaStream_t */
+  /* Source-mode variant of the partial-coherence model (not the paper's form;
+   * 0 or 1 = the paper's IOTF form). n_modes = 9 or 25: the IPSF convolution of
+   * Eq. (1) is replaced by the intensities of K mutually incoherent tilted
+   * plane-wave modes summed with weights: f = sum_j w_j |P2{t P1{x s_j}}|^2,
+   * s_j = exp(i 2 pi (mx_j x / nx + my_j y / ny)), nodes and weights of the
+   * tensor Gauss-Hermite rule (3 or 5 points per axis) of a Gaussian source
+   * whose walk-off over L1 + L2 has std mode_sigma_px pixels at the detector;
+   * tilts rounded to whole frequency bins. x_coh/y_coh still set the
+   * regularization window Gamma^2 (Eqs. (14)-(15)). */
+  int32_t n_modes;
+  double mode_sigma_px;
 } pwf_plan_desc;
 
 /* Creates a plan. Unless PWF_FLAG_NO_TUNE is set, the plan also times every
@@ -146,6 +157,23 @@ pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_h
  * given the call synchronises. psi is updated in place. */
 pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
                      double corr_tol, int32_t* iters_host, double* loss_host);
+
+/* Groups: batches of mixed sizes. One plan per size class (each with its own
+ * sizes, batch, coherence model and tuned column shapes) joined in a group and
+ * solved together: pwf_group_solve runs Algorithm S1 on every class, one CUDA
+ * graph launch per iteration, the graph forking one branch per class so the
+ * classes' passes run concurrently. y, t, psi: arrays of n_plans device
+ * pointers, in the order of `plans` (psi updated in place, as pwf_solve).
+ * stream: cudaStream_t all work is ordered on (NULL = legacy default stream).
+ * A plan may belong to one group at a time and must not be used on its own
+ * while the group's solve runs. pwf_group_read reads class `index`'s loss and
+ * iteration counts (HOST arrays of that plan's batch; synchronises). */
+typedef struct pwf_group pwf_group;
+pwf_status pwf_group_create(pwf_plan* const* plans, int32_t n_plans, pwf_group** out);
+pwf_status pwf_group_destroy(pwf_group* group);
+pwf_status pwf_group_solve(pwf_group* group, void* stream, const float* const* y, const void* const* t,
+                           void* const* psi, int32_t max_iter, double corr_tol);
+pwf_status pwf_group_read(pwf_group* group, int32_t index, double* loss_host, int32_t* iters_host);
 
 /* Checkpoint: pwf_state_bytes gives the size of a host buffer that holds the
  * state (phi and the counters); save/load copy it. Loading into a state of a

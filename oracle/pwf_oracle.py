@@ -434,3 +434,20 @@ def modal_pwf(y, t, geom: Geometry, modes, max_iter: int, corr_tol=None) -> PWFR
         if corr_tol is not None and c > corr_tol:
             break
     return PWFResult(psi, it, losses, corrs)
+
+
+def modal_forward_vjp(psi, t, grad_f, geom: Geometry, modes):
+    """VJP of the modal f for a real cotangent grad_f, convention dL/dRe + i dL/dIm:
+    grad_psi = 2 sum_j w_j conj(x s_j) P1^H{conj(t) P2^H{v_j grad_f}} and
+    grad_t   = 2 sum_j w_j conj(P1{x s_j}) P2^H{v_j grad_f} (same derivation as R7)."""
+    x = np.exp(psi)
+    gp = np.zeros(psi.shape, complex)
+    gt = np.zeros(psi.shape, complex)
+    for mx, my, w in modes:
+        s = mode_wave(geom, mx, my)
+        u1 = FreePropagation(x * s, geom, geom.L1)
+        v = FreePropagation(t * u1, geom, geom.L2)
+        g2 = FreePropagation(v * grad_f, geom, -geom.L2)
+        gt += 2.0 * w * np.conj(u1) * g2
+        gp += 2.0 * w * np.conj(x * s) * FreePropagation(np.conj(t) * g2, geom, -geom.L1)
+    return gp, gt

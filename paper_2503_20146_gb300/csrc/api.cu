@@ -249,6 +249,12 @@ struct AxisTables {
   float* iotf = nullptr;
   float* u2 = nullptr;   // squared frequency, cycles per pixel
   float* stf = nullptr;  // pi gamma u^2 coh^2
+  float2* cis = nullptr; // exp(2 pi i k / n)
+};
+
+struct Mode {
+  int mx, my;
+  float w;
 };
 
 struct pwf_state {
@@ -268,8 +274,15 @@ struct pwf_plan {
   const LengthKernels* krow = nullptr;  // length nx
   const LengthKernels* kcol = nullptr;  // length ny
   int colsel[NUM_COL_OPS] = {0, 0, 0, 0, 0, 0};  // chosen column-pass shape per op
+  float coltime[NUM_COL_OPS][MAX_COL_VARIANTS] = {};  // tuning times (ms per launch)
   AxisTables ax, ay;
   bool coherent = false;
+  // source-mode variant
+  std::vector<Mode> modes;   // empty: the paper's IOTF form
+  float2* M = nullptr;       // per-mode pass buffer
+  float2* ACC = nullptr;     // sum over modes of the back-propagated row spectra
+  float* IBUF = nullptr;     // summed intensity, then the residual
+  float2* VSTACK = nullptr;  // detector fields of all modes (allocated on first use)
   // workspace
   float2* X = nullptr;
   float2* V = nullptr;
@@ -367,7 +380,7 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
         }
     }
   }
-  std::vector<float2> q1(n), q2(n);
+  std::vector<float2> q1(n), q2(n), cs(n);
   std::vector<float> io(n), u2(n), st(n);
   for (int k = 0; k < n; k++) {
     const double f = fftfreq(k, n);  // cycles per pixel
@@ -379,12 +392,14 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
     io[k] = (float)std::exp(-0.5 * M_PI * u * u * coh * coh);
     u2[k] = (float)(f * f);
     st[k] = (float)(M_PI * d.gamma * u * u * coh * coh);
+    cs[k] = make_float2((float)std::cos(2.0 * M_PI * k / n), (float)std::sin(2.0 * M_PI * k / n));
   }
   pwf_status r;
   if ((r = dalloc(p, &A.tw_fwd, tlf)) || (r = dalloc(p, &A.tw_inv, tli)) || (r = dalloc(p, &A.q1, n)) ||
       (r = dalloc(p, &A.q2, n)) || (r = dalloc(p, &A.iotf, n)) || (r = dalloc(p, &A.u2, n)) ||
-      (r = dalloc(p, &A.stf, n)))
+      (r = dalloc(p, &A.stf, n)) || (r = dalloc(p, &A.cis, n)))
     return r;
+  PWF_CUDA(p, cudaMemcpy(A.cis, cs.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.tw_fwd, twf.data(), tlf * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.tw_inv, twi.data(), tli * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.q1, q1.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
@@ -414,13 +429,14 @@ PassArgs base_args(pwf_plan* p) {
   a.alpha_im = no_reg ? 0.f : (float)p->d.alpha_im;
   a.no_precond = (p->d.flags & PWF_FLAG_NO_PRECOND) ? 1 : 0;
   a.gscale = 1.0f;
+  a.mode_w = 1.0f;
   return a;
 }
 
 const char* const kRowNames[NUM_ROW_OPS] = {
     "row_exp_fft", "row_real_fft", "row_fft", "row_ifft", "row_mul_t", "row_intensity", "row_intensity_out",
     "row_real_out", "row_resid", "row_coh_resid", "row_coh_vjp", "row_mul_v", "row_grad_out", "row_grad_pack",
-    "row_nesterov_fft", "row_nesterov", "row_gradt"};
+    "row_nesterov_fft", "row_nesterov", "row_gradt", "row_mode_int", "row_mode_vg"};
 const char* const kColNames[NUM_COL_OPS] = {"col_q", "col_iotf", "col_resid_iotf2", "col_precond_reg", "col_fft",
                                             "col_ifft"};
 
@@ -531,13 +547,163 @@ pwf_status fused_backprop(pwf_plan* p, PassArgs a, const float2* t, bool gradt, 
   return PWF_OK;
 }
 
+// Tensor Gauss-Hermite modes of a Gaussian source (standard normal rule, k1 =
+// 3 or 5 points per axis); node n walks the pattern by sigma n pixels at the
+// detector: tilt sigma n p / (lambda (L1 + L2)) cycles/m = that x N p bins.
+std::vector<Mode> source_modes(const pwf_plan_desc& d) {
+  const int k1 = d.n_modes == 25 ? 5 : 3;
+  double nodes[5], weights[5];
+  if (k1 == 3) {
+    const double r3 = std::sqrt(3.0);
+    const double nn[3] = {-r3, 0.0, r3}, ww[3] = {1.0 / 6, 2.0 / 3, 1.0 / 6};
+    for (int i = 0; i < 3; i++) nodes[i] = nn[i], weights[i] = ww[i];
+  } else {
+    const double a = std::sqrt(5.0 - std::sqrt(10.0)), b = std::sqrt(5.0 + std::sqrt(10.0));
+    const double wa = (7.0 + 2.0 * std::sqrt(10.0)) / 60.0, wb = (7.0 - 2.0 * std::sqrt(10.0)) / 60.0;
+    const double nn[5] = {-b, -a, 0.0, a, b}, ww[5] = {wb, wa, 8.0 / 15, wa, wb};
+    for (int i = 0; i < 5; i++) nodes[i] = nn[i], weights[i] = ww[i];
+  }
+  const double z = d.wavelength_m * (d.L1_m + d.L2_m);
+  std::vector<Mode> m;
+  for (int iy = 0; iy < k1; iy++)
+    for (int ix = 0; ix < k1; ix++) {
+      const double sx = d.mode_sigma_px * nodes[ix] * d.pixel_m, sy = d.mode_sigma_px * nodes[iy] * d.pixel_m;
+      Mode md;
+      md.mx = z > 0 ? (int)std::lrint(sx / z * d.nx * d.pixel_m) : 0;
+      md.my = z > 0 ? (int)std::lrint(sy / z * d.ny * d.pixel_m) : 0;
+      md.w = (float)(weights[ix] * weights[iy]);
+      m.push_back(md);
+    }
+  return m;
+}
+
+// e = y - I; loss += e^2 per projection; I <- -e (= f - y)
+__global__ void k_modal_resid(float* I, const float* __restrict__ y, size_t per_proj, double* acc) {
+  const int proj = blockIdx.y;
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_proj; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)proj * per_proj + i;
+    const float e = y[o] - I[o];
+    s = fmaf(e, e, s);
+    I[o] = -e;
+  }
+  double d = s;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&acc[(size_t)proj * NACC + ACC_LOSS], d);
+}
+
+cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumulate, int nproj) {
+  a.tw_fwd = p->ay.tw_fwd;
+  a.tw_inv = p->ay.tw_inv;
+  a.qx = p->ax.q1;
+  a.qy = p->ay.q1;
+  a.cis_y = p->ay.cis;
+  a.mode_mx = md.mx;
+  a.mode_my = md.my;
+  a.mode_w = md.w;
+  a.accumulate = accumulate;
+  return enqueue(p, mop == CM_FWD ? "col_mode_fwd" : "col_mode_back",
+                 [&] { return p->kcol->colmode[mop](a, nproj, p->stream); });
+}
+
+pwf_status ensure_vstack(pwf_plan* p) {
+  if (p->VSTACK) return PWF_OK;
+  return dalloc(p, &p->VSTACK, p->modes.size() * (size_t)p->d.batch * p->d.ny * p->d.nx);
+}
+
+// X holds F_row{exp psi}. For every mode: propagate, store v_j (if vstack),
+// and accumulate I = sum_j w_j |v_j|^2 into `intensity`.
+pwf_status modal_forward(pwf_plan* p, PassArgs a, const float2* t, float* intensity, bool store_v) {
+  const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
+  for (size_t j = 0; j < p->modes.size(); j++) {
+    const Mode& md = p->modes[j];
+    PassArgs b = a;
+    b.in = p->X;
+    b.out = p->M;
+    LAUNCH(p, colmode(p, CM_FWD, b, md, 0, a.B));  // tilt, P1
+    b.in = p->M;
+    b.t = t;
+    b.conj_t = 0;
+    b.u1 = nullptr;
+    LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
+    LAUNCH(p, col_q(p, b, 2, 0, a.B));              // P2
+    b.v = store_v ? p->VSTACK + j * n : nullptr;
+    b.f_out = intensity;
+    b.mode_w = md.w;
+    b.accumulate = j > 0;
+    LAUNCH(p, row(p, ROW_MODE_INT, b, a.B));
+  }
+  return PWF_OK;
+}
+
+// G (real, f - y or dL/df) in `G`; back-propagate every stored mode and
+// accumulate sum_j w_j F_row{conj(s_j) P1^H{conj(t) P2^H{v_j G}}} into ACC.
+pwf_status modal_backward(pwf_plan* p, PassArgs a, const float2* t, const float* G) {
+  const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
+  for (size_t j = 0; j < p->modes.size(); j++) {
+    const Mode& md = p->modes[j];
+    PassArgs b = a;
+    b.v = p->VSTACK + j * n;
+    b.y = G;
+    b.out = p->M;
+    LAUNCH(p, row(p, ROW_MODE_VG, b, a.B));
+    b.in = p->M;
+    LAUNCH(p, col_q(p, b, 2, 1, a.B));              // P2^H
+    b.t = t;
+    b.conj_t = 1;
+    LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
+    b.out = p->ACC;
+    LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, a.B));  // P1^H, untilt, accumulate
+  }
+  return PWF_OK;
+}
+
+pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
+  (void)active;
+  const size_t per = (size_t)p->d.ny * p->d.nx;
+  dim3 grid((unsigned)((per + 255) / 256 > 64 ? 64 : (per + 255) / 256), (unsigned)p->d.batch);
+  return enqueue(p, "modal_resid", [&] {
+           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc);
+           return cudaGetLastError();
+         }) == cudaSuccess
+             ? PWF_OK
+             : cuda_fail(p, cudaGetLastError(), "k_modal_resid");
+}
+
 // one fused iteration (or the body of pwf_step): X must hold F_row{exp psi}
 pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
                            bool next_fft, double corr_tol) {
   PassArgs a = base_args(p);
   a.active = st->active;
   a.beta = &st->it->beta;
-  pwf_status r = fused_to_detector(p, a, psi, t, nullptr, false, a.B);
+  pwf_status r;
+  if (!p->modes.empty()) {
+    // source-mode variant: forward per mode (v_j kept), residual, adjoint per mode.
+    // The mode fields were allocated by the caller, outside any stream capture.
+    if (!p->VSTACK) return fail(p, PWF_ERR_STATE, "mode field stack not allocated");
+    if ((r = modal_forward(p, a, t, p->IBUF, true)) ||
+        (r = modal_resid(p, y, st->active)) || (r = modal_backward(p, a, t, p->IBUF)))
+      return r;
+    a.in = p->ACC;
+    a.out = p->X;
+    a.psi = psi;
+    a.reg = p->REG;
+    a.aux = p->S;
+    LAUNCH(p, row(p, ROW_GRAD_PACK, a, a.B));
+    a.in = p->X;
+    a.aux_in = p->S;
+    LAUNCH(p, col(p, COL_PRECOND_REG, a, a.B));
+    a.psi_out = psi;
+    a.phi = st->phi;
+    LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, a.B));
+    LAUNCH(p, enqueue(p, "finalize", [&] {
+      k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it,
+                                           corr_tol);
+      return cudaGetLastError();
+    }));
+    return PWF_OK;
+  }
+  r = fused_to_detector(p, a, psi, t, nullptr, false, a.B);
   if (r) return r;
   a.in = p->X;
   a.out = p->X;
@@ -688,6 +854,7 @@ pwf_status tune_columns(pwf_plan* p) {
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      p->coltime[op][v] = ms / 2.0f;
       if (err == cudaSuccess && ms < best) {
         best = ms;
         p->colsel[op] = v;
@@ -739,6 +906,9 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
       (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE)))
     return PWF_ERR_INVALID_ARG;
+  if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
+    return PWF_ERR_INVALID_ARG;
+  if (d.n_modes > 1 && (d.flags & PWF_FLAG_PLAIN)) return PWF_ERR_UNSUPPORTED;  // baseline is the paper's form
   if (!size_ok(d.ny) || !size_ok(d.nx)) return PWF_ERR_UNSUPPORTED;
   // evanescent bins and the separable-propagator bound, in double precision
   {
@@ -756,17 +926,26 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   p->krow = kernels_for_length(d.nx);
   p->kcol = kernels_for_length(d.ny);
   p->coherent = (d.xcoh_m == 0.0 && d.ycoh_m == 0.0);
+  if (d.n_modes > 1) p->modes = source_modes(d);
   const size_t n = (size_t)d.batch * d.ny * d.nx;
   pwf_status r;
   if ((r = build_axis(p, p->ax, d.nx, d.pixel_m, d.xcoh_m)) || (r = build_axis(p, p->ay, d.ny, d.pixel_m, d.ycoh_m)) ||
       (r = dalloc(p, &p->X, n)) || (r = dalloc(p, &p->S, n)) || (r = dalloc(p, &p->REG, n)) ||
       (r = dalloc(p, &p->V, n)) || (r = dalloc(p, &p->YH, n)) ||
-      (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1))) {
+      (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1)) ||
+      (!p->modes.empty() && ((r = dalloc(p, &p->M, n)) || (r = dalloc(p, &p->ACC, n)) ||
+                             (r = dalloc(p, &p->IBUF, n))))) {
     pwf_plan_destroy(p);
     return r;
   }
   for (int op = 0; op < NUM_ROW_OPS; op++)
     if (p->krow->row_prep[op]() != cudaSuccess) {
+      cudaGetLastError();
+      pwf_plan_destroy(p);
+      return PWF_ERR_CUDA;
+    }
+  for (int m = 0; m < 2; m++)
+    if (p->kcol->colmode_prep[m]() != cudaSuccess) {
       cudaGetLastError();
       pwf_plan_destroy(p);
       return PWF_ERR_CUDA;
@@ -816,6 +995,12 @@ pwf_status pwf_forward(pwf_plan* p, const void* psi, const void* t, float* f) {
   if (r) return r;
   if (!psi || !t || !f) return PWF_ERR_INVALID_ARG;
   PassArgs a = base_args(p);
+  if (!p->modes.empty()) {
+    a.psi = (const float2*)psi;
+    a.out = p->X;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    return modal_forward(p, a, (const float2*)t, f, false);
+  }
   if ((r = fused_to_detector(p, a, (const float2*)psi, (const float2*)t, nullptr, true, a.B))) return r;
   a.in = p->X;
   a.out = p->X;
@@ -839,6 +1024,24 @@ pwf_status pwf_gradient(pwf_plan* p, const void* psi, const void* t, const float
   if ((r = compute_maxt2(p, (const float2*)t))) return r;
   PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
   PassArgs a = base_args(p);
+  if (!p->modes.empty()) {
+    a.psi = P;
+    a.out = p->X;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    if ((r = ensure_vstack(p)) || (r = modal_forward(p, a, (const float2*)t, p->IBUF, true)) ||
+        (r = modal_resid(p, y, nullptr)) || (r = modal_backward(p, a, (const float2*)t, p->IBUF)))
+      return r;
+    a.in = p->ACC;
+    a.g_out = (float2*)g;
+    a.div_maxt2 = 1;
+    a.gscale = 1.0f;
+    LAUNCH(p, row(p, ROW_GRAD_OUT, a, a.B));
+    if (loss) {
+      k_gather_loss<<<(a.B + 255) / 256, 256, 0, p->stream>>>(p->acc, loss, a.B);
+      PWF_CUDA(p, cudaGetLastError());
+    }
+    return PWF_OK;
+  }
   if ((r = fused_to_detector(p, a, P, (const float2*)t, nullptr, true, a.B))) return r;
   a.in = p->X;
   a.out = p->X;
@@ -874,6 +1077,60 @@ pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const fl
   if (!grad_psi && !grad_t) return PWF_OK;
   const float2* P = (const float2*)psi;
   PassArgs a = base_args(p);
+  if (!p->modes.empty()) {
+    // per mode: forward to v_j, then straight back (v_j recomputed, never stored)
+    const float2* T = (const float2*)t;
+    a.psi = P;
+    a.out = p->X;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    for (size_t j = 0; j < p->modes.size(); j++) {
+      const Mode& md = p->modes[j];
+      PassArgs b = a;
+      b.in = p->X;
+      b.out = p->M;
+      LAUNCH(p, colmode(p, CM_FWD, b, md, 0, a.B));
+      b.in = p->M;
+      b.t = T;
+      b.u1 = grad_t ? p->S : nullptr;
+      LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
+      b.u1 = nullptr;
+      LAUNCH(p, col_q(p, b, 2, 0, a.B));
+      b.out = p->V;
+      LAUNCH(p, row(p, ROW_IFFT, b, a.B));          // v_j
+      b.v = p->V;
+      b.y = grad_f;
+      b.out = p->M;
+      LAUNCH(p, row(p, ROW_MODE_VG, b, a.B));       // v_j dL/df
+      b.in = p->M;
+      LAUNCH(p, col_q(p, b, 2, 1, a.B));            // P2^H
+      if (grad_t) {
+        b.u1 = p->S;
+        b.gt_scratch = p->YH;
+        b.mode_w = md.w;
+        b.accumulate = j > 0;
+        LAUNCH(p, row(p, ROW_GRADT, b, a.B));
+        b.u1 = nullptr;
+      } else {
+        b.conj_t = 1;
+        LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
+      }
+      b.out = p->ACC;
+      LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, a.B));
+    }
+    if (grad_t) {
+      const size_t n = (size_t)p->d.ny * p->d.nx;
+      k_batch_sum<<<grid_for(n), 256, 0, p->stream>>>(p->YH, (float2*)grad_t, a.B, n);
+      PWF_CUDA(p, cudaGetLastError());
+    }
+    if (grad_psi) {
+      a.in = p->ACC;
+      a.g_out = (float2*)grad_psi;
+      a.div_maxt2 = 0;
+      a.gscale = 2.0f;
+      LAUNCH(p, row(p, ROW_GRAD_OUT, a, a.B));
+    }
+    return PWF_OK;
+  }
   if ((r = fused_to_detector(p, a, P, (const float2*)t, grad_t ? p->S : nullptr, true, a.B))) return r;
   a.in = p->X;
   a.out = p->X;
@@ -966,6 +1223,7 @@ pwf_status pwf_step(pwf_plan* p, pwf_state* st, const float* y, const void* t, v
   if (!st || !y || !t || !psi) return PWF_ERR_INVALID_ARG;
   if (st->B != p->d.batch || st->ny != p->d.ny || st->nx != p->d.nx) return PWF_ERR_STATE;
   float2* P = (float2*)psi;
+  if (!p->modes.empty() && (r = ensure_vstack(p))) return r;
   if ((r = compute_maxt2(p, (const float2*)t))) return r;
   PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
   if (p->d.flags & PWF_FLAG_PLAIN) {
@@ -1011,6 +1269,7 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
   if (r) return r;
   if (!y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
   if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
+  if (!p->modes.empty() && (r = ensure_vstack(p))) return r;  // before the graph capture
   pwf_state* st = p->solve_state;
   if ((r = pwf_state_reset(p, st))) return r;
   float2* P = (float2*)psi;
@@ -1088,12 +1347,22 @@ pwf_status pwf_plan_set_column_shape(pwf_plan* p, int32_t pass, int32_t shape) {
 
 size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   if (!p) return 0;
-  char tmp[512];
+  char tmp[2048];
   size_t o = 0;
+  auto shape = [&](const ColVariant& v) {
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+  };
   o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
-  for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp); op++) {
-    const ColVariant& v = p->kcol->colv[op][p->colsel[op]];
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=C%d%s", kColNames[op], v.C, v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+  for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=", kColNames[op]);
+    shape(p->kcol->colv[op][p->colsel[op]]);
+    if (p->coltime[op][0] > 0.f) {  // tuned: all candidates with their times
+      o += std::snprintf(tmp + o, sizeof(tmp) - o, "[");
+      for (int v = 0; v < p->kcol->ncolv[op] && o < sizeof(tmp) - 32; v++) {
+        shape(p->kcol->colv[op][v]);
+        o += std::snprintf(tmp + o, sizeof(tmp) - o, ":%.3f%s", p->coltime[op][v], v + 1 < p->kcol->ncolv[op] ? "," : "]");
+      }
+    }
   }
   if (buf && len) {
     std::snprintf(buf, len, "%s", tmp);
@@ -1108,6 +1377,7 @@ pwf_status pwf_profile_iteration(pwf_plan* p, const float* y, const void* t, voi
   if (!y || !t || !psi || iters < 1 || !pass_ms || !pass_names || !n_passes) return PWF_ERR_INVALID_ARG;
   if (p->d.flags & PWF_FLAG_PLAIN) return PWF_ERR_UNSUPPORTED;
   if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
+  if (!p->modes.empty() && (r = ensure_vstack(p))) return r;
   pwf_state* st = p->solve_state;
   if ((r = pwf_state_reset(p, st)) || (r = compute_maxt2(p, (const float2*)t))) return r;
   if (!p->coherent && (r = compute_yhat(p, y, st->active))) return r;
@@ -1139,6 +1409,163 @@ pwf_status pwf_profile_iteration(pwf_plan* p, const float* y, const void* t, voi
   }
   *n_passes = (int32_t)per;
   return PWF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// groups: several plans (size classes) iterated together from one graph
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct pwf_group {
+  std::vector<pwf_plan*> plans;
+  std::vector<cudaStream_t> branch;  // one per plan, used only while capturing
+  cudaStream_t main = nullptr;       // capture origin
+  std::vector<cudaEvent_t> ev;       // fork/join events
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> key;
+  double tol = 0.0;
+  long long graph_kernels = 0;
+};
+
+extern "C" {
+
+pwf_status pwf_group_create(pwf_plan* const* plans, int32_t n, pwf_group** out) {
+  if (!plans || n < 1 || !out) return PWF_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; i++) {
+    if (!plans[i]) return PWF_ERR_INVALID_ARG;
+    if (plans[i]->d.flags & PWF_FLAG_PLAIN) return PWF_ERR_UNSUPPORTED;
+    for (int j = 0; j < i; j++)
+      if (plans[j] == plans[i]) return PWF_ERR_INVALID_ARG;
+  }
+  pwf_group* g = new (std::nothrow) pwf_group();
+  if (!g) return PWF_ERR_NOMEM;
+  g->plans.assign(plans, plans + n);
+  bool ok = cudaStreamCreateWithFlags(&g->main, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < n && ok; i++) {
+    cudaStream_t s;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) g->branch.push_back(s);
+  }
+  for (int i = 0; i < 2 * n + 1 && ok; i++) {
+    cudaEvent_t e;
+    ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) g->ev.push_back(e);
+  }
+  if (!ok) {
+    cudaGetLastError();
+    pwf_group_destroy(g);
+    return PWF_ERR_CUDA;
+  }
+  *out = g;
+  return PWF_OK;
+}
+
+pwf_status pwf_group_destroy(pwf_group* g) {
+  if (!g) return PWF_ERR_INVALID_ARG;
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  for (cudaStream_t s : g->branch) cudaStreamDestroy(s);
+  if (g->main) cudaStreamDestroy(g->main);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+  return PWF_OK;
+}
+
+pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, const void* const* t,
+                           void* const* psi, int32_t max_iter, double corr_tol) {
+  if (!g || !y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
+  const int n = (int)g->plans.size();
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  pwf_status r;
+  for (int i = 0; i < n; i++) {
+    pwf_plan* p = g->plans[i];
+    if ((r = check_plan(p))) return r;
+    if (!y[i] || !t[i] || !psi[i]) return PWF_ERR_INVALID_ARG;
+  }
+  if (max_iter == 0) return PWF_OK;
+  // set-up of every class on the caller's stream (Algorithm S1 initialisation)
+  for (int i = 0; i < n; i++) {
+    pwf_plan* p = g->plans[i];
+    p->stream = user;
+    if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
+    if (!p->modes.empty() && (r = ensure_vstack(p))) return r;
+    pwf_state* st = p->solve_state;
+    if ((r = pwf_state_reset(p, st)) || (r = compute_maxt2(p, (const float2*)t[i]))) return r;
+    if (p->modes.empty() && !p->coherent && (r = compute_yhat(p, y[i], st->active))) return r;
+    PassArgs a = base_args(p);
+    a.active = st->active;
+    a.psi = (const float2*)psi[i];
+    a.out = p->X;
+    LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+  }
+  // one graph: fork a branch per class, one fused iteration on each, join
+  std::vector<const void*> key;
+  for (int i = 0; i < n; i++) {
+    key.push_back(y[i]);
+    key.push_back(t[i]);
+    key.push_back(psi[i]);
+  }
+  if (!g->graph || key != g->key || g->tol != corr_tol) {
+    if (g->graph) {
+      cudaGraphExecDestroy(g->graph);
+      g->graph = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    pwf_plan* p0 = g->plans[0];
+    PWF_CUDA(p0, cudaStreamBeginCapture(g->main, cudaStreamCaptureModeThreadLocal));
+    r = PWF_OK;
+    cudaError_t ce = cudaEventRecord(g->ev[0], g->main);
+    long long kernels = 0;
+    for (int i = 0; i < n && r == PWF_OK && ce == cudaSuccess; i++) {
+      pwf_plan* p = g->plans[i];
+      ce = cudaStreamWaitEvent(g->branch[i], g->ev[0], 0);
+      if (ce != cudaSuccess) break;
+      p->stream = g->branch[i];
+      const long long before = p->launches;
+      r = fused_iteration(p, p->solve_state, y[i], (const float2*)t[i], (float2*)psi[i], true, corr_tol);
+      kernels += p->launches - before;
+      p->launches = before;
+      p->stream = user;
+      if (r == PWF_OK) ce = cudaEventRecord(g->ev[1 + i], g->branch[i]);
+      if (r == PWF_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(g->main, g->ev[1 + i], 0);
+    }
+    cudaError_t ce2 = cudaStreamEndCapture(g->main, &graph);
+    for (pwf_plan* p : g->plans) p->stream = user;
+    if (r || ce != cudaSuccess || ce2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (r) return r;
+      return cuda_fail(p0, ce != cudaSuccess ? ce : ce2, "group capture");
+    }
+    ce = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(p0, ce, "group graph instantiate");
+    g->key = key;
+    g->tol = corr_tol;
+    g->graph_kernels = kernels;
+  }
+  pwf_plan* p0 = g->plans[0];
+  for (int k = 0; k < max_iter; k++) {
+    PWF_CUDA(p0, cudaGraphLaunch(g->graph, user));
+    p0->launches += g->graph_kernels;
+    if (corr_tol > 0.0 && (k + 1) % 16 == 0 && k + 1 < max_iter) {
+      int active = 0;
+      for (pwf_plan* p : g->plans) {
+        DevIter it;
+        PWF_CUDA(p, cudaMemcpyAsync(&it, p->solve_state->it, sizeof(DevIter), cudaMemcpyDeviceToHost, user));
+        PWF_CUDA(p, cudaStreamSynchronize(user));
+        active += it.n_active;
+      }
+      if (active == 0) break;
+    }
+  }
+  return PWF_OK;
+}
+
+pwf_status pwf_group_read(pwf_group* g, int32_t index, double* loss_host, int32_t* iters_host) {
+  if (!g || index < 0 || index >= (int)g->plans.size()) return PWF_ERR_INVALID_ARG;
+  pwf_plan* p = g->plans[index];
+  if (!p->solve_state) return PWF_ERR_STATE;
+  return pwf_state_read(p, p->solve_state, loss_host, nullptr, iters_host, nullptr);
 }
 
 size_t pwf_state_bytes(const pwf_state* s) {

@@ -305,8 +305,20 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
     for (int i = 0; i < NB; i++) {
       const int b = t + i * TPF;
       const int k = b % NS;
+      // W^(r k) for r = 1..R-1: the powers r = 1, 2, 4, 8 come from the table,
+      // the others are products of two of them (one rounding each)
+      float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; r++) v[i * R + r] = cmul(v[i * R + r], __ldg(&tw[OFF + (r - 1) * NS + k]));
+      for (int r = 1; r < R; r++) {
+        if ((r & (r - 1)) == 0 || R == 3) {
+          w[r] = __ldg(&tw[OFF + (r - 1) * NS + k]);
+        } else {
+          const int hi = r >= 8 ? 8 : r >= 4 ? 4 : 2;
+          w[r] = cmul(w[hi], w[r - hi]);
+        }
+      }
+#pragma unroll
+      for (int r = 1; r < R; r++) v[i * R + r] = cmul(v[i * R + r], w[r]);
       dft<R, DIR>(&v[i * R]);
     }
   } else {

@@ -77,6 +77,11 @@ struct PassArgs {
   int div_maxt2;           // ROW_GRAD_OUT / PACK: divide by max|t|^2
   int no_precond;          // P^-1 := 1
   int proj0;               // first projection of this launch (plain path)
+  // source-mode variant: tilt bins, weight, accumulate flag, e^(2 pi i k / n) tables
+  int mode_mx, mode_my;
+  float mode_w;
+  int accumulate;
+  const float2* cis_y;     // exp(2 pi i k / ny), k = 0..ny-1
 };
 
 enum RowOp : int {
@@ -96,7 +101,9 @@ enum RowOp : int {
   ROW_GRAD_PACK,       // IFFT -> g; store Re g; FFT(alpha o psi) -> out, FFT(Im g) -> aux
   ROW_NESTEROV_FFT,    // IFFT -> Nesterov update; exp(psi_new) -> FFT
   ROW_NESTEROV,        // IFFT -> Nesterov update
-  ROW_GRADT,           // IFFT -> g2; scratch = 2 conj(u1) g2; conj(t) g2 -> FFT
+  ROW_GRADT,           // IFFT -> g2; scratch (+)= 2 w conj(u1) g2; conj(t) g2 -> FFT
+  ROW_MODE_INT,        // IFFT -> v_j (stored); I (+)= w |v_j|^2          (mode variant)
+  ROW_MODE_VG,         // v_j G (both real-space inputs) -> FFT           (mode variant)
   NUM_ROW_OPS
 };
 
@@ -112,9 +119,9 @@ enum ColOp : int {
 
 template <int OP>
 struct RowT {
-  static constexpr bool ifft_in = !(OP == ROW_EXP_FFT || OP == ROW_REAL_FFT || OP == ROW_FFT);
+  static constexpr bool ifft_in = !(OP == ROW_EXP_FFT || OP == ROW_REAL_FFT || OP == ROW_FFT || OP == ROW_MODE_VG);
   static constexpr bool fft_out = !(OP == ROW_IFFT || OP == ROW_INTENSITY_OUT || OP == ROW_REAL_OUT ||
-                                    OP == ROW_GRAD_OUT || OP == ROW_NESTEROV);
+                                    OP == ROW_GRAD_OUT || OP == ROW_NESTEROV || OP == ROW_MODE_INT);
   static constexpr int nred = (OP == ROW_RESID || OP == ROW_COH_RESID) ? 1
                               : (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) ? 5 : 0;
 };
@@ -181,6 +188,9 @@ __global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a
   if (t == 0) {
     if constexpr (OP == ROW_MUL_T || OP == ROW_GRADT) l2_prefetch(a.t + (size_t)yrow * N, N * sizeof(float2));
     if constexpr (OP == ROW_GRADT) l2_prefetch(a.u1 + rb, N * sizeof(float2));
+    if constexpr (OP == ROW_MODE_INT) {
+      if (a.accumulate) l2_prefetch(a.f_out + rb, N * sizeof(float));
+    }
     if constexpr (OP == ROW_MUL_V) l2_prefetch(a.v + rb, N * sizeof(float2));
     if constexpr (OP == ROW_RESID || OP == ROW_COH_RESID || OP == ROW_COH_VJP) l2_prefetch(a.y + rb, N * sizeof(float));
     if constexpr (OP == ROW_GRAD_PACK || OP == ROW_GRAD_OUT) l2_prefetch(a.psi + rb, N * sizeof(float2));
@@ -202,6 +212,13 @@ __global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a
   } else if constexpr (OP == ROW_REAL_FFT) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = make_float2(a.y[rb + slot_index<N, RS>(t, j)], 0.f);
+  } else if constexpr (OP == ROW_MODE_VG) {
+    // G (real, passed as y) times the stored detector field of this mode
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int x = slot_index<N, RS>(t, j);
+      v[j] = cscale(a.v[rb + x], a.y[rb + x]);
+    }
   } else {  // ROW_FFT
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = a.in[rb + slot_index<N, RS>(t, j)];
@@ -295,12 +312,24 @@ __global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a
       v[j] = xn;
     }
   } else if constexpr (OP == ROW_GRADT) {
+    const float w2 = 2.0f * a.mode_w;
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int x = slot_index<N, RS>(t, j);
       const float2 u = a.u1[rb + x];
-      a.gt_scratch[rb + x] = cscale(cmulc(v[j], u), 2.0f);
+      float2 gt = cscale(cmulc(v[j], u), w2);
+      if (a.accumulate) gt = cadd(gt, a.gt_scratch[rb + x]);
+      a.gt_scratch[rb + x] = gt;
       v[j] = cmulc(v[j], __ldg(&a.t[(size_t)yrow * N + x]));
+    }
+  } else if constexpr (OP == ROW_MODE_INT) {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int x = slot_index<N, RS>(t, j);
+      if (a.v != nullptr) a.v[rb + x] = v[j];
+      float fi = a.mode_w * cabs2(v[j]);
+      if (a.accumulate) fi += a.f_out[rb + x];
+      a.f_out[rb + x] = fi;
     }
   }
 
@@ -652,6 +681,70 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 }
 
 // ---------------------------------------------------------------------------
+// column passes of the source-mode variant
+// ---------------------------------------------------------------------------
+// A mode s(r) = exp(2 pi i (mx x / nx + my y / ny)) shifts the row spectrum:
+// F_row{x s}(kx, y) = exp(2 pi i my y / ny) F_row{x}(kx - mx, y).
+//   CM_FWD : out column kx = F_y^-1{ Q1 scale F_y{ e^(2 pi i my y/ny) in column (kx - mx) } }
+//   CM_BACK: out column (kx - mx) (+)= w e^(-2 pi i my y/ny) F_y^-1{ conj(Q1) scale F_y{ in column kx } }
+// (indices mod nx). Reads and writes go to different buffers.
+enum ColModeOp : int { CM_FWD = 0, CM_BACK = 1 };
+
+template <int N, int MOP, int C>
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+    col_mode_kernel(const PassArgs a) {
+  constexpr int EPT = ept_for(N);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  extern __shared__ float2 smem[];
+  const int tid = threadIdx.x;
+  const int c = tid % C, t = tid / C;
+  const int proj = blockIdx.y + a.proj0;
+  const int col = blockIdx.x * C + c;
+  if (a.active != nullptr && a.active[proj] == 0) return;
+  const int shifted = ((col - a.mode_mx) % a.nx + a.nx) % a.nx;
+  const size_t pb = (size_t)proj * a.ny * a.nx;
+  const size_t ld = (size_t)a.nx;
+  const ColLayout<C> sm{smem + c};
+  const int my = ((a.mode_my % N) + N) % N;
+  float2 v[EPT];
+  if constexpr (MOP == CM_FWD) {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int y = slot_index<N, RS>(t, j);
+      v[j] = cmul(a.in[pb + shifted + (size_t)y * ld], __ldg(&a.cis_y[(my * y) % N]));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) v[j] = a.in[pb + col + (size_t)slot_index<N, RS>(t, j) * ld];
+  }
+  fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+  {
+    const float2 qx = __ldg(&a.qx[col]);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
+      if constexpr (MOP == CM_BACK) q = cconj(q);
+      v[j] = cscale(cmul(v[j], q), a.scale);
+    }
+  }
+  fft_run<N, INV>(v, sm, t, a.tw_inv);
+  if constexpr (MOP == CM_FWD) {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) a.out[pb + col + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int y = slot_index<N, RS>(t, j);
+      float2 r = cscale(cmulc(v[j], __ldg(&a.cis_y[(my * y) % N])), a.mode_w);
+      const size_t o = pb + shifted + (size_t)y * ld;
+      if (a.accumulate) r = cadd(r, a.out[o]);
+      a.out[o] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch for one transform length
 // ---------------------------------------------------------------------------
 using PassFn = cudaError_t (*)(const PassArgs&, int nproj, cudaStream_t);
@@ -746,7 +839,25 @@ struct LengthKernels {
   PrepFn row_prep[NUM_ROW_OPS];
   ColVariant colv[NUM_COL_OPS][MAX_COL_VARIANTS];
   int ncolv[NUM_COL_OPS];
+  PassFn colmode[2];
+  PrepFn colmode_prep[2];
 };
+
+// the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
+__host__ __device__ constexpr int colmode_c(int n) { return n >= 1024 ? (tpf_for(n) * 8 <= 512 ? 8 : 4) : 16; }
+template <int N, int MOP>
+cudaError_t prep_colmode() {
+  constexpr int C = colmode_c(N);
+  return cudaFuncSetAttribute(col_mode_kernel<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)col_smem_bytes(N, C));
+}
+template <int N, int MOP>
+cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
+  constexpr int C = colmode_c(N);
+  dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
+  col_mode_kernel<N, MOP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+  return cudaGetLastError();
+}
 
 // a shape is offered when its CTA has 16..512 threads and its buffers fit
 template <int N, int OP, int C, int PIPE>
@@ -788,7 +899,7 @@ LengthKernels make_length_kernels() {
   PWF_ROW(ROW_EXP_FFT) PWF_ROW(ROW_REAL_FFT) PWF_ROW(ROW_FFT) PWF_ROW(ROW_IFFT) PWF_ROW(ROW_MUL_T)
   PWF_ROW(ROW_INTENSITY) PWF_ROW(ROW_INTENSITY_OUT) PWF_ROW(ROW_REAL_OUT) PWF_ROW(ROW_RESID)
   PWF_ROW(ROW_COH_RESID) PWF_ROW(ROW_COH_VJP) PWF_ROW(ROW_MUL_V) PWF_ROW(ROW_GRAD_OUT) PWF_ROW(ROW_GRAD_PACK)
-  PWF_ROW(ROW_NESTEROV_FFT) PWF_ROW(ROW_NESTEROV) PWF_ROW(ROW_GRADT)
+  PWF_ROW(ROW_NESTEROV_FFT) PWF_ROW(ROW_NESTEROV) PWF_ROW(ROW_GRADT) PWF_ROW(ROW_MODE_INT) PWF_ROW(ROW_MODE_VG)
 #undef PWF_ROW
   add_col_op<N, COL_Q>(k);
   add_col_op<N, COL_IOTF>(k);
@@ -796,6 +907,10 @@ LengthKernels make_length_kernels() {
   add_col_op<N, COL_PRECOND_REG>(k);
   add_col_op<N, COL_FFT>(k);
   add_col_op<N, COL_IFFT>(k);
+  k.colmode[CM_FWD] = launch_colmode<N, CM_FWD>;
+  k.colmode[CM_BACK] = launch_colmode<N, CM_BACK>;
+  k.colmode_prep[CM_FWD] = prep_colmode<N, CM_FWD>;
+  k.colmode_prep[CM_BACK] = prep_colmode<N, CM_BACK>;
   return k;
 }
 

@@ -42,6 +42,7 @@ class pwf_plan_desc(ctypes.Structure):
         ("xcoh_m", ctypes.c_double), ("ycoh_m", ctypes.c_double),
         ("gamma", ctypes.c_double), ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
         ("eta", ctypes.c_double), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+        ("n_modes", ctypes.c_int32), ("mode_sigma_px", ctypes.c_double),
     ]
 
 
@@ -96,6 +97,10 @@ def load(path: str | None = None):
         "pwf_plan_describe": ([_P, ctypes.c_char_p, sz], sz),
         "pwf_plan_column_shapes": ([_P, i32], i32),
         "pwf_plan_set_column_shape": ([_P, i32, i32], i32),
+        "pwf_group_create": ([_P, i32, ctypes.POINTER(_P)], i32),
+        "pwf_group_destroy": ([_P], i32),
+        "pwf_group_solve": ([_P, _P, _P, _P, _P, i32, f64], i32),
+        "pwf_group_read": ([_P, i32, _P, _P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -153,13 +158,19 @@ class PlanDesc:
     alpha_im: float = 0.01
     eta: float = 1.0
     flags: int = 0
+    n_modes: int = 0
+    mode_sigma_px: float = 0.0
+
+
+def _desc_struct(desc: PlanDesc) -> pwf_plan_desc:
+    return pwf_plan_desc(desc.batch, desc.ny, desc.nx, desc.pixel_m, desc.wavelength_m, desc.L1_m, desc.L2_m,
+                         desc.xcoh_m, desc.ycoh_m, desc.gamma, desc.alpha_re, desc.alpha_im, desc.eta,
+                         desc.flags, _stream_ptr(), desc.n_modes, desc.mode_sigma_px)
 
 
 def pwf_plan_create(desc: PlanDesc):
     lib = load()
-    d = pwf_plan_desc(desc.batch, desc.ny, desc.nx, desc.pixel_m, desc.wavelength_m, desc.L1_m, desc.L2_m,
-                      desc.xcoh_m, desc.ycoh_m, desc.gamma, desc.alpha_re, desc.alpha_im, desc.eta,
-                      desc.flags, _stream_ptr())
+    d = _desc_struct(desc)
     plan = ctypes.c_void_p()
     _check(lib.pwf_plan_create(ctypes.byref(d), ctypes.byref(plan)), "pwf_plan_create")
     return plan
@@ -186,9 +197,7 @@ def pwf_forward_noalloc(desc: "PlanDesc", psi, t, f):
     """Forward model without any device allocation by the library (scratch in
     fixed device arrays); for callers that cannot allocate. Runs on the current
     torch stream."""
-    d = pwf_plan_desc(desc.batch, desc.ny, desc.nx, desc.pixel_m, desc.wavelength_m, desc.L1_m, desc.L2_m,
-                      desc.xcoh_m, desc.ycoh_m, desc.gamma, desc.alpha_re, desc.alpha_im, desc.eta,
-                      desc.flags, _stream_ptr())
+    d = _desc_struct(desc)
     _check(load().pwf_forward_noalloc(ctypes.byref(d), _ptr(psi), _ptr(t), _ptr(f)), "pwf_forward_noalloc")
 
 
@@ -301,6 +310,35 @@ def pwf_plan_column_shapes(plan, pass_index: int) -> int:
 
 def pwf_plan_set_column_shape(plan, pass_index: int, shape: int):
     _check(load().pwf_plan_set_column_shape(plan, int(pass_index), int(shape)), "pwf_plan_set_column_shape", plan)
+
+
+def pwf_group_create(plans):
+    arr = (_P * len(plans))(*[p.handle if hasattr(p, "handle") else p for p in plans])
+    g = ctypes.c_void_p()
+    _check(load().pwf_group_create(arr, len(plans), ctypes.byref(g)), "pwf_group_create")
+    return g
+
+
+def pwf_group_destroy(group):
+    _check(load().pwf_group_destroy(group), "pwf_group_destroy")
+
+
+def pwf_group_solve(group, ys, ts, psis, max_iter: int, corr_tol: float = 0.0):
+    n = len(ys)
+    yp = (_P * n)(*[_ptr(y).value for y in ys])
+    tp = (_P * n)(*[_ptr(t).value for t in ts])
+    pp = (_P * n)(*[_ptr(p).value for p in psis])
+    _check(load().pwf_group_solve(group, _stream_ptr(), yp, tp, pp, int(max_iter), float(corr_tol)),
+           "pwf_group_solve")
+
+
+def pwf_group_read(group, index: int, batch: int):
+    import numpy as np
+    loss = np.zeros(batch, np.float64)
+    iters = np.zeros(batch, np.int32)
+    _check(load().pwf_group_read(group, int(index), loss.ctypes.data_as(_P), iters.ctypes.data_as(_P)),
+           "pwf_group_read")
+    return loss, iters
 
 
 def pwf_status_string(status: int) -> str:

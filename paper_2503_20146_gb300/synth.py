@@ -258,6 +258,9 @@ class Workload:
     # the blob workloads stays bounded (the paper's eta = 1 belongs to its own
     # geometry, lambda L2 / p^2 ~ 6, against ~25 here).
     eta: float = 2.0 ** -9
+    # source-mode variant of partial coherence (0: the paper's IOTF form)
+    n_modes: int = 0
+    mode_sigma_px: float = 0.0
 
     @property
     def mpx_per_iter(self) -> float:
@@ -274,9 +277,16 @@ WORKLOADS = {
     # Tomographic series: 180 angles over [0, 180) degrees of an ellipsoid phantom.
     "tomo180x1024_iotf": Workload("tomo180x1024_iotf", 3, 180, 1024, 1024, 100,
                                   xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4),
+    # The same series with partial coherence as 9 tilted source modes (sigma = 2 px).
+    "tomo180x1024_k9": Workload("tomo180x1024_k9", 3, 180, 1024, 1024, 100,
+                                xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4,
+                                n_modes=9, mode_sigma_px=2.0),
     # Differentiation workload: 16 projections at 2048^2.
     "grad16x2048_iotf": Workload("grad16x2048_iotf", 4, 16, 2048, 2048, 1,
                                  xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4),
+    "grad16x2048_k25": Workload("grad16x2048_k25", 4, 16, 2048, 2048, 1,
+                                xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4,
+                                n_modes=25, mode_sigma_px=2.0),
 }
 
 

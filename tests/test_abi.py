@@ -31,7 +31,7 @@ def test_status_strings(lib):
 def _desc(**kw):
     base = dict(batch=1, ny=128, nx=128, pixel_m=1e-6, wavelength_m=6.2e-11, L1_m=0.1, L2_m=0.4,
                 xcoh_m=0.0, ycoh_m=0.0, gamma=1.0, alpha_re=0.1, alpha_im=0.01, eta=1e-3, flags=0,
-                stream=None)
+                stream=None, n_modes=0, mode_sigma_px=0.0)
     base.update(kw)
     return pwf.pwf_plan_desc(**base)
 
@@ -45,6 +45,8 @@ def _desc(**kw):
     (dict(flags=0x80), 1),
     (dict(wavelength_m=2e-6), 2),  # evanescent bins at this pixel pitch
     (dict(L2_m=5e3), 2),           # separable-propagator bound exceeded
+    (dict(n_modes=4, mode_sigma_px=2.0), 1),   # mode count must be 0, 1, 9 or 25
+    (dict(n_modes=9, mode_sigma_px=-1.0), 1),
 ])
 def test_plan_validation_before_any_cuda_call(lib, kw, status):
     plan = ctypes.c_void_p()

@@ -363,3 +363,22 @@ def test_modal_gradient_matches_central_differences():
         Lp = O.loss(y, O.ModalPhysicalModel(psi + eps * d, t, g, modes)[0])
         Lm = O.loss(y, O.ModalPhysicalModel(psi - eps * d, t, g, modes)[0])
         assert abs((Lp - Lm) / (2 * eps) - an) <= 1e-7 * abs(an)
+
+
+def test_modal_vjp_matches_central_differences():
+    rng = np.random.default_rng(14)
+    g = geom(32, 32)
+    modes = O.source_modes(O.Geometry(32, 32, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4), 9, 1.5)
+    psi = 0.3 * crandn(rng, (32, 32))
+    t = np.exp(1j * rng.standard_normal((32, 32))) * (1 + 0.2 * rng.standard_normal((32, 32)))
+    gf = rng.standard_normal((32, 32))
+    gp, gt = O.modal_forward_vjp(psi, t, gf, g, modes)
+    eps = 1e-6
+    for grad, which in ((gp, "psi"), (gt, "t")):
+        d = crandn(rng, psi.shape)
+        a = (psi + eps * d, t) if which == "psi" else (psi, t + eps * d)
+        b = (psi - eps * d, t) if which == "psi" else (psi, t - eps * d)
+        Fp = np.sum(gf * O.ModalPhysicalModel(a[0], a[1], g, modes)[0])
+        Fm = np.sum(gf * O.ModalPhysicalModel(b[0], b[1], g, modes)[0])
+        an = np.sum(grad.real * d.real + grad.imag * d.imag)
+        assert abs((Fp - Fm) / (2 * eps) - an) <= 1e-7 * abs(an)
