@@ -269,6 +269,53 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line))
 
 
+def run_mixed(P, S, torch, dev, stream, steps=4):
+    """One group of four size-class plans; seeded blob objects, the CUDA
+    forward model and Poisson noise at per-projection photon counts."""
+    import numpy as np
+    wm = S.WORKLOADS["mixed64_k25"]
+    plans, ys, ts, psis = [], [], [], []
+    mpx = 0.0
+    for ci, n in enumerate(S.MIXED_SIZES):
+        d = P.PlanDesc(S.MIXED_PER_SIZE, n, n, wm.pixel_m, wm.wavelength_m, wm.L1_m, wm.L2_m, wm.xcoh_m, wm.ycoh_m,
+                       wm.gamma, wm.alpha.real, wm.alpha.imag, wm.eta, 0, wm.n_modes, wm.mode_sigma_px)
+        plan = P.Plan(d)
+        psi_true = torch.empty((S.MIXED_PER_SIZE, n, n), dtype=torch.complex64, device=dev)
+        for b in range(S.MIXED_PER_SIZE):
+            phi = S.blob_phase(n, n, S.rng_for(wm.config, 16 * ci + b), xp=torch, device=dev)
+            psi_true[b] = torch.complex(-0.05 * phi, phi).to(torch.complex64)
+        t = torch.from_numpy(S.diffuser(n, n, S.rng_for(wm.config, 99)).astype(np.complex64)).to(dev)
+        f = plan.forward(psi_true, t)
+        ph = torch.tensor([S.mixed_photons(wm.config, 16 * ci + b) for b in range(S.MIXED_PER_SIZE)],
+                          dtype=torch.float32, device=dev)[:, None, None]
+        g = torch.Generator(device=dev).manual_seed(20146500 + ci)
+        y = (torch.poisson(f.clamp_min(0) * ph, generator=g) / ph).contiguous()
+        plans.append(plan)
+        ys.append(y)
+        ts.append(t)
+        psis.append(torch.zeros_like(psi_true))
+        mpx += S.MIXED_PER_SIZE * n * n / 1e6
+        del f, psi_true
+    group = P.pwf_group_create(plans)
+    P.pwf_group_solve(group, ys, ts, psis, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for p in psis:
+        p.zero_()
+    P.pwf_group_solve(group, ys, ts, psis, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    shapes = [P.pwf_plan_describe(p.handle).split(" col_q")[0] for p in plans]
+    P.pwf_group_destroy(group)
+    for p in plans:
+        p.close()
+    return {"value": mpx * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "workload": wm.name, "mpx_per_iter": mpx, "classes": shapes,
+            "launch": "one CUDA graph launch per iteration over all four size classes"}
+
+
 # ----------------------------------------------------------------------------
 # main arm
 # ----------------------------------------------------------------------------
@@ -420,6 +467,10 @@ def main():
                                   "workload": wk.name, "steps": msteps}
             mplan.close()
             del pm
+
+        # uneven batch: 16 each of 256^2, 768^2, 1536^2, 2048^2, 25 modes, one group
+        if w.name == "tomo180x1024_iotf":
+            extras["mixed_k25"] = run_mixed(P, S, torch, dev, stream)
 
         # FP64 oracle on the host cores, bounded sample
         dt, work = oracle_sample(w, 1, 3)

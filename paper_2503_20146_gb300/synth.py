@@ -48,26 +48,28 @@ def xcoh_from_blur_sigma(sigma_px: float, pixel_m: float = PIXEL_M) -> float:
 # Object: sum of Gaussian blobs (Fig. S7-style phantom)
 # ----------------------------------------------------------------------------
 def blob_phase(ny: int, nx: int, rng: np.random.Generator, n_blobs: int = 8,
-               peak_rad: float = 2.0) -> np.ndarray:
+               peak_rad: float = 2.0, xp=np, device=None):
     """Phase map made of ``n_blobs`` Gaussian blobs, rescaled to max |phi| = peak.
 
     Centres are uniform in the central 80 % of the field, standard deviations
     uniform in [n/32, n/8] pixels (n = min(ny, nx)), amplitudes uniform in
-    [-1, 1] before the rescale.
+    [-1, 1] before the rescale. The draws come from ``rng`` (numpy); the grid
+    arithmetic runs on ``xp`` (numpy, or torch with ``device``).
     """
     n = min(ny, nx)
-    yy = np.arange(ny, dtype=np.float64)[:, None]
-    xx = np.arange(nx, dtype=np.float64)[None, :]
-    phi = np.zeros((ny, nx), dtype=np.float64)
+    kw = {} if xp is np else {"device": device}
+    yy = xp.arange(ny, dtype=xp.float64, **kw)[:, None]
+    xx = xp.arange(nx, dtype=xp.float64, **kw)[None, :]
+    phi = xp.zeros((ny, nx), dtype=xp.float64, **kw)
     for _ in range(n_blobs):
         cy = rng.uniform(0.1 * ny, 0.9 * ny)
         cx = rng.uniform(0.1 * nx, 0.9 * nx)
         sd = rng.uniform(n / 32.0, n / 8.0)
         amp = rng.uniform(-1.0, 1.0)
-        phi += amp * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2.0 * sd * sd))
-    m = np.max(np.abs(phi))
+        phi = phi + amp * xp.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2.0 * sd * sd))
+    m = float(abs(phi).max())
     if m > 0:
-        phi *= peak_rad / m
+        phi = phi * (peak_rad / m)
     return phi
 
 
@@ -284,6 +286,12 @@ WORKLOADS = {
     # Differentiation workload: 16 projections at 2048^2.
     "grad16x2048_iotf": Workload("grad16x2048_iotf", 4, 16, 2048, 2048, 1,
                                  xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4),
+    # Uneven batch: 16 projections each of 256^2, 768^2, 1536^2, 2048^2 (one
+    # plan per size class in a group), 25 source modes, photons log-uniform in
+    # [1e3, 1e5] per projection.
+    "mixed64_k25": Workload("mixed64_k25", 5, 64, 0, 0, 100,
+                            xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 0.0,
+                            n_modes=25, mode_sigma_px=2.0),
     "grad16x2048_k25": Workload("grad16x2048_k25", 4, 16, 2048, 2048, 1,
                                 xcoh_from_blur_sigma(2.0), xcoh_from_blur_sigma(2.0), 1e4,
                                 n_modes=25, mode_sigma_px=2.0),
@@ -297,6 +305,15 @@ def blob_case(w: Workload, proj: int = 0):
     rng = rng_for(w.config, proj)
     psi = complex_phase_from(blob_phase(w.ny, w.nx, rng))
     return psi, t
+
+
+MIXED_SIZES = (256, 768, 1536, 2048)
+MIXED_PER_SIZE = 16
+
+
+def mixed_photons(config: int, index: int) -> float:
+    """Photons per pixel of projection ``index`` of the uneven batch: log-uniform in [1e3, 1e5]."""
+    return float(np.exp(rng_for(config, 300 + index).uniform(np.log(1e3), np.log(1e5))))
 
 
 def tomo_angles(n: int) -> np.ndarray:

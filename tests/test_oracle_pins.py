@@ -118,10 +118,12 @@ def test_piston_reading_matches_literal_transfer_function():
 def test_no_evanescent_bins_and_exact_adjoint_at_workload_geometry():
     """Reading R2: rho^2 < lambda^-2 everywhere, so P(-L) = conj(Q)."""
     for w in S.WORKLOADS.values():
-        g = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m)
-        Q = O.transfer_function(g, g.L2)
-        assert np.all(np.abs(np.abs(Q) - 1) < 1e-15)
-        assert np.max(np.abs(O.transfer_function(g, -g.L2) - np.conj(Q))) < 1e-15
+        sizes = [(w.ny, w.nx)] if w.ny else [(n, n) for n in S.MIXED_SIZES]
+        for ny, nx in sizes:
+            g = O.Geometry(ny, nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m)
+            Q = O.transfer_function(g, g.L2)
+            assert np.all(np.abs(np.abs(Q) - 1) < 1e-15)
+            assert np.max(np.abs(O.transfer_function(g, -g.L2) - np.conj(Q))) < 1e-15
 
 
 # ----------------------------------------------------------------------------
