@@ -316,6 +316,46 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
             "launch": "one CUDA graph launch per iteration over all four size classes"}
 
 
+def run_autograd(P, S, torch, dev, stream, reps=3):
+    """Forward model + hand-written backward (w.r.t. psi and the diffuser) via
+    the autograd Function, 16 projections of 2048^2, in the IOTF form and with
+    25 source modes (mode fields recomputed in the backward, never stored)."""
+    import numpy as np
+    from paper_2503_20146_gb300.autograd import physical_model
+    out = {}
+    for name in ("grad16x2048_iotf", "grad16x2048_k25"):
+        wg = S.WORKLOADS[name]
+        plan = P.Plan(plan_desc(P, wg, wg.batch))
+        psi = torch.empty((wg.batch, wg.ny, wg.nx), dtype=torch.complex64, device=dev)
+        for b in range(wg.batch):
+            phi = S.blob_phase(wg.ny, wg.nx, S.rng_for(wg.config, b), xp=torch, device=dev)
+            psi[b] = torch.complex(-0.05 * phi, phi).to(torch.complex64)
+        t = torch.from_numpy(S.diffuser(wg.ny, wg.nx, S.rng_for(wg.config, 99)).astype(np.complex64)).to(dev)
+        wts = torch.randn(psi.shape, generator=torch.Generator(device=dev).manual_seed(4), device=dev)
+        psi.requires_grad_(True)
+        t.requires_grad_(True)
+
+        def step():
+            psi.grad = None
+            t.grad = None
+            (physical_model(psi, t, plan) * wts).sum().backward()
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        mpx = wg.batch * wg.ny * wg.nx / 1e6
+        out[name] = {"ms_per_forward_backward": ms, "Mpx_per_s": mpx / (ms / 1e3), "n_modes": wg.n_modes}
+        plan.close()
+        del psi, t, wts
+    return out
+
+
 # ----------------------------------------------------------------------------
 # main arm
 # ----------------------------------------------------------------------------
@@ -471,6 +511,10 @@ def main():
         # uneven batch: 16 each of 256^2, 768^2, 1536^2, 2048^2, 25 modes, one group
         if w.name == "tomo180x1024_iotf":
             extras["mixed_k25"] = run_mixed(P, S, torch, dev, stream)
+
+        # differentiation: 16 x 2048^2 forward + backward through torch.autograd
+        if w.name == "tomo180x1024_iotf":
+            extras["autograd_16x2048"] = run_autograd(P, S, torch, dev, stream)
 
         # FP64 oracle on the host cores, bounded sample
         dt, work = oracle_sample(w, 1, 3)

@@ -161,6 +161,69 @@ __device__ __forceinline__ void dft16(float2* x) {
   }
 }
 
+// exp(s 2 pi i m / 32) for the compile-time exponent m
+template <int DIR, int M>
+__device__ __forceinline__ float2 twm32(float2 a) {
+  constexpr int m = M & 31;
+  if constexpr ((m & 1) == 0) {
+    return twm16<DIR, m / 2>(a);
+  } else {
+    // cos and sin of m*pi/16 for odd m
+    constexpr double PI = 3.14159265358979323846;
+    constexpr float c1 = 0.98078528040323043f, s1 = 0.19509032201612825f;  // pi/16
+    constexpr float c3 = 0.83146961230254524f, s3 = 0.55557023301960218f;  // 3 pi/16
+    constexpr float c5 = 0.55557023301960218f, s5 = 0.83146961230254524f;  // 5 pi/16
+    constexpr float c7 = 0.19509032201612825f, s7 = 0.98078528040323043f;  // 7 pi/16
+    (void)PI;
+    // reduce m to the first quadrant: angle = m pi / 16
+    constexpr int q = m / 8, r = m % 8;  // m = 8q + r, r odd
+    constexpr float cr = r == 1 ? c1 : r == 3 ? c3 : r == 5 ? c5 : c7;
+    constexpr float sr = r == 1 ? s1 : r == 3 ? s3 : r == 5 ? s5 : s7;
+    // rotate by q quarter turns
+    constexpr float c = q == 0 ? cr : q == 1 ? -sr : q == 2 ? -cr : sr;
+    constexpr float sn = q == 0 ? sr : q == 1 ? cr : q == 2 ? -sr : -cr;
+    return cmul(a, make_float2(c, DIR == FWD ? -sn : sn));
+  }
+}
+
+// 32-point: radix-2 split into the 16-point DFTs of the even and odd
+// samples, combined with the twiddles W32^k.
+template <int DIR>
+__device__ __forceinline__ void dft32(float2* x) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    e[k] = x[2 * k];
+    o[k] = x[2 * k + 1];
+  }
+  dft16<DIR>(e);
+  dft16<DIR>(o);
+#pragma unroll
+  for (int k = 0; k < 16; k++) {
+    float2 w;
+    switch (k) {  // resolved at compile time after unrolling
+      case 0: w = o[0]; break;
+      case 1: w = twm32<DIR, 1>(o[1]); break;
+      case 2: w = twm32<DIR, 2>(o[2]); break;
+      case 3: w = twm32<DIR, 3>(o[3]); break;
+      case 4: w = twm32<DIR, 4>(o[4]); break;
+      case 5: w = twm32<DIR, 5>(o[5]); break;
+      case 6: w = twm32<DIR, 6>(o[6]); break;
+      case 7: w = twm32<DIR, 7>(o[7]); break;
+      case 8: w = twm32<DIR, 8>(o[8]); break;
+      case 9: w = twm32<DIR, 9>(o[9]); break;
+      case 10: w = twm32<DIR, 10>(o[10]); break;
+      case 11: w = twm32<DIR, 11>(o[11]); break;
+      case 12: w = twm32<DIR, 12>(o[12]); break;
+      case 13: w = twm32<DIR, 13>(o[13]); break;
+      case 14: w = twm32<DIR, 14>(o[14]); break;
+      default: w = twm32<DIR, 15>(o[15]); break;
+    }
+    x[k] = cadd(e[k], w);
+    x[k + 16] = csub(e[k], w);
+  }
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* x) {
   if constexpr (R == 2) dft2<DIR>(x);
@@ -168,6 +231,7 @@ __device__ __forceinline__ void dft(float2* x) {
   else if constexpr (R == 4) dft4<DIR>(x);
   else if constexpr (R == 8) dft8<DIR>(x);
   else if constexpr (R == 16) dft16<DIR>(x);
+  else if constexpr (R == 32) dft32<DIR>(x);
   else static_assert(R == 2, "unsupported radix");
 }
 
@@ -313,7 +377,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
         if ((r & (r - 1)) == 0 || R == 3) {
           w[r] = __ldg(&tw[OFF + (r - 1) * NS + k]);
         } else {
-          const int hi = r >= 8 ? 8 : r >= 4 ? 4 : 2;
+          const int hi = r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : 2;
           w[r] = cmul(w[hi], w[r - hi]);
         }
       }

@@ -166,7 +166,7 @@ __device__ __forceinline__ void block_reduce_add(const float (&part)[5], double*
 // row pass
 // ---------------------------------------------------------------------------
 template <int N, int OP>
-__global__ void __launch_bounds__(row_threads(N), 3) row_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_kernel(const PassArgs a) {
   constexpr int EPT = ept_for(N), TPF = tpf_for(N), ROWS = rows_for(N);
   constexpr int RS = first_radix<N, FWD>();  // slot radix of real-space data
   constexpr int RK = last_radix<N, FWD>();   // slot radix of spectra
@@ -374,7 +374,9 @@ __host__ __device__ constexpr size_t col_smem_bytes(int n, int c) {
   return (size_t)c * col_tile_rows(n, c) * sizeof(float2);
 }
 __host__ __device__ constexpr size_t colp_smem_bytes(int n, int c) { return 2 * col_smem_bytes(n, c); }
-__host__ __device__ constexpr int col_min_blocks(int threads) { return threads >= 512 ? 1 : threads >= 256 ? 3 : 4; }
+__host__ __device__ constexpr int col_min_blocks(int threads, int ept = 16) {
+  return ept >= 32 ? (threads >= 512 ? 1 : 2) : (threads >= 512 ? 1 : threads >= 256 ? 3 : 4);
+}
 
 // the filter step and the inverse transform of one tile (v holds the forward
 // spectrum of the column in slots of the last forward radix)
@@ -426,7 +428,7 @@ __device__ __forceinline__ void col_tile_filter(const PassArgs& a, const L& sm, 
 }
 
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_kernel(const PassArgs a) {
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
@@ -481,7 +483,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The copy of tile k+1 is one cp.async commit group (16-byte chunks); the wait
 // for tile k is cp.async.wait_group 1, which returns once that group landed.
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_kernel_pipe(const PassArgs a, int nproj) {
   constexpr int EPT = ept_for(N);
   constexpr int NT = col_threads(N, C);
@@ -585,7 +587,7 @@ __host__ __device__ constexpr size_t colt_smem_bytes(int n, int c) {
 }
 
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_kernel_t(const PassArgs a, int nproj) {
   constexpr int EPT = ept_for(N), TPF = tpf_for(N);
   constexpr int NT = col_threads(N, C);
@@ -691,7 +693,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 enum ColModeOp : int { CM_FWD = 0, CM_BACK = 1 };
 
 template <int N, int MOP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_mode_kernel(const PassArgs a) {
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
