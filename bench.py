@@ -64,6 +64,7 @@ def parse_args():
     ap.add_argument("--workload", default="tomo180x1024_iotf")
     ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
+    ap.add_argument("--overlap", action="store_true", help="two half-batch chains (PWF_FLAG_OVERLAP)")
     return ap.parse_args()
 
 
@@ -385,7 +386,7 @@ def main():
     mpx_iter = batch * w.ny * w.nx / 1e6
 
     psi_true, t = make_workload(P, S, w, batch, dev, rank, world)
-    plan = P.Plan(plan_desc(P, w, batch))
+    plan = P.Plan(plan_desc(P, w, batch, P.FLAG_OVERLAP if args.overlap else 0))
     f = plan.forward(psi_true, t)
     gen = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config + rank)
     y = (torch.poisson(f.clamp_min(0) * w.photons, generator=gen) / w.photons).contiguous()
@@ -531,7 +532,8 @@ def main():
                        "coherence": "IOTF, Gaussian sigma = 2 px" if w.xcoh_m > 0 else "coherent",
                        "eta": w.eta, "l2_flush": "inputs larger than L2 (state ~1.5 GB per field)",
                        "step": "one PWF iteration over all projections",
-                       "column_shapes": tuned},
+                       "column_shapes": tuned,
+                       "overlap": "two half-batch chains offset by one pass" if args.overlap else "one chain"},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "iteration": iteration,

@@ -55,6 +55,11 @@ typedef struct pwf_state pwf_state;
 #define PWF_FLAG_PLAIN 0x4u      /* unfused per-operation kernels, one projection at
                                     a time: Algorithm S2 executed step by step     */
 #define PWF_FLAG_NO_TUNE 0x8u    /* skip the plan-time column-pass autotuning      */
+#define PWF_FLAG_OVERLAP 0x10u   /* pwf_solve iterates the two halves of the batch as
+                                    two graph branches offset by one pass, so column
+                                    passes (arithmetic-bound) of one half run beside
+                                    row passes (bandwidth-bound) of the other; column
+                                    shapes are then tuned among one-tile-per-CTA ones */
 
 /* Inputs of Algorithm S1 other than y and t. All lengths in metres. */
 typedef struct {

@@ -300,6 +300,13 @@ struct pwf_plan {
   double graph_tol = 0.0;
   pwf_status sticky = PWF_OK;
   char err[256] = "";
+  // overlap of two half-batches (PWF_FLAG_OVERLAP): the projection range of
+  // the passes being enqueued, and the per-pass events of the two chains
+  int rng_proj0 = 0, rng_nproj = 0;
+  int ovl_mode = 0;  // 0 off, 1 record after each pass, 2 wait before each pass
+  int ovl_k = 0;
+  std::vector<cudaEvent_t> ovl_ev;
+  cudaStream_t ovl_stream[2] = {nullptr, nullptr};
   // instrumentation: kernels enqueued, and per-pass event timing
   long long launches = 0;
   long long graph_kernels = 0;  // kernels in the captured iteration graph
@@ -430,8 +437,12 @@ PassArgs base_args(pwf_plan* p) {
   a.no_precond = (p->d.flags & PWF_FLAG_NO_PRECOND) ? 1 : 0;
   a.gscale = 1.0f;
   a.mode_w = 1.0f;
+  a.proj0 = p->rng_proj0;
   return a;
 }
+
+// projections covered by the passes being enqueued (all, or one half when overlapping)
+int nproj_of(const pwf_plan* p) { return p->rng_nproj > 0 ? p->rng_nproj : p->d.batch; }
 
 const char* const kRowNames[NUM_ROW_OPS] = {
     "row_exp_fft", "row_real_fft", "row_fft", "row_ifft", "row_mul_t", "row_intensity", "row_intensity_out",
@@ -443,6 +454,18 @@ const char* const kColNames[NUM_COL_OPS] = {"col_q", "col_iotf", "col_resid_iotf
 // Enqueues one kernel; under pwf_profile_iteration it is bracketed by events.
 template <class F>
 cudaError_t enqueue(pwf_plan* p, const char* name, F&& launch) {
+  if (p->ovl_mode) {  // chain B waits for chain A's pass k; chain A marks it
+    if (p->ovl_k >= (int)p->ovl_ev.size()) return cudaErrorInvalidValue;
+    if (p->ovl_mode == 2) {
+      cudaError_t e = cudaStreamWaitEvent(p->stream, p->ovl_ev[p->ovl_k], 0);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch();
+    p->launches++;
+    if (e == cudaSuccess && p->ovl_mode == 1) e = cudaEventRecord(p->ovl_ev[p->ovl_k], p->stream);
+    p->ovl_k++;
+    return e;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (p->prof) {
     if (p->prof_n + 2 > p->ev_pool.size()) {
@@ -578,8 +601,8 @@ std::vector<Mode> source_modes(const pwf_plan_desc& d) {
 }
 
 // e = y - I; loss += e^2 per projection; I <- -e (= f - y)
-__global__ void k_modal_resid(float* I, const float* __restrict__ y, size_t per_proj, double* acc) {
-  const int proj = blockIdx.y;
+__global__ void k_modal_resid(float* I, const float* __restrict__ y, size_t per_proj, double* acc, int proj0) {
+  const int proj = blockIdx.y + proj0;
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_proj; i += (size_t)gridDim.x * blockDim.x) {
     const size_t o = (size_t)proj * per_proj + i;
@@ -620,18 +643,18 @@ pwf_status modal_forward(pwf_plan* p, PassArgs a, const float2* t, float* intens
     PassArgs b = a;
     b.in = p->X;
     b.out = p->M;
-    LAUNCH(p, colmode(p, CM_FWD, b, md, 0, a.B));  // tilt, P1
+    LAUNCH(p, colmode(p, CM_FWD, b, md, 0, nproj_of(p)));  // tilt, P1
     b.in = p->M;
     b.t = t;
     b.conj_t = 0;
     b.u1 = nullptr;
-    LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
-    LAUNCH(p, col_q(p, b, 2, 0, a.B));              // P2
+    LAUNCH(p, row(p, ROW_MUL_T, b, nproj_of(p)));
+    LAUNCH(p, col_q(p, b, 2, 0, nproj_of(p)));              // P2
     b.v = store_v ? p->VSTACK + j * n : nullptr;
     b.f_out = intensity;
     b.mode_w = md.w;
     b.accumulate = j > 0;
-    LAUNCH(p, row(p, ROW_MODE_INT, b, a.B));
+    LAUNCH(p, row(p, ROW_MODE_INT, b, nproj_of(p)));
   }
   return PWF_OK;
 }
@@ -646,14 +669,14 @@ pwf_status modal_backward(pwf_plan* p, PassArgs a, const float2* t, const float*
     b.v = p->VSTACK + j * n;
     b.y = G;
     b.out = p->M;
-    LAUNCH(p, row(p, ROW_MODE_VG, b, a.B));
+    LAUNCH(p, row(p, ROW_MODE_VG, b, nproj_of(p)));
     b.in = p->M;
-    LAUNCH(p, col_q(p, b, 2, 1, a.B));              // P2^H
+    LAUNCH(p, col_q(p, b, 2, 1, nproj_of(p)));              // P2^H
     b.t = t;
     b.conj_t = 1;
-    LAUNCH(p, row(p, ROW_MUL_T, b, a.B));
+    LAUNCH(p, row(p, ROW_MUL_T, b, nproj_of(p)));
     b.out = p->ACC;
-    LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, a.B));  // P1^H, untilt, accumulate
+    LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, nproj_of(p)));  // P1^H, untilt, accumulate
   }
   return PWF_OK;
 }
@@ -661,9 +684,9 @@ pwf_status modal_backward(pwf_plan* p, PassArgs a, const float2* t, const float*
 pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
   (void)active;
   const size_t per = (size_t)p->d.ny * p->d.nx;
-  dim3 grid((unsigned)((per + 255) / 256 > 64 ? 64 : (per + 255) / 256), (unsigned)p->d.batch);
+  dim3 grid((unsigned)((per + 255) / 256 > 64 ? 64 : (per + 255) / 256), (unsigned)nproj_of(p));
   return enqueue(p, "modal_resid", [&] {
-           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc);
+           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc, p->rng_proj0);
            return cudaGetLastError();
          }) == cudaSuccess
              ? PWF_OK
@@ -689,46 +712,88 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     a.psi = psi;
     a.reg = p->REG;
     a.aux = p->S;
-    LAUNCH(p, row(p, ROW_GRAD_PACK, a, a.B));
+    LAUNCH(p, row(p, ROW_GRAD_PACK, a, nproj_of(p)));
     a.in = p->X;
     a.aux_in = p->S;
-    LAUNCH(p, col(p, COL_PRECOND_REG, a, a.B));
+    LAUNCH(p, col(p, COL_PRECOND_REG, a, nproj_of(p)));
     a.psi_out = psi;
     a.phi = st->phi;
-    LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, a.B));
-    LAUNCH(p, enqueue(p, "finalize", [&] {
-      k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it,
-                                           corr_tol);
-      return cudaGetLastError();
-    }));
+    LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
+    if (p->ovl_mode == 0)
+      LAUNCH(p, enqueue(p, "finalize", [&] {
+        k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it,
+                                             corr_tol);
+        return cudaGetLastError();
+      }));
     return PWF_OK;
   }
-  r = fused_to_detector(p, a, psi, t, nullptr, false, a.B);
+  r = fused_to_detector(p, a, psi, t, nullptr, false, nproj_of(p));
   if (r) return r;
   a.in = p->X;
   a.out = p->X;
   a.y = y;
   if (p->coherent) {
-    LAUNCH(p, row(p, ROW_COH_RESID, a, a.B));   // e = y - |v|^2; loss; v (-e)
+    LAUNCH(p, row(p, ROW_COH_RESID, a, nproj_of(p)));   // e = y - |v|^2; loss; v (-e)
   } else {
     a.v = p->V;
-    LAUNCH(p, row(p, ROW_INTENSITY, a, a.B));   // v stored; F_row{|v|^2}
+    LAUNCH(p, row(p, ROW_INTENSITY, a, nproj_of(p)));   // v stored; F_row{|v|^2}
     a.yhat = p->YH;
-    LAUNCH(p, col(p, COL_RESID_IOTF2, a, a.B)); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
-    LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v Filter(-e, IOTF)
+    LAUNCH(p, col(p, COL_RESID_IOTF2, a, nproj_of(p))); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
+    LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v Filter(-e, IOTF)
   }
-  if ((r = fused_backprop(p, a, t, false, a.B))) return r;
+  if ((r = fused_backprop(p, a, t, false, nproj_of(p)))) return r;
   a.psi = psi;
   a.reg = p->REG;
   a.aux = p->S;
-  LAUNCH(p, row(p, ROW_GRAD_PACK, a, a.B));     // Re g; F_row{alpha o psi}; F_row{Im g}
+  LAUNCH(p, row(p, ROW_GRAD_PACK, a, nproj_of(p)));     // Re g; F_row{alpha o psi}; F_row{Im g}
   a.aux_in = p->S;
-  LAUNCH(p, col(p, COL_PRECOND_REG, a, a.B));   // Gamma^2 H + i P^-1 S
+  LAUNCH(p, col(p, COL_PRECOND_REG, a, nproj_of(p)));   // Gamma^2 H + i P^-1 S
   a.psi_out = psi;
   a.phi = st->phi;
-  LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, a.B));
+  LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
+  if (p->ovl_mode == 0)
+    LAUNCH(p, enqueue(p, "finalize", [&] {
+      k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
+      return cudaGetLastError();
+    }));
+  return PWF_OK;
+}
+
+// One iteration as two chains over the halves of the batch, captured from
+// p->capture_stream; finalize runs once after both.
+pwf_status overlapped_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
+                                double corr_tol) {
+  cudaStream_t main = p->capture_stream;
+  const int B = p->d.batch, B1 = B / 2;
+  cudaEvent_t fork = p->ovl_ev[p->ovl_ev.size() - 1], joinA = p->ovl_ev[p->ovl_ev.size() - 2],
+              joinB = p->ovl_ev[p->ovl_ev.size() - 3];
+  PWF_CUDA(p, cudaEventRecord(fork, main));
+  pwf_status r = PWF_OK;
+  for (int h = 0; h < 2 && r == PWF_OK; h++) {
+    cudaStream_t s = p->ovl_stream[h];
+    PWF_CUDA(p, cudaStreamWaitEvent(s, fork, 0));
+    p->stream = s;
+    p->rng_proj0 = h == 0 ? 0 : B1;
+    p->rng_nproj = h == 0 ? B1 : B - B1;
+    p->ovl_mode = h == 0 ? 1 : 2;
+    p->ovl_k = 0;
+    r = fused_iteration(p, st, y, t, psi, true, corr_tol);
+    if (r == PWF_OK && p->ovl_k > (int)p->ovl_ev.size() - 3) r = fail(p, PWF_ERR_STATE, "too many passes to overlap");
+    if (r == PWF_OK) {
+      cudaError_t e = cudaEventRecord(h == 0 ? joinA : joinB, s);
+      if (e != cudaSuccess) r = cuda_fail(p, e, "join");
+    }
+  }
+  p->ovl_mode = 0;
+  p->ovl_k = 0;
+  p->rng_proj0 = 0;
+  p->rng_nproj = 0;
+  p->stream = main;
+  if (r) return r;
+  PWF_CUDA(p, cudaStreamWaitEvent(main, joinA, 0));
+  PWF_CUDA(p, cudaStreamWaitEvent(main, joinB, 0));
   LAUNCH(p, enqueue(p, "finalize", [&] {
-    k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
+    k_finalize<<<1, 256, 0, main>>>(p->acc, B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
     return cudaGetLastError();
   }));
   return PWF_OK;
@@ -843,9 +908,13 @@ pwf_status tune_columns(pwf_plan* p) {
   a.ex = p->ax.stf;
   a.ey = p->ay.stf;
   cudaError_t err = cudaSuccess;
+  // when two half-batches overlap, persistent column kernels would fill the
+  // SMs and serialise the two chains: only one-tile-per-CTA shapes compete
+  const bool overlap = !p->ovl_ev.empty();
   for (int op = 0; op < NUM_COL_OPS && err == cudaSuccess; op++) {
     float best = 1e30f;
     for (int v = 0; v < p->kcol->ncolv[op] && err == cudaSuccess; v++) {
+      if (overlap && p->kcol->colv[op][v].pipe) continue;
       const PassFn fn = p->kcol->colv[op][v].launch;
       if ((err = fn(a, a.B, p->stream)) != cudaSuccess) break;
       cudaEventRecord(e0, p->stream);
@@ -904,7 +973,7 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   const pwf_plan_desc& d = *desc;
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
-      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE)))
+      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE | PWF_FLAG_OVERLAP)))
     return PWF_ERR_INVALID_ARG;
   if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
     return PWF_ERR_INVALID_ARG;
@@ -963,6 +1032,21 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
     pwf_plan_destroy(p);
     return PWF_ERR_CUDA;
   }
+  if ((d.flags & PWF_FLAG_OVERLAP) && d.batch >= 2) {
+    bool ok = cudaStreamCreateWithFlags(&p->ovl_stream[0], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p->ovl_stream[1], cudaStreamNonBlocking) == cudaSuccess;
+    const size_t nev = 8 + 8 * (p->modes.size() + 4);  // passes per iteration, generously
+    for (size_t i = 0; i < nev && ok; i++) {
+      cudaEvent_t e;
+      ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) p->ovl_ev.push_back(e);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      pwf_plan_destroy(p);
+      return PWF_ERR_CUDA;
+    }
+  }
   if (!(d.flags & PWF_FLAG_NO_TUNE) && (r = tune_columns(p)) != PWF_OK) {
     pwf_plan_destroy(p);
     return r;
@@ -976,6 +1060,9 @@ pwf_status pwf_plan_destroy(pwf_plan* p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->solve_state) pwf_state_destroy(p->solve_state);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ovl_ev) cudaEventDestroy(e);
+  for (cudaStream_t s : p->ovl_stream)
+    if (s) cudaStreamDestroy(s);
   for (void* q : p->allocs) cudaFree(q);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   delete p;
@@ -1296,10 +1383,16 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
       cudaGraph_t g = nullptr;
       PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
       const long long before = p->launches;
-      r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
+      if (!p->ovl_ev.empty()) {
+        // two half-batches in two branches; pass k of the second waits for pass
+        // k of the first, so their column and row passes run side by side
+        r = overlapped_iteration(p, st, y, (const float2*)t, P, corr_tol);
+      } else {
+        r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
+      }
       p->graph_kernels = p->launches - before;
       p->launches = before;
-      cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
+      cudaError_t ce = cudaStreamEndCapture(p->capture_stream, &g);
       p->stream = user;
       if (r) {
         if (g) cudaGraphDestroy(g);

@@ -21,6 +21,7 @@ FLAG_NO_PRECOND = 0x1
 FLAG_NO_REG = 0x2
 FLAG_PLAIN = 0x4
 FLAG_NO_TUNE = 0x8
+FLAG_OVERLAP = 0x10
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
           4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE"}
