@@ -44,6 +44,10 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
       standard normal (k1 = 1, 3, 5 per axis, K = k1^2); a node n walks the
       pattern by sigma n pixels at the detector, i.e. a tilt of
       sigma n p / (lambda (L1 + L2)) cycles/m, rounded to whole bins.
+  R14 Calibration (Methods): g2 is the circular, line-averaged intensity
+      autocorrelation over the squared mean; the Gaussian model is fitted in
+      log space over lags 1..max_lag; the Wiener filter is IOTF/(IOTF^2 + eps);
+      negative deconvolved intensities are clipped before the square root.
 """
 from __future__ import annotations
 
@@ -451,3 +455,48 @@ def modal_forward_vjp(psi, t, grad_f, geom: Geometry, modes):
         gt += 2.0 * w * np.conj(u1) * g2
         gp += 2.0 * w * np.conj(x * s) * FreePropagation(np.conj(t) * g2, geom, -geom.L1)
     return gp, gt
+
+
+# ----------------------------------------------------------------------------
+# Calibration from the reference speckle (Methods: "Intensity optical transfer
+# function (IOTF)" and "Diffuser transmission function")
+# ----------------------------------------------------------------------------
+# Readings (R14): g2 is the circular, line-averaged autocorrelation normalised
+# by the squared mean intensity; the Gaussian model g2 = 1 + A exp(-pi D^2 /
+# x_coh^2) is fitted by least squares on ln(g2 - 1) against D^2 over lags
+# 1..max_lag (lag 0 carries the shot-noise spike); the Wiener filter is
+# IOTF / (IOTF^2 + eps) with eps a noise-to-signal constant the caller picks;
+# negative deconvolved intensities are clipped to zero before the square root.
+def intensity_autocorrelation(I: np.ndarray, axis: int) -> np.ndarray:
+    """g2(D) = <I(r) I(r + D e_axis)> / <I>^2, averaged over all r (circular)."""
+    n = I.shape[axis]
+    ac = np.fft.ifft(np.abs(np.fft.fft(I, axis=axis)) ** 2, axis=axis).real / n
+    return ac.mean(axis=1 - axis) / np.mean(I) ** 2
+
+
+def fit_coherence_length(g2: np.ndarray, max_lag: int):
+    """(x_coh in pixels, A) of g2(D) - 1 = A exp(-pi D^2 / x_coh^2), D = 1..max_lag."""
+    lags = np.arange(1, max_lag + 1, dtype=np.float64)
+    z = np.log(np.clip(g2[1:max_lag + 1] - 1.0, 1e-300, None))
+    slope, intercept = np.polyfit(lags * lags, z, 1)
+    return float(np.sqrt(-np.pi / slope)), float(np.exp(intercept))
+
+
+def calibrate_coherence(I_ref: np.ndarray, pixel: float, max_lag: int):
+    """(x_coh, y_coh) in metres from the reference speckle."""
+    xc, _ = fit_coherence_length(intensity_autocorrelation(I_ref, 1), max_lag)
+    yc, _ = fit_coherence_length(intensity_autocorrelation(I_ref, 0), max_lag)
+    return xc * pixel, yc * pixel
+
+
+def wiener_deconvolve(I: np.ndarray, geom: Geometry, eps: float) -> np.ndarray:
+    """Re Filter(I, IOTF / (IOTF^2 + eps))."""
+    W = iotf(geom)
+    return Filter(I, W / (W * W + eps)).real
+
+
+def diffuser_from_reference(I_ref: np.ndarray, geom: Geometry, eps: float) -> np.ndarray:
+    """t = P(-L2){ sqrt(max(I_coh, 0)) } with I_coh the Wiener-deconvolved
+    reference speckle and its phase set to zero at the detector."""
+    I_coh = np.clip(wiener_deconvolve(I_ref, geom, eps), 0.0, None)
+    return FreePropagation(np.sqrt(I_coh), geom, -geom.L2)

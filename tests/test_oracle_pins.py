@@ -405,3 +405,46 @@ def test_without_preconditioner_the_phase_is_underestimated():
     rms = lambda a: float(np.sqrt(np.mean((a.imag - a.imag.mean()) ** 2)))  # noqa: E731
     assert rms(psi) < 0.1 * rms(with_p)
     assert rms(with_p) > 0.2 * rms(psi_true)
+
+
+# ----------------------------------------------------------------------------
+# Calibration (Methods: IOTF from the reference speckle; diffuser)
+# ----------------------------------------------------------------------------
+def _gaussian_speckle(n, xc_px, seed):
+    """Fully developed speckle whose field has the power spectrum
+    exp(-2 pi xc^2 u^2): then |g1(D)|^2 = exp(-pi D^2 / xc^2) exactly in the
+    ensemble (Siegert: g2 = 1 + |g1|^2)."""
+    rng = np.random.default_rng(seed)
+    u = np.fft.fftfreq(n)
+    A = np.exp(-np.pi * xc_px ** 2 * (u[:, None] ** 2 + u[None, :] ** 2))
+    E = np.fft.ifft2(A * np.exp(2j * np.pi * rng.uniform(size=(n, n))))
+    return np.abs(E) ** 2
+
+
+def test_autocorrelation_fit_recovers_the_coherence_length():
+    I = _gaussian_speckle(512, 4.0, 3)
+    g2x = O.intensity_autocorrelation(I, 1)
+    assert abs(g2x[0] - 2.0) < 0.05                      # fully developed: <I^2>/<I>^2 = 2
+    # lags 1..3: beyond them g2 - 1 < 0.05 and the +-0.01 baseline fluctuation of
+    # one 512^2 realisation dominates the logarithm
+    xc, A = O.fit_coherence_length(g2x, 3)
+    assert abs(xc - 4.0) < 0.16 and abs(A - 1.0) < 0.1
+    xcm, ycm = O.calibrate_coherence(I, 1e-6, 3)
+    assert abs(xcm - 4e-6) < 0.16e-6 and abs(ycm - 4e-6) < 0.16e-6
+    # brute-force autocorrelation on a small image
+    J = _gaussian_speckle(16, 2.0, 4)
+    bf = np.array([np.mean(J * np.roll(J, -d, axis=1)) for d in range(16)]) / np.mean(J) ** 2
+    assert np.max(np.abs(O.intensity_autocorrelation(J, 1) - bf)) < 1e-12
+
+
+def test_wiener_inverts_a_noise_free_blur_and_the_diffuser_reproduces_the_reference():
+    n = 64
+    g = O.Geometry(n, n, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4, 3e-6, 3.5e-6)
+    t_true = S.diffuser(n, n, S.rng_for(1, 6))
+    I_coh = np.abs(O.FreePropagation(t_true, g, g.L2)) ** 2     # coherent reference speckle
+    I_ref = O.Filter(I_coh, O.iotf(g)).real                     # partial coherence (Eq. (1), no sample)
+    assert np.max(np.abs(O.wiener_deconvolve(I_ref, g, 1e-14) - I_coh)) < 1e-8
+    t = O.diffuser_from_reference(I_ref, g, 1e-14)
+    v = O.FreePropagation(t, g, g.L2)
+    assert np.max(np.abs(np.abs(v) ** 2 - I_coh)) < 1e-7         # reproduces the reference
+    assert np.max(np.abs(v.imag)) < 1e-7                         # zero phase at the detector
