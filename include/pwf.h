@@ -180,6 +180,22 @@ pwf_status pwf_group_solve(pwf_group* group, void* stream, const float* const* y
                            void* const* psi, int32_t max_iter, double corr_tol);
 pwf_status pwf_group_read(pwf_group* group, int32_t index, double* loss_host, int32_t* iters_host);
 
+/* Calibration from the reference speckle I_ref (float32 [ny][nx], device; the
+ * plan's first projection slot is used as workspace), Methods "Intensity
+ * optical transfer function (IOTF)" and "Diffuser transmission function".
+ * pwf_calibrate_coherence: normalised intensity autocorrelation along x and
+ * along y (circular, averaged over the other axis; Siegert relation), Gaussian
+ * model g2 = 1 + A exp(-pi D^2 / coh^2) fitted by least squares on
+ * ln(g2 - 1) over lags 1..max_lag; HOST outputs x_coh, y_coh in metres.
+ * Synchronises. PWF_ERR_NONFINITE if g2 - 1 is not positive and decreasing
+ * over the lags. pwf_diffuser_from_reference: I_coh = Re Filter(I_ref,
+ * IOTF/(IOTF^2 + wiener_eps)) with the plan's IOTF, then
+ * t = P(-L2){sqrt(max(I_coh, 0))} (phase zero at the detector); t_out is
+ * complex64 [ny][nx] device memory. */
+pwf_status pwf_calibrate_coherence(pwf_plan* plan, const float* I_ref, int32_t max_lag, double* xcoh_m_host,
+                                   double* ycoh_m_host);
+pwf_status pwf_diffuser_from_reference(pwf_plan* plan, const float* I_ref, double wiener_eps, void* t_out);
+
 /* Checkpoint: pwf_state_bytes gives the size of a host buffer that holds the
  * state (phi and the counters); save/load copy it. Loading into a state of a
  * plan with other sizes returns PWF_ERR_STATE. Both synchronise. */

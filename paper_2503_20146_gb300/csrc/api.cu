@@ -130,7 +130,7 @@ __global__ void k_batch_sum(const float2* __restrict__ s, float2* __restrict__ o
 }
 
 // ---- unfused per-operation kernels (the plain baseline) ----
-enum PlainFilter : int { PF_Q = 0, PF_IOTF = 1, PF_PINV = 2, PF_GAMMA2 = 3 };
+enum PlainFilter : int { PF_Q = 0, PF_IOTF = 1, PF_PINV = 2, PF_GAMMA2 = 3, PF_WIENER = 4 };
 
 __global__ void k_exp(const float2* __restrict__ psi, float2* __restrict__ x, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -138,7 +138,7 @@ __global__ void k_exp(const float2* __restrict__ psi, float2* __restrict__ x, si
 }
 __global__ void k_filter(float2* X, int ny, int nx, int which, const float2* qx, const float2* qy, int conj,
                          const float* ix, const float* iy, const float* u2x, const float* u2y, const float* ex,
-                         const float* ey, int no_precond) {
+                         const float* ey, int no_precond, float wiener_eps = 0.f) {
   const size_t n = (size_t)ny * nx;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int kx = (int)(i % nx), ky = (int)(i / nx);
@@ -149,6 +149,9 @@ __global__ void k_filter(float2* X, int ny, int nx, int which, const float2* qx,
       v = cmul(v, q);
     } else if (which == PF_IOTF) {
       v = cscale(v, ix[kx] * iy[ky]);
+    } else if (which == PF_WIENER) {
+      const float w = ix[kx] * iy[ky];
+      v = cscale(v, w / fmaf(w, w, wiener_eps));
     } else if (which == PF_PINV) {
       const float r2 = u2x[kx] + u2y[ky];
       v = cscale(v, no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f));
@@ -205,6 +208,43 @@ __global__ void k_copy(const float2* __restrict__ a, float2* b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
+// ---- calibration helpers ----
+__global__ void k_real_to_complex(const float* __restrict__ I, float2* X, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = make_float2(I[i], 0.f);
+}
+__global__ void k_abs2_scale(float2* X, size_t n, float s) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = make_float2(cabs2(X[i]) * s, 0.f);
+}
+__global__ void k_sqrt_clip(float2* X, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = make_float2(sqrtf(fmaxf(X[i].x, 0.f)), 0.f);
+}
+// out[d] = mean over the other axis of Re X at lag d (axis 1: X[y][d]; axis 0: X[d][x])
+__global__ void k_line_mean(const float2* __restrict__ X, int ny, int nx, int axis, double* out) {
+  const int lag = blockIdx.x;
+  const int n_other = axis == 1 ? ny : nx;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n_other; k += blockDim.x)
+    s += axis == 1 ? (double)X[(size_t)k * nx + lag].x : (double)X[(size_t)lag * nx + k].x;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    out[lag] = t / n_other;
+  }
+}
+__global__ void k_mean(const float* __restrict__ I, size_t n, double* out) {
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) s += I[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s / (double)n);
+}
+
 // g = (Re g + i Re Filter(Im g, P^-1)) + (Re a Re rho + i Im a Im rho); Nesterov.
 __global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __restrict__ S,
                                  const float2* __restrict__ H, float2* psi, float2* phi, size_t n, float eta,
@@ -271,6 +311,7 @@ struct pwf_plan {
   pwf_plan_desc d{};
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
+  double* calib = nullptr;               // calibration sums, nx + ny + 1 (allocated on first use)
   const LengthKernels* krow = nullptr;  // length nx
   const LengthKernels* kcol = nullptr;  // length ny
   int colsel[NUM_COL_OPS] = {0, 0, 0, 0, 0, 0};  // chosen column-pass shape per op
@@ -1659,6 +1700,83 @@ pwf_status pwf_group_read(pwf_group* g, int32_t index, double* loss_host, int32_
   pwf_plan* p = g->plans[index];
   if (!p->solve_state) return PWF_ERR_STATE;
   return pwf_state_read(p, p->solve_state, loss_host, nullptr, iters_host, nullptr);
+}
+
+pwf_status pwf_calibrate_coherence(pwf_plan* p, const float* I_ref, int32_t max_lag, double* xcoh_m,
+                                   double* ycoh_m) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  const int ny = p->d.ny, nx = p->d.nx;
+  if (!I_ref || !xcoh_m || !ycoh_m || max_lag < 1 || max_lag >= nx / 2 || max_lag >= ny / 2)
+    return PWF_ERR_INVALID_ARG;
+  const size_t n = (size_t)ny * nx;
+  if (!p->calib && (r = dalloc(p, &p->calib, (size_t)nx + ny + 1))) return r;  // released with the plan
+  double* d = p->calib;
+  PWF_CUDA(p, cudaMemsetAsync(d, 0, sizeof(double) * (nx + ny + 1), p->stream));
+  const int G = grid_for(n);
+  k_mean<<<G, 256, 0, p->stream>>>(I_ref, n, d + nx + ny);
+  PassArgs a = base_args(p);
+  a.proj0 = 0;
+  a.in = p->X;
+  a.out = p->X;
+  for (int axis = 1; axis >= 0; axis--) {  // along x (rows), then along y (columns)
+    k_real_to_complex<<<G, 256, 0, p->stream>>>(I_ref, p->X, n);
+    const int len = axis == 1 ? nx : ny;
+    if (axis == 1) {
+      LAUNCH(p, row(p, ROW_FFT, a, 1));
+      k_abs2_scale<<<G, 256, 0, p->stream>>>(p->X, n, 1.0f / ((float)len * (float)len));
+      LAUNCH(p, row(p, ROW_IFFT, a, 1));
+    } else {
+      LAUNCH(p, col(p, COL_FFT, a, 1));
+      k_abs2_scale<<<G, 256, 0, p->stream>>>(p->X, n, 1.0f / ((float)len * (float)len));
+      PassArgs b = a;
+      b.scale = 1.0f;
+      LAUNCH(p, col(p, COL_IFFT, b, 1));
+    }
+    k_line_mean<<<len, 256, 0, p->stream>>>(p->X, ny, nx, axis, d + (axis == 1 ? 0 : nx));
+    PWF_CUDA(p, cudaGetLastError());
+  }
+  std::vector<double> h((size_t)nx + ny + 1);
+  PWF_CUDA(p, cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  const double m2 = h[nx + ny] * h[nx + ny];
+  // least squares of ln(g2 - 1) against D^2 over D = 1..max_lag (reading of Methods)
+  auto fit = [&](const double* g, double* out) -> bool {
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int k = 1; k <= max_lag; k++) {
+      const double g2 = g[k] / m2 - 1.0;
+      if (!(g2 > 0)) return false;
+      const double x = (double)k * k, yv = std::log(g2);
+      sx += x, sy += yv, sxx += x * x, sxy += x * yv;
+    }
+    const double m = max_lag, slope = (m * sxy - sx * sy) / (m * sxx - sx * sx);
+    if (!(slope < 0)) return false;
+    *out = std::sqrt(-M_PI / slope) * p->d.pixel_m;
+    return true;
+  };
+  if (!fit(h.data(), xcoh_m) || !fit(h.data() + nx, ycoh_m))
+    return fail(p, PWF_ERR_NONFINITE, "autocorrelation not decreasing over the fitted lags");
+  return PWF_OK;
+}
+
+pwf_status pwf_diffuser_from_reference(pwf_plan* p, const float* I_ref, double wiener_eps, void* t_out) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!I_ref || !t_out || !(wiener_eps >= 0)) return PWF_ERR_INVALID_ARG;
+  const size_t n = (size_t)p->d.ny * p->d.nx;
+  const int G = grid_for(n);
+  k_real_to_complex<<<G, 256, 0, p->stream>>>(I_ref, p->X, n);
+  PWF_CUDA(p, cudaGetLastError());
+  if ((r = plain_fft2(p, p->X, 0, false))) return r;
+  k_filter<<<G, 256, 0, p->stream>>>(p->X, p->d.ny, p->d.nx, PF_WIENER, nullptr, nullptr, 0, p->ax.iotf, p->ay.iotf,
+                                     nullptr, nullptr, nullptr, nullptr, 0, (float)wiener_eps);
+  PWF_CUDA(p, cudaGetLastError());
+  if ((r = plain_fft2(p, p->X, 0, true))) return r;
+  k_sqrt_clip<<<G, 256, 0, p->stream>>>(p->X, n);
+  PWF_CUDA(p, cudaGetLastError());
+  if ((r = plain_filter(p, p->X, 0, PF_Q, 2, 1))) return r;  // back over L2
+  PWF_CUDA(p, cudaMemcpyAsync(t_out, p->X, n * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
+  return PWF_OK;
 }
 
 size_t pwf_state_bytes(const pwf_state* s) {

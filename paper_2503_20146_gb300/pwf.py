@@ -102,6 +102,8 @@ def load(path: str | None = None):
         "pwf_group_destroy": ([_P], i32),
         "pwf_group_solve": ([_P, _P, _P, _P, _P, i32, f64], i32),
         "pwf_group_read": ([_P, i32, _P, _P], i32),
+        "pwf_calibrate_coherence": ([_P, _P, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)], i32),
+        "pwf_diffuser_from_reference": ([_P, _P, f64, _P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -342,6 +344,21 @@ def pwf_group_read(group, index: int, batch: int):
     return loss, iters
 
 
+def pwf_calibrate_coherence(plan, I_ref, max_lag: int):
+    """(x_coh, y_coh) in metres from the reference speckle I_ref (float32 [ny][nx])."""
+    xc, yc = ctypes.c_double(), ctypes.c_double()
+    _on_current_stream(plan)
+    _check(load().pwf_calibrate_coherence(plan, _ptr(I_ref), int(max_lag), ctypes.byref(xc), ctypes.byref(yc)),
+           "pwf_calibrate_coherence", plan)
+    return xc.value, yc.value
+
+
+def pwf_diffuser_from_reference(plan, I_ref, wiener_eps: float, t_out):
+    _on_current_stream(plan)
+    _check(load().pwf_diffuser_from_reference(plan, _ptr(I_ref), float(wiener_eps), _ptr(t_out)),
+           "pwf_diffuser_from_reference", plan)
+
+
 def pwf_status_string(status: int) -> str:
     return load().pwf_status_string(int(status)).decode()
 
@@ -418,6 +435,16 @@ class Plan:
 
     def reset(self):
         pwf_state_reset(self.handle, self.state)
+
+    def calibrate_coherence(self, I_ref, max_lag=3):
+        return pwf_calibrate_coherence(self.handle, I_ref, max_lag)
+
+    def diffuser_from_reference(self, I_ref, wiener_eps, t_out=None):
+        import torch
+        if t_out is None:
+            t_out = torch.empty(I_ref.shape, dtype=torch.complex64, device=I_ref.device)
+        pwf_diffuser_from_reference(self.handle, I_ref, wiener_eps, t_out)
+        return t_out
 
     def read(self):
         return pwf_state_read(self.handle, self.state, self.desc.batch)
