@@ -48,6 +48,14 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
       autocorrelation over the squared mean; the Gaussian model is fitted in
       log space over lags 1..max_lag; the Wiener filter is IOTF/(IOTF^2 + eps);
       negative deconvolved intensities are clipped before the square root.
+  R16 Joint diffuser refinement (Methods, "Diffuser transmission function",
+      and Fig. S12: t shared by, and updated across, all projections). The
+      update rule is not printed. Reading: after each iteration of Algorithm S1
+      over the whole series, t <- t - eta_t sum_b g_t,b, a plain gradient step
+      (no preconditioner, no momentum) with g_t the Wirtinger derivative of
+      the loss w.r.t. conj(t) in Algorithm S2's normalisation (factor 2
+      dropped, divided by max|t|^2 of the current t), evaluated at the same
+      point as the sample gradient. Fixed iteration count (no stopping rule).
 """
 from __future__ import annotations
 
@@ -295,6 +303,49 @@ def forward_vjp(psi, t, grad_f, geom: Geometry):
     g2 = FreePropagation(v * G, geom, -geom.L2)
     grad_t = 2.0 * np.conj(u1) * g2
     return grad_psi, grad_t
+
+
+def diffuser_gradient(psi, t, y, geom: Geometry):
+    """g_t = conj(P1{x}) P2^H{ v Filter(-e, IOTF) } / max|t|^2 (reading R16):
+    the diffuser counterpart of WirtingerDerivative, so that the gradient of
+    the loss in the dL/dRe t + i dL/dIm t convention is 4 max|t|^2 g_t."""
+    f, x, v = PhysicalModel(psi, t, geom)
+    e = y - f
+    G = Filter(-e, iotf(geom)).real                # R5
+    g2 = FreePropagation(v * G, geom, -geom.L2)
+    u1 = FreePropagation(x, geom, geom.L1)
+    return np.conj(u1) * g2 / np.max(np.abs(t) ** 2)
+
+
+@dataclass
+class JointResult:
+    psi: np.ndarray       # [B][ny][nx]
+    t: np.ndarray         # refined diffuser
+    losses: list          # total loss of the series at the start of each iteration
+
+
+def joint_pwf(y_b, t0, geom: Geometry, max_iter: int, eta_t: float) -> JointResult:
+    """Algorithm S1 over a series of projections that share the diffuser, with
+    t refined after every iteration (reading R16)."""
+    B = len(y_b)
+    psi = np.zeros((B, geom.ny, geom.nx), np.complex128)
+    phi = np.zeros_like(psi)
+    mu = 1.0
+    t = np.asarray(t0, np.complex128).copy()
+    Pinv, Gamma2 = precond_filter(geom), reg_window(geom)
+    losses = []
+    for _ in range(max_iter):
+        gt = np.zeros_like(t)
+        total = 0.0
+        mu_next = mu
+        for b in range(B):
+            gt = gt + diffuser_gradient(psi[b], t, y_b[b], geom)
+            psi[b], phi[b], mu_next, L = pwf_iteration(psi[b], phi[b], mu, y_b[b], t, geom, Pinv, Gamma2)
+            total += L
+        mu = mu_next
+        t = t - eta_t * gt
+        losses.append(total)
+    return JointResult(psi, t, losses)
 
 
 # ----------------------------------------------------------------------------

@@ -448,3 +448,46 @@ def test_wiener_inverts_a_noise_free_blur_and_the_diffuser_reproduces_the_refere
     v = O.FreePropagation(t, g, g.L2)
     assert np.max(np.abs(np.abs(v) ** 2 - I_coh)) < 1e-7         # reproduces the reference
     assert np.max(np.abs(v.imag)) < 1e-7                         # zero phase at the detector
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_diffuser_gradient_matches_central_differences(coherent):
+    # dL/dRe t + i dL/dIm t = 4 max|t|^2 g_t (the normalisation of Algorithm S2)
+    rng, g, psi, t, y = _fd_case(seed=21, coherent=coherent)
+    gt = 4.0 * np.max(np.abs(t) ** 2) * O.diffuser_gradient(psi, t, y, g)
+    for _ in range(3):
+        d = crandn(rng, t.shape)
+        an = np.sum(gt.real * d.real + gt.imag * d.imag)
+        eps = 1e-6
+        Lp = O.loss(y, O.PhysicalModel(psi, t + eps * d, g)[0])
+        Lm = O.loss(y, O.PhysicalModel(psi, t - eps * d, g)[0])
+        assert abs((Lp - Lm) / (2 * eps) - an) <= 1e-7 * abs(an)
+
+
+def _joint_case(n=32, B=3):
+    w = S.WORKLOADS["blob512_iotf"]
+    g = O.Geometry(n, n, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m, w.gamma, w.alpha, w.eta)
+    t = S.diffuser(n, n, S.rng_for(w.config, 99))
+    psi_true = np.stack([S.complex_phase_from(S.blob_phase(n, n, S.rng_for(w.config, b))) for b in range(B)])
+    f = O.physical_model_batch(psi_true, t, g)
+    y = np.stack([S.poisson_measurement(f[b], 1e4, S.rng_for(w.config, 50 + b)) for b in range(B)])
+    return g, t, y
+
+
+def test_joint_refinement_with_zero_step_is_algorithm_s1_per_projection():
+    g, t, y = _joint_case()
+    r = O.joint_pwf(y, t, g, 6, 0.0)
+    plain = O.pwf_batch(y, t, g, 6)
+    for b in range(len(y)):
+        assert np.max(np.abs(r.psi[b] - plain[b].psi)) < 1e-12
+    assert np.array_equal(r.t, t)
+    assert abs(r.losses[0] - sum(p.losses[0] for p in plain)) < 1e-9 * r.losses[0]
+
+
+def test_joint_refinement_lowers_the_loss_from_a_perturbed_diffuser():
+    g, t, y = _joint_case(n=48, B=3)
+    t0 = t * np.exp(0.3j * np.angle(S.diffuser(48, 48, np.random.default_rng(5))))
+    fixed = O.joint_pwf(y, t0, g, 25, 0.0)
+    joint = O.joint_pwf(y, t0, g, 25, 3e-3)
+    assert joint.losses[-1] < 0.97 * fixed.losses[-1]
+    assert not np.array_equal(joint.t, t0)
