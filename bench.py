@@ -361,6 +361,29 @@ def run_autograd(P, S, torch, dev, stream, reps=3):
     return out
 
 
+def run_fbp(P, S, torch, dev, stream, psi, w, reps=3):
+    """Tomography after the path: filtered back projection (Ram-Lak, one slice
+    per detector row) of the retrieved series into a ny x nx x nx volume."""
+    n_ang, ny, nx = psi.shape
+    angles = S.tomo_angles(n_ang)
+    vol = torch.empty((ny, nx, nx), dtype=torch.complex64, device=dev)
+    ws = torch.empty(P.pwf_fbp_workspace_bytes(n_ang, ny, nx), dtype=torch.uint8, device=dev)
+    P.pwf_fbp(psi, angles, w.wavelength_m, w.pixel_m, vol, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        P.pwf_fbp(psi, angles, w.wavelength_m, w.pixel_m, vol, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    updates = float(n_ang) * ny * nx * nx
+    out = {"ms": ms, "voxel_angle_updates_per_s": updates / (ms / 1e3), "volume": [ny, nx, nx],
+           "angles": n_ang, "note": "includes the host-side ramp and angle tables (synchronous copies)"}
+    del vol, ws
+    return out
+
+
 # ----------------------------------------------------------------------------
 # main arm
 # ----------------------------------------------------------------------------
@@ -520,6 +543,17 @@ def main():
         # differentiation: 16 x 2048^2 forward + backward through torch.autograd
         if w.name == "tomo180x1024_iotf":
             extras["autograd_16x2048"] = run_autograd(P, S, torch, dev, stream)
+
+        # tomography after the path: FBP of the retrieved series
+        if w.name == "tomo180x1024_iotf":
+            extras["fbp_180x1024"] = run_fbp(P, S, torch, dev, stream, psi, w)
+
+        # ablations on a small synthetic series (preconditioner, gamma, alpha): PWF + FBP + scores
+        if w.name == "tomo180x1024_iotf":
+            from paper_2503_20146_gb300 import ablation as A
+            series = A.make_series(n_angles=32, n=128)
+            extras["ablation_32x128"] = {"iterations": 150, "rows": A.run_ablation(series, iters=150)}
+            del series
 
         # FP64 oracle on the host cores, bounded sample
         dt, work = oracle_sample(w, 1, 3)

@@ -163,6 +163,19 @@ pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_h
 pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
                      double corr_tol, int32_t* iters_host, double* loss_host);
 
+/* Joint refinement of the shared diffuser (Methods, "Diffuser transmission
+ * function", and Fig. S12: t is updated across all projections). Runs
+ * max_iter iterations of Algorithm S1 over the batch (no stopping rule) and,
+ * after each, t <- t - eta_t sum_b g_t,b with g_t = conj(P1{x})
+ * P2^H{v Filter(-e, IOTF)} / max|t|^2 evaluated at the same point as the
+ * sample gradient (a plain gradient step; max|t|^2 is recomputed from the new
+ * t). t (complex64 [ny][nx], device) is updated in place, as is psi.
+ * eta_t = 0 reproduces pwf_solve with corr_tol = 0. Keeps B extra fields of
+ * workspace (allocated on the first call). PWF_ERR_UNSUPPORTED for source-mode,
+ * plain or overlapped plans; PWF_ERR_INVALID_ARG if eta_t < 0. */
+pwf_status pwf_solve_joint(pwf_plan* plan, const float* y, void* t, void* psi, int32_t max_iter, double eta_t,
+                           int32_t* iters_host, double* loss_host);
+
 /* Groups: batches of mixed sizes. One plan per size class (each with its own
  * sizes, batch, coherence model and tuned column shapes) joined in a group and
  * solved together: pwf_group_solve runs Algorithm S1 on every class, one CUDA
@@ -195,6 +208,33 @@ pwf_status pwf_group_read(pwf_group* group, int32_t index, double* loss_host, in
 pwf_status pwf_calibrate_coherence(pwf_plan* plan, const float* I_ref, int32_t max_lag, double* xcoh_m_host,
                                    double* ycoh_m_host);
 pwf_status pwf_diffuser_from_reference(pwf_plan* plan, const float* I_ref, double wiener_eps, void* t_out);
+
+/* Filtered back projection after PWF (Methods, "Reconstruction procedure"):
+ * standard parallel-beam FBP with the Ram-Lak filter, one slice per detector
+ * row, then the factor -lambda / (2 pi p), which turns the retrieved
+ * psi = -k int beta - i k int delta into beta + i delta.
+ *   psi      complex64 [n_angles][ny][nx], device; detector pixel j sits at
+ *            s = j - nx/2 + 1/2 pixels from the rotation axis
+ *   angles_rad_host  n_angles projection angles (host), normally [0, pi)
+ *   vol_out  complex64 [ny][nx][nx], device: slice y, row z (beam direction at
+ *            angle 0), column x; Re = beta, Im = delta
+ *   workspace  device memory of pwf_fbp_workspace_bytes(...) bytes, 256-byte
+ *            aligned (filtered rows, filter and angle tables)
+ *   stream   cudaStream_t (null: legacy default stream)
+ * Ram-Lak: h(0) = 1/4, h(k) = -1/(pi^2 k^2) for odd k, 0 otherwise (unit
+ * sampling); linear convolution along the row (zero padding to 2 nx); back
+ * projection f = (pi / n_angles) sum_a q_a(x cos theta_a + z sin theta_a) with
+ * linear interpolation, zero outside the detector. Sizes: 1 <= n_angles <=
+ * PWF_FBP_MAX_ANGLES, ny <= 65535, 2 nx one of 32, 64, 96, 128, 192, 256, 384,
+ * 512, 768, 1024, 1536, 2048; otherwise PWF_ERR_INVALID_ARG (workspace_bytes
+ * returns 0).
+ * The tables are copied from the host synchronously on the stream; the two
+ * kernels are then enqueued asynchronously. */
+#define PWF_FBP_MAX_ANGLES 4096
+size_t pwf_fbp_workspace_bytes(int32_t n_angles, int32_t ny, int32_t nx);
+pwf_status pwf_fbp(const void* psi, int32_t n_angles, int32_t ny, int32_t nx, const double* angles_rad_host,
+                   double wavelength_m, double voxel_m, void* vol_out, void* workspace, size_t workspace_bytes,
+                   void* stream);
 
 /* Checkpoint: pwf_state_bytes gives the size of a host buffer that holds the
  * state (phi and the counters); save/load copy it. Loading into a state of a

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/pwf.h"
+#include "host_tables.h"
 #include "passes.cuh"
 
 namespace pwf {
@@ -126,6 +127,19 @@ __global__ void k_batch_sum(const float2* __restrict__ s, float2* __restrict__ o
     float2 a = make_float2(0.f, 0.f);
     for (int b = 0; b < B; b++) a = cadd(a, s[(size_t)b * n + i]);
     out[i] = a;
+  }
+}
+
+// t <- t - (eta_t / (2 max|t|^2)) sum_b s_b; s_b = 2 conj(P1{x_b}) P2^H{v_b G_b}
+// (the per-projection terms of the diffuser-gradient pass), i.e. a plain step
+// along the batch sum of g_t in Algorithm S2's normalisation
+__global__ void k_t_update(float2* t, const float2* __restrict__ s, int B, size_t n, float eta_t,
+                           const float* __restrict__ maxt2) {
+  const float c = eta_t / (2.0f * *maxt2);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int b = 0; b < B; b++) a = cadd(a, s[(size_t)b * n + i]);
+    t[i] = make_float2(fmaf(-c, a.x, t[i].x), fmaf(-c, a.y, t[i].y));
   }
 }
 
@@ -273,6 +287,26 @@ __global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __
   }
 }
 
+// Twiddle table of the length-n transform in direction D, in the layout the
+// stage runner reads (stage k >= 1 of radix R after NS points: W^(r j) at
+// stage_twoff + (r - 1) NS + j), computed in double precision.
+bool host_twiddles(int n, int D, std::vector<float2>& tab) {
+  tab.assign(twiddle_len(n, D) > 0 ? twiddle_len(n, D) : 1, make_float2(1.f, 0.f));
+  const Sched s = sched_for(n);
+  for (int k = 1; k < s.s; k++) {
+    const int R = stage_radix(n, D, k), NS = stage_ns(n, D, k), off = stage_twoff(n, D, k);
+    for (int r = 1; r < R; r++)
+      for (int j = 0; j < NS; j++) {
+        const long m = ((long)r * j) % ((long)NS * R);
+        const double ang = 2.0 * M_PI * (double)m / (double)(NS * R);
+        const size_t idx = (size_t)off + (size_t)(r - 1) * NS + j;
+        if (idx >= tab.size()) return false;
+        tab[idx] = make_float2((float)std::cos(ang), (float)(D * std::sin(ang)));
+      }
+  }
+  return true;
+}
+
 }  // namespace pwf
 
 using namespace pwf;
@@ -339,6 +373,8 @@ struct pwf_plan {
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   double graph_tol = 0.0;
+  double graph_eta_t = -1.0;  // joint diffuser step of the captured graph (< 0: t fixed)
+  float2* GT = nullptr;       // per-projection diffuser-gradient terms (joint refinement)
   pwf_status sticky = PWF_OK;
   char err[256] = "";
   // overlap of two half-batches (PWF_FLAG_OVERLAP): the projection range of
@@ -409,25 +445,10 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
   A.n = n;
   const pwf_plan_desc& d = p->d;
   // the inverse runs the radices in reverse order, so its table length differs
-  const int tlf = twiddle_len(n, FWD) > 0 ? twiddle_len(n, FWD) : 1;
-  const int tli = twiddle_len(n, INV) > 0 ? twiddle_len(n, INV) : 1;
-  std::vector<float2> twf(tlf, make_float2(1.f, 0.f)), twi(tli, make_float2(1.f, 0.f));
-  const Sched s = sched_for(n);
-  for (int dir = 0; dir < 2; dir++) {
-    const int D = dir == 0 ? FWD : INV;
-    for (int k = 1; k < s.s; k++) {
-      const int R = stage_radix(n, D, k), NS = stage_ns(n, D, k), off = stage_twoff(n, D, k);
-      std::vector<float2>& tab = dir == 0 ? twf : twi;
-      for (int r = 1; r < R; r++)
-        for (int j = 0; j < NS; j++) {
-          const long m = ((long)r * j) % ((long)NS * R);
-          const double ang = 2.0 * M_PI * (double)m / (double)(NS * R);
-          const size_t idx = (size_t)off + (size_t)(r - 1) * NS + j;
-          if (idx >= tab.size()) return fail(p, PWF_ERR_UNSUPPORTED, "twiddle table layout");
-          tab[idx] = make_float2((float)std::cos(ang), (float)(D * std::sin(ang)));
-        }
-    }
-  }
+  std::vector<float2> twf, twi;
+  if (!host_twiddles(n, FWD, twf) || !host_twiddles(n, INV, twi))
+    return fail(p, PWF_ERR_UNSUPPORTED, "twiddle table layout");
+  const int tlf = (int)twf.size(), tli = (int)twi.size();
   std::vector<float2> q1(n), q2(n), cs(n);
   std::vector<float> io(n), u2(n), st(n);
   for (int k = 0; k < n; k++) {
@@ -593,14 +614,15 @@ pwf_status fused_to_detector(pwf_plan* p, PassArgs a, const float2* psi, const f
 }
 
 // X holds the row spectrum of w = v G; back-propagate: P2^H, conj(t), P1^H.
-pwf_status fused_backprop(pwf_plan* p, PassArgs a, const float2* t, bool gradt, int nproj) {
+pwf_status fused_backprop(pwf_plan* p, PassArgs a, const float2* t, bool gradt, int nproj,
+                          float2* gt_scratch = nullptr) {
   a.in = p->X;
   a.out = p->X;
   a.t = t;
   LAUNCH(p, col_q(p, a, 2, 1, nproj));
   if (gradt) {
     a.u1 = p->S;
-    a.gt_scratch = p->YH;
+    a.gt_scratch = gt_scratch ? gt_scratch : p->YH;
     LAUNCH(p, row(p, ROW_GRADT, a, nproj));
     a.u1 = nullptr;
   } else {
@@ -736,7 +758,7 @@ pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
 
 // one fused iteration (or the body of pwf_step): X must hold F_row{exp psi}
 pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
-                           bool next_fft, double corr_tol) {
+                           bool next_fft, double corr_tol, float2* t_refine = nullptr, double eta_t = 0.0) {
   PassArgs a = base_args(p);
   a.active = st->active;
   a.beta = &st->it->beta;
@@ -768,7 +790,8 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
       }));
     return PWF_OK;
   }
-  r = fused_to_detector(p, a, psi, t, nullptr, false, nproj_of(p));
+  const bool joint = t_refine != nullptr;
+  r = fused_to_detector(p, a, psi, t, joint ? p->S : nullptr, false, nproj_of(p));  // u1 kept for g_t
   if (r) return r;
   a.in = p->X;
   a.out = p->X;
@@ -782,7 +805,7 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     LAUNCH(p, col(p, COL_RESID_IOTF2, a, nproj_of(p))); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
     LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v Filter(-e, IOTF)
   }
-  if ((r = fused_backprop(p, a, t, false, nproj_of(p)))) return r;
+  if ((r = fused_backprop(p, a, t, joint, nproj_of(p), p->GT))) return r;
   a.psi = psi;
   a.reg = p->REG;
   a.aux = p->S;
@@ -797,6 +820,17 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
       k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
       return cudaGetLastError();
     }));
+  if (joint) {
+    // joint refinement: step t along the batch sum of g_t (max|t|^2 of the
+    // t this iteration used), then max|t|^2 of the new t for the next one
+    const size_t n = (size_t)p->d.ny * p->d.nx;
+    LAUNCH(p, enqueue(p, "t_update", [&] {
+      k_t_update<<<grid_for(n), 256, 0, p->stream>>>(t_refine, p->GT, a.B, n, (float)eta_t, p->maxt2);
+      return cudaGetLastError();
+    }));
+    pwf_status rr = compute_maxt2(p, t_refine);
+    if (rr) return rr;
+  }
   return PWF_OK;
 }
 
@@ -1391,13 +1425,33 @@ pwf_status pwf_state_read(pwf_plan* p, const pwf_state* s, double* loss_host, do
   return PWF_OK;
 }
 
+static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* psi, int32_t max_iter,
+                             double corr_tol, int32_t* iters_host, double* loss_host, double eta_t);
+
 pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int32_t max_iter, double corr_tol,
                      int32_t* iters_host, double* loss_host) {
+  return solve_impl(p, y, t, psi, max_iter, corr_tol, iters_host, loss_host, -1.0);
+}
+
+pwf_status pwf_solve_joint(pwf_plan* p, const float* y, void* t, void* psi, int32_t max_iter, double eta_t,
+                           int32_t* iters_host, double* loss_host) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!(eta_t >= 0.0)) return PWF_ERR_INVALID_ARG;
+  if (!p->modes.empty() || (p->d.flags & (PWF_FLAG_PLAIN | PWF_FLAG_OVERLAP)))
+    return fail(p, PWF_ERR_UNSUPPORTED, "joint refinement runs the fused single-chain IOTF/coherent path");
+  return solve_impl(p, y, t, psi, max_iter, 0.0, iters_host, loss_host, eta_t);
+}
+
+static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* psi, int32_t max_iter,
+                             double corr_tol, int32_t* iters_host, double* loss_host, double eta_t) {
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
+  const bool joint = eta_t >= 0.0;
   if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
   if (!p->modes.empty() && (r = ensure_vstack(p))) return r;  // before the graph capture
+  if (joint && !p->GT && (r = dalloc(p, &p->GT, (size_t)p->d.batch * p->d.ny * p->d.nx))) return r;
   pwf_state* st = p->solve_state;
   if ((r = pwf_state_reset(p, st))) return r;
   float2* P = (float2*)psi;
@@ -1414,7 +1468,8 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
     LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
     // capture one fused iteration into a graph (re-captured when the operands change)
     const void* key[4] = {y, t, psi, p->stream};
-    if (!p->graph || std::memcmp(key, p->graph_key, sizeof(key)) != 0 || p->graph_tol != corr_tol) {
+    if (!p->graph || std::memcmp(key, p->graph_key, sizeof(key)) != 0 || p->graph_tol != corr_tol ||
+        p->graph_eta_t != (joint ? eta_t : -1.0)) {
       if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
@@ -1424,7 +1479,9 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
       cudaGraph_t g = nullptr;
       PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
       const long long before = p->launches;
-      if (!p->ovl_ev.empty()) {
+      if (joint) {
+        r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol, (float2*)t, eta_t);
+      } else if (!p->ovl_ev.empty()) {
         // two half-batches in two branches; pass k of the second waits for pass
         // k of the first, so their column and row passes run side by side
         r = overlapped_iteration(p, st, y, (const float2*)t, P, corr_tol);
@@ -1445,6 +1502,7 @@ pwf_status pwf_solve(pwf_plan* p, const float* y, const void* t, void* psi, int3
       if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaGraphInstantiate");
       std::memcpy(p->graph_key, key, sizeof(key));
       p->graph_tol = corr_tol;
+      p->graph_eta_t = joint ? eta_t : -1.0;
     }
     const int check_every = 16;
     for (int k = 0; k < max_iter; k++) {
@@ -1484,7 +1542,7 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   char tmp[2048];
   size_t o = 0;
   auto shape = [&](const ColVariant& v) {
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   };
   o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {

@@ -411,6 +411,96 @@ __device__ __forceinline__ void fft_run(float2 (&v)[ept_for(N)], const L& sm, in
   fft_stages<N, DIR, 0, L>(v, sm, t, tw);
 }
 
+// Two interleaved columns per thread (columns c and c + 1 of a ColLayout tile,
+// c even): the same stages on two transforms that share every index, twiddle
+// and barrier, with one 16-byte shared access per element pair.
+template <int C>
+struct ColPairLayout {
+  float2* base;  // offset by the even column c
+  __device__ __forceinline__ float4& operator[](int p) const {
+    return *reinterpret_cast<float4*>(base + col_row(p, C) * C);
+  }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+template <int N, int DIR, int K, int C>
+__device__ __forceinline__ void fft_stages2(float2 (&v)[ept_for(N)], float2 (&u)[ept_for(N)],
+                                            const ColPairLayout<C>& sm, int t, const float2* __restrict__ tw) {
+  constexpr Sched S = sched_for(N);
+  constexpr int EPT = ept_for(N);
+  constexpr int TPF = tpf_for(N);
+  constexpr int R = stage_radix(N, DIR, K);
+  constexpr int NS = stage_ns(N, DIR, K);
+  constexpr int NB = EPT / R;
+  constexpr bool LAST = (K + 1 == S.s);
+
+  if constexpr (K > 0) {
+    constexpr int OFF = stage_twoff(N, DIR, K);
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const float4 q = sm[b + r * (N / R)];
+        v[i * R + r] = make_float2(q.x, q.y);
+        u[i * R + r] = make_float2(q.z, q.w);
+      }
+    }
+    if constexpr (!LAST) sm.sync();
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+      const int k = b % NS;
+      float2 w[R];
+#pragma unroll
+      for (int r = 1; r < R; r++) {
+        if ((r & (r - 1)) == 0 || R == 3) {
+          w[r] = __ldg(&tw[OFF + (r - 1) * NS + k]);
+        } else {
+          const int hi = r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : 2;
+          w[r] = cmul(w[hi], w[r - hi]);
+        }
+      }
+#pragma unroll
+      for (int r = 1; r < R; r++) {
+        v[i * R + r] = cmul(v[i * R + r], w[r]);
+        u[i * R + r] = cmul(u[i * R + r], w[r]);
+      }
+      dft<R, DIR>(&v[i * R]);
+      dft<R, DIR>(&u[i * R]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      dft<R, DIR>(&v[i * R]);
+      dft<R, DIR>(&u[i * R]);
+    }
+  }
+
+  if constexpr (!LAST) {
+    if constexpr (K == 0) sm.sync();
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+      const int b = t + i * TPF;
+      const int k = b % NS;
+      const int base = (b / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const float2 a = v[i * R + r], c = u[i * R + r];
+        sm[base + r * NS] = make_float4(a.x, a.y, c.x, c.y);
+      }
+    }
+    sm.sync();
+    fft_stages2<N, DIR, K + 1, C>(v, u, sm, t, tw);
+  }
+}
+
+template <int N, int DIR, int C>
+__device__ __forceinline__ void fft_run2(float2 (&v)[ept_for(N)], float2 (&u)[ept_for(N)],
+                                         const ColPairLayout<C>& sm, int t, const float2* __restrict__ tw) {
+  fft_stages2<N, DIR, 0, C>(v, u, sm, t, tw);
+}
+
 // radix of the slot layout at the start / end of a transform
 template <int N, int DIR>
 __host__ __device__ constexpr int first_radix() { return stage_radix(N, DIR, 0); }

@@ -586,6 +586,147 @@ __host__ __device__ constexpr size_t colt_smem_bytes(int n, int c) {
   return 2 * (size_t)c * colt_stride(n) * sizeof(float2);
 }
 
+// Two columns per thread (the pair c, c + 1): tile staging as col_kernel_pipe,
+// then the transforms of both columns share indices, twiddles and barriers and
+// move through shared memory 16 bytes at a time. Single-input passes only.
+__host__ __device__ constexpr int col2_threads(int n, int c) { return c / 2 * tpf_for(n); }
+
+template <int N, int OP, class P>
+__device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int col, size_t base,
+                                                float2 (&v)[ept_for(N)], float2 (&u)[ept_for(N)], float (&part)[5]) {
+  constexpr int EPT = ept_for(N);
+  constexpr int RK = last_radix<N, FWD>();
+  const size_t ld = (size_t)a.nx;
+  if constexpr (OP == COL_Q) {
+    float2 qa = cscale(__ldg(&a.qx[col]), a.scale), qb = cscale(__ldg(&a.qx[col + 1]), a.scale);
+    if (a.conj_q) qa = cconj(qa), qb = cconj(qb);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      float2 qy = __ldg(&a.qy[slot_index<N, RK>(t, j)]);
+      if (a.conj_q) qy = cconj(qy);
+      v[j] = cmul(v[j], cmul(qa, qy));
+      u[j] = cmul(u[j], cmul(qb, qy));
+    }
+  } else if constexpr (OP == COL_IOTF) {
+    const float ia = __ldg(&a.ix[col]) * a.scale, ib = __ldg(&a.ix[col + 1]) * a.scale;
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float iy = __ldg(&a.iy[slot_index<N, RK>(t, j)]);
+      v[j] = cscale(v[j], ia * iy);
+      u[j] = cscale(u[j], ib * iy);
+    }
+  } else if constexpr (OP == COL_RESID_IOTF2) {
+    const float ia = __ldg(&a.ix[col]), ib = __ldg(&a.ix[col + 1]);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int ky = slot_index<N, RK>(t, j);
+      const float iy = __ldg(&a.iy[ky]);
+      const float4 yh = *reinterpret_cast<const float4*>(a.yhat + base + (size_t)ky * ld);
+      const float wa = ia * iy, wb = ib * iy;
+      const float2 ra = make_float2(fmaf(wa, v[j].x, -yh.x), fmaf(wa, v[j].y, -yh.y));
+      const float2 rb = make_float2(fmaf(wb, u[j].x, -yh.z), fmaf(wb, u[j].y, -yh.w));
+      part[0] = fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, part[0]));
+      part[0] = fmaf(rb.x, rb.x, fmaf(rb.y, rb.y, part[0]));
+      v[j] = cscale(ra, wa * a.scale);
+      u[j] = cscale(rb, wb * a.scale);
+    }
+    part[0] *= a.scale;
+  }
+}
+
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const PassArgs a, int nproj) {
+  constexpr int EPT = ept_for(N);
+  constexpr int NT = col2_threads(N, C);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  constexpr int CHUNKS = N * C / 2;  // 16-byte chunks per tile
+  constexpr int TILE = C * col_tile_rows(N, C);
+  static_assert(CHUNKS % NT == 0, "tile chunks must divide evenly");
+  static_assert(OP != COL_PRECOND_REG, "single-input passes only");
+  extern __shared__ float2 smem[];
+
+  const int tid = threadIdx.x;
+  const int c2 = tid % (C / 2), t = tid / (C / 2);
+  const int tiles_per_proj = a.nx / C;
+  const int ntiles = nproj * tiles_per_proj;
+  const size_t ld = (size_t)a.nx;
+
+  auto tile_base = [&](int tile, int& proj, int& col0) -> size_t {
+    proj = a.proj0 + tile / tiles_per_proj;
+    col0 = (tile % tiles_per_proj) * C;
+    return (size_t)proj * a.ny * a.nx + col0;
+  };
+  auto prefetch = [&](int tile, float2* buf) {
+    int proj, col0;
+    const size_t b = tile_base(tile, proj, col0);
+    if (a.active != nullptr && a.active[proj] == 0) return;
+#pragma unroll
+    for (int k = 0; k < CHUNKS / NT; k++) {
+      const int q = tid + k * NT;  // chunk q: row q / (C/2), column pair q % (C/2)
+      const int row = q / (C / 2), pr = q % (C / 2);
+      cp_async16(buf + col_row(row, C) * C + 2 * pr, a.in + b + (size_t)row * ld + 2 * pr);
+    }
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, smem);
+  cp_async_commit();
+  for (int k = 0; tile < ntiles; k++, tile += gridDim.x) {
+    float2* cur = smem + (k & 1) * TILE;
+    float2* nxt = smem + ((k + 1) & 1) * TILE;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    int proj, col0;
+    const size_t base = tile_base(tile, proj, col0) + 2 * c2;
+    const int col = col0 + 2 * c2;
+    if (a.active != nullptr && a.active[proj] == 0) {
+      __syncthreads();
+      continue;
+    }
+    const ColPairLayout<C> sm{cur + 2 * c2};
+    float2 v[EPT], u[EPT];
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+
+    if constexpr (OP == COL_IFFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) {
+        const float4 q = sm[slot_index<N, RK>(t, j)];
+        v[j] = make_float2(q.x * a.scale, q.y * a.scale);
+        u[j] = make_float2(q.z * a.scale, q.w * a.scale);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) {
+        const float4 q = sm[slot_index<N, RS>(t, j)];
+        v[j] = make_float2(q.x, q.y);
+        u[j] = make_float2(q.z, q.w);
+      }
+      fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
+      if constexpr (OP != COL_FFT) col_pair_filter<N, OP, ColPairLayout<C>>(a, t, col, base, v, u, part);
+    }
+    if constexpr (OP == COL_FFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++)
+        *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RK>(t, j) * ld) =
+            make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
+    } else {
+      fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
+#pragma unroll
+      for (int j = 0; j < EPT; j++)
+        *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RS>(t, j) * ld) =
+            make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
+    }
+    if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, cur);
+    __syncthreads();  // cur is refilled by the prefetch of the next-but-one tile
+  }
+  cp_async_wait<0>();
+}
+
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_kernel_t(const PassArgs a, int nproj) {
@@ -784,7 +925,16 @@ template <int N, int OP, int C, int PIPE>
 struct ColShape {
   static int resident;  // CTAs per SM of the persistent kernels (set by prep)
   static cudaError_t prep() {
-    if constexpr (PIPE == 2) {
+    if constexpr (PIPE == 3) {
+      cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe2<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)colp_smem_bytes(N, C));
+      if (e != cudaSuccess) return e;
+      int r = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_pipe2<N, OP, C>, col2_threads(N, C),
+                                                        colp_smem_bytes(N, C));
+      resident = r > 0 ? r : 1;
+      return e;
+    } else if constexpr (PIPE == 2) {
       cudaError_t e = cudaFuncSetAttribute(col_kernel_t<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)colt_smem_bytes(N, C));
       if (e != cudaSuccess) return e;
@@ -812,7 +962,9 @@ struct ColShape {
       const long long ntiles = (long long)nproj * (a.nx / C);
       const long long slots = (long long)device_sms() * resident;
       const int grid = (int)(ntiles < slots ? ntiles : slots);
-      if constexpr (PIPE == 2)
+      if constexpr (PIPE == 3)
+        col_kernel_pipe2<N, OP, C><<<grid, col2_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+      else if constexpr (PIPE == 2)
         col_kernel_t<N, OP, C><<<grid, col_threads(N, C), colt_smem_bytes(N, C), s>>>(a, nproj);
       else
         col_kernel_pipe<N, OP, C><<<grid, col_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
@@ -832,7 +984,7 @@ struct ColVariant {
   int C;
   int pipe;
 };
-constexpr int MAX_COL_VARIANTS = 8;
+constexpr int MAX_COL_VARIANTS = 10;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
@@ -864,10 +1016,12 @@ cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
 // a shape is offered when its CTA has 16..512 threads and its buffers fit
 template <int N, int OP, int C, int PIPE>
 constexpr bool col_shape_ok() {
-  constexpr int th = col_threads(N, C);
-  constexpr size_t sm = PIPE == 2 ? colt_smem_bytes(N, C) : PIPE == 1 ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
-  return th >= 16 && th <= 512 && sm <= 200 * 1024 && (PIPE != 1 || (N * C / 2) % th == 0) &&
-         (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8));
+  constexpr int th = PIPE == 3 ? col2_threads(N, C) : col_threads(N, C);
+  constexpr size_t sm =
+      PIPE == 2 ? colt_smem_bytes(N, C) : (PIPE == 1 || PIPE == 3) ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
+  return th >= 16 && th <= 512 && sm <= 200 * 1024 && ((PIPE != 1 && PIPE != 3) || (N * C / 2) % th == 0) &&
+         (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8)) &&
+         (PIPE != 3 || (OP != COL_PRECOND_REG && C >= 4 && th >= 32));
 }
 
 template <int N, int OP, int C, int PIPE>
@@ -889,6 +1043,8 @@ void add_col_op(LengthKernels& k) {
   if constexpr (N < 1024) add_col_variant<N, OP, 8, 1>(k);
   add_col_variant<N, OP, 8, 2>(k);
   add_col_variant<N, OP, 4, 2>(k);
+  add_col_variant<N, OP, 8, 3>(k);
+  add_col_variant<N, OP, 16, 3>(k);
 }
 
 template <int N>

@@ -102,6 +102,9 @@ def load(path: str | None = None):
         "pwf_group_destroy": ([_P], i32),
         "pwf_group_solve": ([_P, _P, _P, _P, _P, i32, f64], i32),
         "pwf_group_read": ([_P, i32, _P, _P], i32),
+        "pwf_solve_joint": ([_P, _P, _P, _P, i32, f64, _P, _P], i32),
+        "pwf_fbp_workspace_bytes": ([i32, i32, i32], ctypes.c_size_t),
+        "pwf_fbp": ([_P, i32, i32, i32, ctypes.POINTER(f64), f64, f64, _P, _P, ctypes.c_size_t, _P], i32),
         "pwf_calibrate_coherence": ([_P, _P, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)], i32),
         "pwf_diffuser_from_reference": ([_P, _P, f64, _P], i32),
     }
@@ -264,6 +267,21 @@ def pwf_solve(plan, y, t, psi, max_iter: int, corr_tol: float = 0.0, batch: int 
     return (it, loss) if batch is not None else None
 
 
+def pwf_solve_joint(plan, y, t, psi, max_iter: int, eta_t: float, batch: int | None = None):
+    """Algorithm S1 with the shared diffuser t refined in place after every
+    iteration (fixed iteration count). With ``batch`` given, returns (iters, loss)."""
+    import numpy as np
+    _on_current_stream(plan)
+    it = loss = None
+    if batch is not None:
+        it = np.zeros(batch, np.int32)
+        loss = np.zeros(batch, np.float64)
+    _check(load().pwf_solve_joint(plan, _ptr(y), _ptr(t), _ptr(psi), int(max_iter), float(eta_t),
+                                  None if it is None else it.ctypes.data_as(_P),
+                                  None if loss is None else loss.ctypes.data_as(_P)), "pwf_solve_joint", plan)
+    return (it, loss) if batch is not None else None
+
+
 def pwf_state_bytes(state) -> int:
     return int(load().pwf_state_bytes(state))
 
@@ -359,6 +377,26 @@ def pwf_diffuser_from_reference(plan, I_ref, wiener_eps: float, t_out):
            "pwf_diffuser_from_reference", plan)
 
 
+def pwf_fbp_workspace_bytes(n_angles: int, ny: int, nx: int) -> int:
+    return int(load().pwf_fbp_workspace_bytes(int(n_angles), int(ny), int(nx)))
+
+
+def pwf_fbp(psi, angles_rad, wavelength_m: float, voxel_m: float, vol=None, workspace=None):
+    """beta + i delta [ny][nx][nx] (complex64, device) from psi [n_angles][ny][nx]."""
+    import torch
+    n_angles, ny, nx = psi.shape
+    if vol is None:
+        vol = torch.empty((ny, nx, nx), dtype=torch.complex64, device=psi.device)
+    need = pwf_fbp_workspace_bytes(n_angles, ny, nx)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=psi.device)
+    ang = (ctypes.c_double * n_angles)(*[float(a) for a in angles_rad])
+    _check(load().pwf_fbp(_ptr(psi), n_angles, ny, nx, ang, float(wavelength_m), float(voxel_m), _ptr(vol),
+                          _ptr(workspace), workspace.numel() * workspace.element_size(), _stream_ptr()),
+           "pwf_fbp")
+    return vol
+
+
 def pwf_status_string(status: int) -> str:
     return load().pwf_status_string(int(status)).decode()
 
@@ -429,6 +467,9 @@ class Plan:
 
     def solve(self, y, t, psi, max_iter, corr_tol=0.0, read_back=True):
         return pwf_solve(self.handle, y, t, psi, max_iter, corr_tol, self.desc.batch if read_back else None)
+
+    def solve_joint(self, y, t, psi, max_iter, eta_t, read_back=True):
+        return pwf_solve_joint(self.handle, y, t, psi, max_iter, eta_t, self.desc.batch if read_back else None)
 
     def step(self, y, t, psi, corr_tol=0.0):
         pwf_step(self.handle, self.state, y, t, psi, corr_tol)
