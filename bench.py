@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--workload", default="tomo180x1024_iotf")
     ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
+    ap.add_argument("--legs", default="all",
+                    help="comma list of extra legs to run (plain,e2e,modal,mixed,autograd,fbp,ablation,cpu) or all")
     ap.add_argument("--overlap", action="store_true", help="two half-batch chains (PWF_FLAG_OVERLAP)")
     return ap.parse_args()
 
@@ -469,55 +471,62 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        # plain per-projection baseline (unfused, Algorithm S2 step by step) on a sample
-        nplain, iplain = 4, 2
-        plain = P.Plan(plan_desc(P, w, nplain, P.FLAG_PLAIN))
-        yp = y[:nplain].contiguous()
-        pp = torch.zeros((nplain, w.ny, w.nx), dtype=torch.complex64, device=dev)
-        plain.solve(yp, t, pp, 1, read_back=False)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        pp.zero_()
-        plain.solve(yp, t, pp, iplain, read_back=False)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        pv = nplain * w.ny * w.nx * iplain / 1e6 / (a0.elapsed_time(a1) / 1e3)
-        extras["plain_gpu"] = {"value": pv, "unit": UNIT, "sample": f"{nplain} projections x {iplain} iterations",
-                               "fused_over_plain": value / world / pv}
-        plain.close()
-        del yp, pp
+        legs = set(args.legs.split(",")) if args.legs != "all" else None
 
-        # end to end through host buffers: H2D (y, t) + solve + D2H psi per call
-        e2e_iters = 10
-        y_h = y.cpu().pin_memory()
-        t_h = t.cpu().pin_memory()
-        psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
-        y_d = torch.empty_like(y)
-        t_d = torch.empty_like(t)
-        times = []
-        for rep in range(3):
+        def leg(name):
+            return legs is None or name in legs
+
+        if leg("plain"):
+            # plain per-projection baseline (unfused, Algorithm S2 step by step) on a sample
+            nplain, iplain = 4, 2
+            plain = P.Plan(plan_desc(P, w, nplain, P.FLAG_PLAIN))
+            yp = y[:nplain].contiguous()
+            pp = torch.zeros((nplain, w.ny, w.nx), dtype=torch.complex64, device=dev)
+            plain.solve(yp, t, pp, 1, read_back=False)
             torch.cuda.synchronize()
-            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            y_d.copy_(y_h, non_blocking=True)
-            t_d.copy_(t_h, non_blocking=True)
-            psi.zero_()
-            plan.solve(y_d, t_d, psi, e2e_iters, read_back=False)
-            psi_h.copy_(psi, non_blocking=True)
-            b1.record(stream)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            pp.zero_()
+            plain.solve(yp, t, pp, iplain, read_back=False)
+            a1.record(stream)
             torch.cuda.synchronize()
-            if rep > 0:
-                times.append(b0.elapsed_time(b1))
-        ems = sum(times) / len(times)
-        extras["e2e"] = {"value": mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
-                         "h2d_bytes_per_step": int(y.numel() * 4 + t.numel() * 8),
-                         "d2h_bytes_per_step": int(psi.numel() * 8),
-                         "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers"}
-        del y_h, psi_h
+            pv = nplain * w.ny * w.nx * iplain / 1e6 / (a0.elapsed_time(a1) / 1e3)
+            extras["plain_gpu"] = {"value": pv, "unit": UNIT, "sample": f"{nplain} projections x {iplain} iterations",
+                                   "fused_over_plain": value / world / pv}
+            plain.close()
+            del yp, pp
+
+        if leg("e2e"):
+            # end to end through host buffers: H2D (y, t) + solve + D2H psi per call
+            e2e_iters = 10
+            y_h = y.cpu().pin_memory()
+            t_h = t.cpu().pin_memory()
+            psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
+            y_d = torch.empty_like(y)
+            t_d = torch.empty_like(t)
+            times = []
+            for rep in range(3):
+                torch.cuda.synchronize()
+                b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                b0.record(stream)
+                y_d.copy_(y_h, non_blocking=True)
+                t_d.copy_(t_h, non_blocking=True)
+                psi.zero_()
+                plan.solve(y_d, t_d, psi, e2e_iters, read_back=False)
+                psi_h.copy_(psi, non_blocking=True)
+                b1.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times.append(b0.elapsed_time(b1))
+            ems = sum(times) / len(times)
+            extras["e2e"] = {"value": mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
+                             "h2d_bytes_per_step": int(y.numel() * 4 + t.numel() * 8),
+                             "d2h_bytes_per_step": int(psi.numel() * 8),
+                             "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers"}
+            del y_h, psi_h
 
         # the same series with partial coherence as 9 tilted source modes
-        if w.name == "tomo180x1024_iotf":
+        if leg("modal") and w.name == "tomo180x1024_iotf":
             wk = S.WORKLOADS["tomo180x1024_k9"]
             mplan = P.Plan(plan_desc(P, wk, batch))
             pm = torch.zeros_like(psi)
@@ -537,29 +546,30 @@ def main():
             del pm
 
         # uneven batch: 16 each of 256^2, 768^2, 1536^2, 2048^2, 25 modes, one group
-        if w.name == "tomo180x1024_iotf":
+        if leg("mixed") and w.name == "tomo180x1024_iotf":
             extras["mixed_k25"] = run_mixed(P, S, torch, dev, stream)
 
         # differentiation: 16 x 2048^2 forward + backward through torch.autograd
-        if w.name == "tomo180x1024_iotf":
+        if leg("autograd") and w.name == "tomo180x1024_iotf":
             extras["autograd_16x2048"] = run_autograd(P, S, torch, dev, stream)
 
         # tomography after the path: FBP of the retrieved series
-        if w.name == "tomo180x1024_iotf":
+        if leg("fbp") and w.name == "tomo180x1024_iotf":
             extras["fbp_180x1024"] = run_fbp(P, S, torch, dev, stream, psi, w)
 
         # ablations on a small synthetic series (preconditioner, gamma, alpha): PWF + FBP + scores
-        if w.name == "tomo180x1024_iotf":
+        if leg("ablation") and w.name == "tomo180x1024_iotf":
             from paper_2503_20146_gb300 import ablation as A
             series = A.make_series(n_angles=32, n=128)
             extras["ablation_32x128"] = {"iterations": 150, "rows": A.run_ablation(series, iters=150)}
             del series
 
-        # FP64 oracle on the host cores, bounded sample
-        dt, work = oracle_sample(w, 1, 3)
-        extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                  "sample": f"1 projection of {w.ny}x{w.nx}, 3 iterations, numpy FP64 (single thread)",
-                                  "seconds": dt}
+        if leg("cpu"):
+            # FP64 oracle on the host cores, bounded sample
+            dt, work = oracle_sample(w, 1, 3)
+            extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                      "sample": f"1 projection of {w.ny}x{w.nx}, 3 iterations, numpy FP64 (single thread)",
+                                      "seconds": dt}
 
     if rank == 0:
         line = {

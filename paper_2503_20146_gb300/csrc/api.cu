@@ -1542,7 +1542,7 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   char tmp[2048];
   size_t o = 0;
   auto shape = [&](const ColVariant& v) {
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   };
   o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {

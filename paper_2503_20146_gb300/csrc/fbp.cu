@@ -11,12 +11,15 @@
 //     (Ram-Lak) kernel, transformed back, and the first nx samples kept. The
 //     complex field psi is filtered as is: the kernel is real and even, so the
 //     real and the imaginary parts are filtered independently in one pass.
-//   * fbp_backproject_kernel: one thread per (x, 4 values of z) of one slice;
+//     The filtered row is stored in the middle of a zeroed row of width 2 nx
+//     (detector pixel i at column i + nx/2), so that the back projection of
+//     any voxel of the nx x nx grid (|s| <= nx / sqrt(2) + 1) reads inside the
+//     row without bounds checks and gets zero outside the detector.
+//   * fbp_backproject_kernel: one thread per (x, 8 values of z) of one slice;
 //     per angle, s = x cos(theta) + z sin(theta), linear interpolation of the
-//     filtered row (zero outside the detector), accumulation in FP32. The
-//     angle table sits in shared memory; the filtered rows of one slice are
-//     read through L1/L2 (a 32 x 32 voxel tile touches at most ~46 samples per
-//     angle).
+//     filtered row, accumulation in FP32. The angle table sits in shared
+//     memory; the filtered rows of one slice are read through L1/L2 (a 32 x 64
+//     voxel tile touches at most ~70 samples per angle).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -57,11 +60,13 @@ __global__ void __launch_bounds__(row_threads(L))
   for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], __ldg(&ramp[slot_index<L, RK>(t, j)]));
   fft_run<L, INV>(v, sm, t, tw_inv);
   if (valid) {
-    float2* dst = out + (size_t)row * nx;
+    // padded row of width L = 2 nx: samples at nx/2 .. 3nx/2 - 1, zeros around
+    float2* dst = out + (size_t)row * L;
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int i = slot_index<L, RS>(t, j);
-      if (i < nx) dst[i] = v[j];
+      const int o = i + nx / 2;
+      dst[o < L ? o : o - L] = i < nx ? v[j] : make_float2(0.f, 0.f);
     }
   }
 }
@@ -101,7 +106,7 @@ FilterFn filter_for(int L) {
   }
 }
 
-constexpr int BP_TX = 32, BP_TY = 8, BP_ZPT = 4;  // tile 32 (x) by 32 (z) voxels
+constexpr int BP_TX = 32, BP_TY = 8, BP_ZPT = 8;  // tile 32 (x) by 64 (z) voxels
 
 __global__ void __launch_bounds__(BP_TX * BP_TY)
     fbp_backproject_kernel(const float2* __restrict__ q, float2* __restrict__ vol, const float2* __restrict__ cs,
@@ -114,15 +119,23 @@ __global__ void __launch_bounds__(BP_TX * BP_TY)
   const int zb = blockIdx.y * (BP_TY * BP_ZPT) + threadIdx.y;
   const int y = blockIdx.z;
   const float half = 0.5f * (float)nx - 0.5f;  // detector index of s = 0
-  const float xc = (float)x - half;
+  // voxels past the grid (tile overhang) compute on the last row / column,
+  // which keeps their reads inside the padded rows; they store nothing
+  const float xc = (float)(x < nx ? x : nx - 1) - half;
   float zc[BP_ZPT];
 #pragma unroll
-  for (int m = 0; m < BP_ZPT; m++) zc[m] = (float)(zb + m * BP_TY) - half;
+  for (int m = 0; m < BP_ZPT; m++) {
+    const int z = zb + m * BP_TY;
+    zc[m] = (float)(z < nx ? z : nx - 1) - half;
+  }
   float2 acc[BP_ZPT];
 #pragma unroll
   for (int m = 0; m < BP_ZPT; m++) acc[m] = make_float2(0.f, 0.f);
-  const size_t plane = (size_t)ny * nx;
-  const float2* qy = q + (size_t)y * nx;
+  // rows of width 2 nx, detector index u at column u + nx/2; every voxel of
+  // the grid has |u - half| <= nx / sqrt(2) + 1, so both taps stay in the row
+  const int W = 2 * nx;
+  const size_t plane = (size_t)ny * W;
+  const float2* qy = q + (size_t)y * W + nx / 2;
   for (int a = 0; a < n_angles; a++) {
     const float2 c = scs[a];
     const float2* row = qy + (size_t)a * plane;
@@ -132,9 +145,8 @@ __global__ void __launch_bounds__(BP_TX * BP_TY)
       const float u = fmaf(zc[m], c.y, base);
       const float uf = floorf(u);
       const float w = u - uf;
-      const int j = (int)uf;
-      const float2 q0 = (j >= 0 && j < nx) ? __ldg(&row[j]) : make_float2(0.f, 0.f);
-      const float2 q1 = (j + 1 >= 0 && j + 1 < nx) ? __ldg(&row[j + 1]) : make_float2(0.f, 0.f);
+      const float2* r = row + (int)uf;
+      const float2 q0 = __ldg(r), q1 = __ldg(r + 1);
       acc[m].x += fmaf(w, q1.x - q0.x, q0.x);
       acc[m].y += fmaf(w, q1.y - q0.y, q0.y);
     }
@@ -160,7 +172,7 @@ FbpLayout fbp_layout(int n_angles, int ny, int nx) {
   host_twiddles(L, FWD, a);
   host_twiddles(L, INV, b);
   l.q = 0;
-  l.ramp = l.q + align256((size_t)n_angles * ny * nx * sizeof(float2));
+  l.ramp = l.q + align256((size_t)n_angles * ny * 2 * nx * sizeof(float2));
   l.twf = l.ramp + align256((size_t)L * sizeof(float));
   l.twi = l.twf + align256(a.size() * sizeof(float2));
   l.cs = l.twi + align256(b.size() * sizeof(float2));

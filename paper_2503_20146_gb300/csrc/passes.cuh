@@ -634,7 +634,10 @@ __device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int co
   }
 }
 
-template <int N, int OP, int C>
+// NBUF = 2: tile k + 1 is copied while tile k is transformed (one CTA per SM
+// at 8 columns); NBUF = 1: one buffer, the copy of the next tile starts after
+// the current one is done, and the overlap comes from the second CTA on the SM.
+template <int N, int OP, int C, int NBUF>
 __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const PassArgs a, int nproj) {
   constexpr int EPT = ept_for(N);
   constexpr int NT = col2_threads(N, C);
@@ -670,15 +673,21 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
   };
 
   int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile, smem);
+  if (NBUF == 2 && tile < ntiles) prefetch(tile, smem);
   cp_async_commit();
   for (int k = 0; tile < ntiles; k++, tile += gridDim.x) {
-    float2* cur = smem + (k & 1) * TILE;
-    float2* nxt = smem + ((k + 1) & 1) * TILE;
-    const int next = tile + gridDim.x;
-    if (next < ntiles) prefetch(next, nxt);
-    cp_async_commit();
-    cp_async_wait<1>();
+    float2* cur = smem + (NBUF == 2 ? (k & 1) * TILE : 0);
+    if constexpr (NBUF == 2) {
+      float2* nxt = smem + ((k + 1) & 1) * TILE;
+      const int next = tile + gridDim.x;
+      if (next < ntiles) prefetch(next, nxt);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      prefetch(tile, cur);
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
     __syncthreads();
 
     int proj, col0;
@@ -925,13 +934,14 @@ template <int N, int OP, int C, int PIPE>
 struct ColShape {
   static int resident;  // CTAs per SM of the persistent kernels (set by prep)
   static cudaError_t prep() {
-    if constexpr (PIPE == 3) {
-      cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe2<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)colp_smem_bytes(N, C));
+    if constexpr (PIPE == 3 || PIPE == 4) {
+      constexpr int NB = PIPE == 3 ? 2 : 1;
+      constexpr size_t SM = NB * col_smem_bytes(N, C);
+      cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe2<N, OP, C, NB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
       if (e != cudaSuccess) return e;
       int r = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_pipe2<N, OP, C>, col2_threads(N, C),
-                                                        colp_smem_bytes(N, C));
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_pipe2<N, OP, C, NB>, col2_threads(N, C), SM);
       resident = r > 0 ? r : 1;
       return e;
     } else if constexpr (PIPE == 2) {
@@ -963,7 +973,9 @@ struct ColShape {
       const long long slots = (long long)device_sms() * resident;
       const int grid = (int)(ntiles < slots ? ntiles : slots);
       if constexpr (PIPE == 3)
-        col_kernel_pipe2<N, OP, C><<<grid, col2_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+        col_kernel_pipe2<N, OP, C, 2><<<grid, col2_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+      else if constexpr (PIPE == 4)
+        col_kernel_pipe2<N, OP, C, 1><<<grid, col2_threads(N, C), col_smem_bytes(N, C), s>>>(a, nproj);
       else if constexpr (PIPE == 2)
         col_kernel_t<N, OP, C><<<grid, col_threads(N, C), colt_smem_bytes(N, C), s>>>(a, nproj);
       else
@@ -1016,12 +1028,13 @@ cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
 // a shape is offered when its CTA has 16..512 threads and its buffers fit
 template <int N, int OP, int C, int PIPE>
 constexpr bool col_shape_ok() {
-  constexpr int th = PIPE == 3 ? col2_threads(N, C) : col_threads(N, C);
+  constexpr bool pair = PIPE == 3 || PIPE == 4;
+  constexpr int th = pair ? col2_threads(N, C) : col_threads(N, C);
   constexpr size_t sm =
       PIPE == 2 ? colt_smem_bytes(N, C) : (PIPE == 1 || PIPE == 3) ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
-  return th >= 16 && th <= 512 && sm <= 200 * 1024 && ((PIPE != 1 && PIPE != 3) || (N * C / 2) % th == 0) &&
+  return th >= 16 && th <= 512 && sm <= 200 * 1024 && ((PIPE == 0 || PIPE == 2) || (N * C / 2) % th == 0) &&
          (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8)) &&
-         (PIPE != 3 || (OP != COL_PRECOND_REG && C >= 4 && th >= 32));
+         (!pair || (OP != COL_PRECOND_REG && C >= 4 && th >= 32 && th <= 256));
 }
 
 template <int N, int OP, int C, int PIPE>
@@ -1044,7 +1057,8 @@ void add_col_op(LengthKernels& k) {
   add_col_variant<N, OP, 8, 2>(k);
   add_col_variant<N, OP, 4, 2>(k);
   add_col_variant<N, OP, 8, 3>(k);
-  add_col_variant<N, OP, 16, 3>(k);
+  add_col_variant<N, OP, 8, 4>(k);
+  add_col_variant<N, OP, 16, 4>(k);
 }
 
 template <int N>
