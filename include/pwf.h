@@ -219,8 +219,9 @@ pwf_status pwf_diffuser_from_reference(pwf_plan* plan, const float* I_ref, doubl
  *   vol_out  complex64 [ny][nx][nx], device: slice y, row z (beam direction at
  *            angle 0), column x; Re = beta, Im = delta
  *   workspace  device memory of pwf_fbp_workspace_bytes(...) bytes, 256-byte
- *            aligned (filtered rows zero-padded to 2 nx, filter and angle
- *            tables; about 2 n_angles ny nx complex64)
+ *            aligned (filtered rows zero-padded to 2 nx as 16-byte
+ *            interpolation records, filter and angle tables; about
+ *            32 n_angles ny nx bytes)
  *   stream   cudaStream_t (null: legacy default stream)
  * Ram-Lak: h(0) = 1/4, h(k) = -1/(pi^2 k^2) for odd k, 0 otherwise (unit
  * sampling); linear convolution along the row (zero padding to 2 nx); back

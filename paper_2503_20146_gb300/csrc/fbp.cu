@@ -14,10 +14,12 @@
 //     The filtered row is stored in the middle of a zeroed row of width 2 nx
 //     (detector pixel i at column i + nx/2), so that the back projection of
 //     any voxel of the nx x nx grid (|s| <= nx / sqrt(2) + 1) reads inside the
-//     row without bounds checks and gets zero outside the detector.
+//     row without bounds checks and gets zero outside the detector; each
+//     column holds the record (q[o], q[o+1] - q[o]), so one 16-byte load gives
+//     both taps of the linear interpolation.
 //   * fbp_backproject_kernel: one thread per (x, 8 values of z) of one slice;
-//     per angle, s = x cos(theta) + z sin(theta), linear interpolation of the
-//     filtered row, accumulation in FP32. The angle table sits in shared
+//     per angle, s = x cos(theta) + z sin(theta), linear interpolation
+//     q[j] + w (q[j+1] - q[j]) from one record, accumulation in FP32. The angle table sits in shared
 //     memory; the filtered rows of one slice are read through L1/L2 (a 32 x 64
 //     voxel tile touches at most ~70 samples per angle).
 #include <cuda_runtime.h>
@@ -59,14 +61,24 @@ __global__ void __launch_bounds__(row_threads(L))
 #pragma unroll
   for (int j = 0; j < EPT; j++) v[j] = cscale(v[j], __ldg(&ramp[slot_index<L, RK>(t, j)]));
   fft_run<L, INV>(v, sm, t, tw_inv);
-  if (valid) {
-    // padded row of width L = 2 nx: samples at nx/2 .. 3nx/2 - 1, zeros around
-    float2* dst = out + (size_t)row * L;
+  // records (q[o], q[o+1] - q[o]) of the padded row of width L = 2 nx (samples
+  // at nx/2 .. 3nx/2 - 1, zeros around): first the samples into shared memory
+  // (the transform's buffer is free again; every row of a warp takes part in
+  // the barriers), then the records of valid rows
+  float2* rowbuf = smem + rr * row_smem_len(L);
+  sm.sync();
 #pragma unroll
-    for (int j = 0; j < EPT; j++) {
-      const int i = slot_index<L, RS>(t, j);
-      const int o = i + nx / 2;
-      dst[o < L ? o : o - L] = i < nx ? v[j] : make_float2(0.f, 0.f);
+  for (int j = 0; j < EPT; j++) {
+    const int i = slot_index<L, RS>(t, j);
+    const int o = i + nx / 2;
+    rowbuf[o < L ? o : o - L] = i < nx ? v[j] : make_float2(0.f, 0.f);
+  }
+  sm.sync();
+  if (valid) {
+    float4* dst = reinterpret_cast<float4*>(out) + (size_t)row * L;
+    for (int o = t; o < L; o += TPF) {
+      const float2 q0 = rowbuf[o], q1 = rowbuf[o + 1 < L ? o + 1 : o];
+      dst[o] = make_float4(q0.x, q0.y, q1.x - q0.x, q1.y - q0.y);
     }
   }
 }
@@ -135,20 +147,20 @@ __global__ void __launch_bounds__(BP_TX * BP_TY)
   // the grid has |u - half| <= nx / sqrt(2) + 1, so both taps stay in the row
   const int W = 2 * nx;
   const size_t plane = (size_t)ny * W;
-  const float2* qy = q + (size_t)y * W + nx / 2;
+  const float4* qy = reinterpret_cast<const float4*>(q) + (size_t)y * W + nx / 2;
+#pragma unroll 4
   for (int a = 0; a < n_angles; a++) {
     const float2 c = scs[a];
-    const float2* row = qy + (size_t)a * plane;
+    const float4* row = qy + (size_t)a * plane;
     const float base = fmaf(xc, c.x, half);
 #pragma unroll
     for (int m = 0; m < BP_ZPT; m++) {
       const float u = fmaf(zc[m], c.y, base);
       const float uf = floorf(u);
       const float w = u - uf;
-      const float2* r = row + (int)uf;
-      const float2 q0 = __ldg(r), q1 = __ldg(r + 1);
-      acc[m].x += fmaf(w, q1.x - q0.x, q0.x);
-      acc[m].y += fmaf(w, q1.y - q0.y, q0.y);
+      const float4 qd = __ldg(row + (int)uf);
+      acc[m].x += fmaf(w, qd.z, qd.x);
+      acc[m].y += fmaf(w, qd.w, qd.y);
     }
   }
   if (x >= nx) return;
@@ -172,7 +184,7 @@ FbpLayout fbp_layout(int n_angles, int ny, int nx) {
   host_twiddles(L, FWD, a);
   host_twiddles(L, INV, b);
   l.q = 0;
-  l.ramp = l.q + align256((size_t)n_angles * ny * 2 * nx * sizeof(float2));
+  l.ramp = l.q + align256((size_t)n_angles * ny * 2 * nx * sizeof(float4));
   l.twf = l.ramp + align256((size_t)L * sizeof(float));
   l.twi = l.twf + align256(a.size() * sizeof(float2));
   l.cs = l.twi + align256(b.size() * sizeof(float2));
