@@ -896,6 +896,76 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
   }
 }
 
+// The same passes with the pair of adjacent columns (col, col + 1) per thread
+// (shared indices, twiddles and barriers; 16-byte exchanges). The shifted
+// columns (col - mx, col + 1 - mx) are adjacent but not 16-byte aligned for
+// odd mx (and wrap at the edge), so they move as two 8-byte accesses.
+template <int N, int MOP, int C>
+__global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const PassArgs a) {
+  constexpr int EPT = ept_for(N);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  extern __shared__ float2 smem[];
+  const int tid = threadIdx.x;
+  const int c2 = tid % (C / 2), t = tid / (C / 2);
+  const int proj = blockIdx.y + a.proj0;
+  const int col = blockIdx.x * C + 2 * c2;
+  if (a.active != nullptr && a.active[proj] == 0) return;
+  const int sh0 = ((col - a.mode_mx) % a.nx + a.nx) % a.nx;
+  const int sh1 = sh0 + 1 < a.nx ? sh0 + 1 : 0;
+  const size_t pb = (size_t)proj * a.ny * a.nx;
+  const size_t ld = (size_t)a.nx;
+  const ColPairLayout<C> sm{smem + 2 * c2};
+  const int my = ((a.mode_my % N) + N) % N;
+  float2 v[EPT], u[EPT];
+  if constexpr (MOP == CM_FWD) {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int y = slot_index<N, RS>(t, j);
+      const float2 m = __ldg(&a.cis_y[(my * y) % N]);
+      v[j] = cmul(a.in[pb + sh0 + (size_t)y * ld], m);
+      u[j] = cmul(a.in[pb + sh1 + (size_t)y * ld], m);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float4 q = *reinterpret_cast<const float4*>(a.in + pb + col + (size_t)slot_index<N, RS>(t, j) * ld);
+      v[j] = make_float2(q.x, q.y);
+      u[j] = make_float2(q.z, q.w);
+    }
+  }
+  fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
+  {
+    const float2 qa = cscale(__ldg(&a.qx[col]), a.scale), qb = cscale(__ldg(&a.qx[col + 1]), a.scale);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float2 qy = __ldg(&a.qy[slot_index<N, RK>(t, j)]);
+      float2 q0 = cmul(qa, qy), q1 = cmul(qb, qy);
+      if constexpr (MOP == CM_BACK) q0 = cconj(q0), q1 = cconj(q1);
+      v[j] = cmul(v[j], q0);
+      u[j] = cmul(u[j], q1);
+    }
+  }
+  fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
+  if constexpr (MOP == CM_FWD) {
+#pragma unroll
+    for (int j = 0; j < EPT; j++)
+      *reinterpret_cast<float4*>(a.out + pb + col + (size_t)slot_index<N, RS>(t, j) * ld) =
+          make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
+  } else {
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int y = slot_index<N, RS>(t, j);
+      const float2 m = __ldg(&a.cis_y[(my * y) % N]);
+      float2 r0 = cscale(cmulc(v[j], m), a.mode_w), r1 = cscale(cmulc(u[j], m), a.mode_w);
+      const size_t o0 = pb + sh0 + (size_t)y * ld, o1 = pb + sh1 + (size_t)y * ld;
+      if (a.accumulate) r0 = cadd(r0, a.out[o0]), r1 = cadd(r1, a.out[o1]);
+      a.out[o0] = r0;
+      a.out[o1] = r1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host-side launch for one transform length
 // ---------------------------------------------------------------------------
@@ -1011,17 +1081,27 @@ struct LengthKernels {
 
 // the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
 __host__ __device__ constexpr int colmode_c(int n) { return n >= 1024 ? (tpf_for(n) * 8 <= 512 ? 8 : 4) : 16; }
+// lengths with 16 values per thread and at most 64 threads per transform take
+// the column-pair kernel (8-column tiles, 256 threads, two CTAs per SM)
+__host__ __device__ constexpr bool colmode_pair(int n) { return ept_for(n) == 16 && tpf_for(n) <= 64 && n >= 128; }
 template <int N, int MOP>
 cudaError_t prep_colmode() {
-  constexpr int C = colmode_c(N);
-  return cudaFuncSetAttribute(col_mode_kernel<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)col_smem_bytes(N, C));
+  constexpr int C = colmode_pair(N) ? 8 : colmode_c(N);
+  if constexpr (colmode_pair(N))
+    return cudaFuncSetAttribute(col_mode_kernel2<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)col_smem_bytes(N, C));
+  else
+    return cudaFuncSetAttribute(col_mode_kernel<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)col_smem_bytes(N, C));
 }
 template <int N, int MOP>
 cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
-  constexpr int C = colmode_c(N);
+  constexpr int C = colmode_pair(N) ? 8 : colmode_c(N);
   dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
-  col_mode_kernel<N, MOP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+  if constexpr (colmode_pair(N))
+    col_mode_kernel2<N, MOP, C><<<grid, col2_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+  else
+    col_mode_kernel<N, MOP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
   return cudaGetLastError();
 }
 
