@@ -182,6 +182,15 @@ def make_workload(P, S, w, batch, device, rank=0, world=1):
     return psi_true, t
 
 
+# Algorithmic bytes per pixel of one source-mode iteration (K modes): per mode
+# the forward CM_FWD 16, ROW_MUL_T 24, COL_Q 16, ROW_MODE_INT 24 (v_j stored,
+# intensity accumulated) and the backward ROW_MODE_VG 20, COL_Q 16, ROW_MUL_T 24,
+# CM_BACK 24 (spectrum accumulated) = 164 B/px; once per iteration the residual
+# 12 and ROW_GRAD_PACK + COL_PRECOND_REG + ROW_NESTEROV_FFT 112.
+def modal_bytes_per_px(k: int) -> int:
+    return 164 * k + 12 + 112
+
+
 def plan_desc(P, w, batch, flags=0, n_modes=None):
     return P.PlanDesc(batch, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
                       w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags,
@@ -318,9 +327,13 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
     P.pwf_group_destroy(group)
     for p in plans:
         p.close()
+    bpp = modal_bytes_per_px(wm.n_modes)
+    gbs = mpx * 1e6 * bpp / (ms / steps / 1e3) / 1e9
+    hbm, _ = peaks()
     return {"value": mpx * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "workload": wm.name, "mpx_per_iter": mpx, "classes": shapes,
-            "launch": "one CUDA graph launch per iteration over all four size classes"}
+            "launch": "one CUDA graph launch per iteration over all four size classes",
+            "model_bytes_per_px": bpp, "model_gbs": gbs, "model_frac_of_measured_hbm": gbs / hbm}
 
 
 def run_autograd(P, S, torch, dev, stream, reps=3):
@@ -540,8 +553,11 @@ def main():
             m1.record(stream)
             torch.cuda.synchronize()
             mms = m0.elapsed_time(m1)
+            mbpp = modal_bytes_per_px(wk.n_modes)
+            mgbs = batch * w.ny * w.nx * mbpp / (mms / msteps / 1e3) / 1e9
             extras["modal_k9"] = {"value": mpx_iter * msteps / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / msteps,
-                                  "workload": wk.name, "steps": msteps}
+                                  "workload": wk.name, "steps": msteps, "model_bytes_per_px": mbpp,
+                                  "model_gbs": mgbs, "model_frac_of_measured_hbm": mgbs / hbm}
             mplan.close()
             del pm
 
