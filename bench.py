@@ -324,16 +324,31 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     shapes = [P.pwf_plan_describe(p.handle).split(" col_q")[0] for p in plans]
+    # each size class alone (its own graph, whole GPU): where the group's time goes
+    hbm, _ = peaks()
+    per_class = []
+    for ci, n in enumerate(S.MIXED_SIZES):
+        plans[ci].solve(ys[ci], ts[ci], psis[ci], 1, read_back=False)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        plans[ci].solve(ys[ci], ts[ci], psis[ci], 2, read_back=False)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / 2
+        px = S.MIXED_PER_SIZE * n * n
+        per_class.append({"n": n, "ms_per_iter_alone": cms,
+                          "model_frac_of_measured_hbm": px * modal_bytes_per_px(wm.n_modes) / (cms / 1e3) / 1e9 / hbm})
     P.pwf_group_destroy(group)
     for p in plans:
         p.close()
     bpp = modal_bytes_per_px(wm.n_modes)
     gbs = mpx * 1e6 * bpp / (ms / steps / 1e3) / 1e9
-    hbm, _ = peaks()
     return {"value": mpx * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "workload": wm.name, "mpx_per_iter": mpx, "classes": shapes,
             "launch": "one CUDA graph launch per iteration over all four size classes",
-            "model_bytes_per_px": bpp, "model_gbs": gbs, "model_frac_of_measured_hbm": gbs / hbm}
+            "model_bytes_per_px": bpp, "model_gbs": gbs, "model_frac_of_measured_hbm": gbs / hbm,
+            "per_class_alone": per_class}
 
 
 def run_autograd(P, S, torch, dev, stream, reps=3):

@@ -1066,7 +1066,7 @@ struct ColVariant {
   int C;
   int pipe;
 };
-constexpr int MAX_COL_VARIANTS = 10;
+constexpr int MAX_COL_VARIANTS = 12;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
@@ -1139,6 +1139,7 @@ void add_col_op(LengthKernels& k) {
   add_col_variant<N, OP, 8, 3>(k);
   add_col_variant<N, OP, 8, 4>(k);
   add_col_variant<N, OP, 16, 4>(k);
+  add_col_variant<N, OP, 4, 4>(k);
 }
 
 template <int N>
