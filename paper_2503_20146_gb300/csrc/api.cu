@@ -3,6 +3,7 @@
 // and the unfused per-operation baseline.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1663,6 +1664,9 @@ pwf_status pwf_group_destroy(pwf_group* g) {
   return PWF_OK;
 }
 
+// classes of at least this many pixels (batch x ny x nx) fill the GPU on their own
+constexpr long long kGroupChainPixels = 8LL << 20;
+
 pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, const void* const* t,
                            void* const* psi, int32_t max_iter, double corr_tol) {
   if (!g || !y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
@@ -1690,7 +1694,10 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
     a.out = p->X;
     LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
   }
-  // one graph: fork a branch per class, one fused iteration on each, join
+  // One graph per iteration. Classes large enough to fill the GPU on their own
+  // run one after another on the main chain (largest first): side by side
+  // their persistent column passes only contend for the SMs. Smaller classes
+  // run on forked branches beside that chain and join at its end.
   std::vector<const void*> key;
   for (int i = 0; i < n; i++) {
     key.push_back(y[i]);
@@ -1704,22 +1711,41 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
     }
     cudaGraph_t graph = nullptr;
     pwf_plan* p0 = g->plans[0];
+    std::vector<int> chain, side;
+    for (int i = 0; i < n; i++)
+      ((long long)g->plans[i]->d.batch * g->plans[i]->d.ny * g->plans[i]->d.nx >= kGroupChainPixels ? chain : side)
+          .push_back(i);
+    std::sort(chain.begin(), chain.end(), [&](int a, int b) {
+      const pwf_plan_desc &da = g->plans[a]->d, &db = g->plans[b]->d;
+      return (long long)da.batch * da.ny * da.nx > (long long)db.batch * db.ny * db.nx;
+    });
     PWF_CUDA(p0, cudaStreamBeginCapture(g->main, cudaStreamCaptureModeThreadLocal));
     r = PWF_OK;
     cudaError_t ce = cudaEventRecord(g->ev[0], g->main);
     long long kernels = 0;
-    for (int i = 0; i < n && r == PWF_OK && ce == cudaSuccess; i++) {
+    auto run_class = [&](int i, cudaStream_t s) {
       pwf_plan* p = g->plans[i];
-      ce = cudaStreamWaitEvent(g->branch[i], g->ev[0], 0);
-      if (ce != cudaSuccess) break;
-      p->stream = g->branch[i];
+      p->stream = s;
       const long long before = p->launches;
       r = fused_iteration(p, p->solve_state, y[i], (const float2*)t[i], (float2*)psi[i], true, corr_tol);
       kernels += p->launches - before;
       p->launches = before;
       p->stream = user;
+    };
+    for (int i : side) {
+      if (r != PWF_OK || ce != cudaSuccess) break;
+      ce = cudaStreamWaitEvent(g->branch[i], g->ev[0], 0);
+      if (ce != cudaSuccess) break;
+      run_class(i, g->branch[i]);
       if (r == PWF_OK) ce = cudaEventRecord(g->ev[1 + i], g->branch[i]);
-      if (r == PWF_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(g->main, g->ev[1 + i], 0);
+    }
+    for (int i : chain) {
+      if (r != PWF_OK || ce != cudaSuccess) break;
+      run_class(i, g->main);
+    }
+    for (int i : side) {
+      if (r != PWF_OK || ce != cudaSuccess) break;
+      ce = cudaStreamWaitEvent(g->main, g->ev[1 + i], 0);
     }
     cudaError_t ce2 = cudaStreamEndCapture(g->main, &graph);
     for (pwf_plan* p : g->plans) p->stream = user;

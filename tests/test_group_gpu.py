@@ -78,3 +78,34 @@ def test_group_matches_individual_solves_and_oracle(pwf):
         pwf.pwf_group_destroy(g)
         for p in plans:
             p.close()
+
+
+def test_group_chains_large_classes_and_matches_individual_solves(pwf):
+    # two classes that fill the GPU on their own (>= 8 Mi pixels: solved one
+    # after another in the graph) and one small class on a side branch
+    iters = 3
+    classes = [(1024, 1024, 8), (2048, 2048, 3), (128, 128, 2)]
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    plans, ys, ts, psis, descs = [], [], [], [], []
+    for ny, nx, batch in classes:
+        geom = geometry(W2, ny, nx)
+        d = pwf.PlanDesc(batch, ny, nx, geom.pixel, geom.wavelength, geom.L1, geom.L2, geom.xcoh, geom.ycoh,
+                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta)
+        plans.append(pwf.Plan(d))
+        ys.append(0.5 + torch.rand((batch, ny, nx), generator=gen, device="cuda"))
+        ts.append(dev(to_c64(S.diffuser(ny, nx, S.rng_for(5, ny)))))
+        psis.append(torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda"))
+        descs.append(d)
+    g = pwf.pwf_group_create(plans)
+    try:
+        pwf.pwf_group_solve(g, ys, ts, psis, iters)
+        torch.cuda.synchronize()
+        for k, d in enumerate(descs):
+            with pwf.Plan(d) as alone:
+                p = torch.zeros_like(psis[k])
+                alone.solve(ys[k], ts[k], p, iters)
+            assert torch.equal(p, psis[k]), k
+    finally:
+        pwf.pwf_group_destroy(g)
+        for p in plans:
+            p.close()
