@@ -532,25 +532,29 @@ def main():
             psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
             y_d = torch.empty_like(y)
             t_d = torch.empty_like(t)
-            times = []
+            times, parts = [], []
             for rep in range(3):
                 torch.cuda.synchronize()
-                b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                b0.record(stream)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record(stream)
                 y_d.copy_(y_h, non_blocking=True)
                 t_d.copy_(t_h, non_blocking=True)
+                ev[1].record(stream)
                 psi.zero_()
                 plan.solve(y_d, t_d, psi, e2e_iters, read_back=False)
+                ev[2].record(stream)
                 psi_h.copy_(psi, non_blocking=True)
-                b1.record(stream)
+                ev[3].record(stream)
                 torch.cuda.synchronize()
                 if rep > 0:
-                    times.append(b0.elapsed_time(b1))
+                    times.append(ev[0].elapsed_time(ev[3]))
+                    parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
             ems = sum(times) / len(times)
             extras["e2e"] = {"value": mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
                              "h2d_bytes_per_step": int(y.numel() * 4 + t.numel() * 8),
                              "d2h_bytes_per_step": int(psi.numel() * 8),
-                             "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers"}
+                             "step": f"one pwf_solve call of {e2e_iters} iterations with host buffers",
+                             "ms_h2d_solve_d2h": [sum(p[i] for p in parts) / len(parts) for i in range(3)]}
             del y_h, psi_h
 
         # the same series with partial coherence as 9 tilted source modes
