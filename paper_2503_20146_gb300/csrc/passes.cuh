@@ -377,6 +377,12 @@ __host__ __device__ constexpr size_t colp_smem_bytes(int n, int c) { return 2 * 
 __host__ __device__ constexpr int col_min_blocks(int threads, int ept = 16) {
   return ept >= 32 ? (threads >= 512 ? 1 : 2) : (threads >= 512 ? 1 : threads >= 256 ? 3 : 4);
 }
+// COL_PRECOND_REG holds two transforms' values per thread: at most two CTAs
+// per SM so that they stay in registers
+template <int OP>
+__host__ __device__ constexpr int col_min_blocks_op(int threads, int ept = 16) {
+  return OP == COL_PRECOND_REG && col_min_blocks(threads, ept) > 2 ? 2 : col_min_blocks(threads, ept);
+}
 
 // the filter step and the inverse transform of one tile (v holds the forward
 // spectrum of the column in slots of the last forward radix)
@@ -428,7 +434,7 @@ __device__ __forceinline__ void col_tile_filter(const PassArgs& a, const L& sm, 
 }
 
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
     col_kernel(const PassArgs a) {
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
@@ -483,7 +489,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The copy of tile k+1 is one cp.async commit group (16-byte chunks); the wait
 // for tile k is cp.async.wait_group 1, which returns once that group landed.
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
     col_kernel_pipe(const PassArgs a, int nproj) {
   constexpr int EPT = ept_for(N);
   constexpr int NT = col_threads(N, C);
