@@ -51,6 +51,12 @@ PASS_BYTES_PER_PX = {
     "col_precond_reg": 24,  # two fields in, one out
     "row_nesterov_fft": 52, # field, psi, phi, Re g in; phi, psi, field out
     "row_coh_resid": 20,    # field in, y in, field out
+    # source-mode variant (per mode; see modal_bytes_per_px)
+    "col_mode_fwd": 16,     # shifted column in, field out
+    "row_mode_int": 24,     # field in, v_j out, intensity accumulated
+    "modal_resid": 12,      # intensity, y in; G out
+    "row_mode_vg": 20,      # v_j, G in; field out
+    "col_mode_back": 24,    # field in, spectrum accumulated
     "finalize": 0,
 }
 

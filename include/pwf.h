@@ -255,7 +255,7 @@ pwf_status pwf_state_load(pwf_plan* plan, pwf_state* state, const void* host_buf
  * of PWF_MAX_PASSES) and its static name (pass_names, HOST array of
  * PWF_MAX_PASSES pointers); *n_passes receives the count. psi is updated as by
  * pwf_solve. Synchronises. PWF_ERR_UNSUPPORTED for PWF_FLAG_PLAIN plans. */
-#define PWF_MAX_PASSES 32
+#define PWF_MAX_PASSES 256
 long long pwf_plan_launch_count(const pwf_plan* plan);
 /* Writes a one-line description of the plan (sizes and the column-pass shape
  * chosen per pass, e.g. "col_q=C8p" = 8 columns per tile, pipelined) into buf

@@ -903,9 +903,11 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 }
 
 // The same passes with the pair of adjacent columns (col, col + 1) per thread
-// (shared indices, twiddles and barriers; 16-byte exchanges). The shifted
-// columns (col - mx, col + 1 - mx) are adjacent but not 16-byte aligned for
-// odd mx (and wrap at the edge), so they move as two 8-byte accesses.
+// (shared indices, twiddles and barriers; 16-byte exchanges). Each thread owns
+// an aligned pair on the unshifted side (CM_FWD's output, CM_BACK's
+// accumulated output); the shifted columns (col -/+ mx, ...) are adjacent but
+// not 16-byte aligned for odd mx (and wrap at the edge), so they are read as
+// two 8-byte accesses.
 template <int N, int MOP, int C>
 __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const PassArgs a) {
   constexpr int EPT = ept_for(N);
@@ -915,9 +917,13 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
   const int tid = threadIdx.x;
   const int c2 = tid % (C / 2), t = tid / (C / 2);
   const int proj = blockIdx.y + a.proj0;
-  const int col = blockIdx.x * C + 2 * c2;
+  const int col = blockIdx.x * C + 2 * c2;  // the thread's aligned pair of columns
   if (a.active != nullptr && a.active[proj] == 0) return;
-  const int sh0 = ((col - a.mode_mx) % a.nx + a.nx) % a.nx;
+  // the other pair: CM_FWD reads columns col - mx, CM_BACK reads col + mx
+  // (and writes the aligned pair), so the read-modify-write of the
+  // accumulated spectrum stays 16-byte aligned
+  const int dm = MOP == CM_FWD ? -a.mode_mx : a.mode_mx;
+  const int sh0 = ((col + dm) % a.nx + a.nx) % a.nx;
   const int sh1 = sh0 + 1 < a.nx ? sh0 + 1 : 0;
   const size_t pb = (size_t)proj * a.ny * a.nx;
   const size_t ld = (size_t)a.nx;
@@ -935,14 +941,17 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
   } else {
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const float4 q = *reinterpret_cast<const float4*>(a.in + pb + col + (size_t)slot_index<N, RS>(t, j) * ld);
-      v[j] = make_float2(q.x, q.y);
-      u[j] = make_float2(q.z, q.w);
+      const size_t o = pb + (size_t)slot_index<N, RS>(t, j) * ld;
+      v[j] = a.in[o + sh0];
+      u[j] = a.in[o + sh1];
     }
   }
   fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
   {
-    const float2 qa = cscale(__ldg(&a.qx[col]), a.scale), qb = cscale(__ldg(&a.qx[col + 1]), a.scale);
+    // Q1 is indexed by the column in the mode's own frame: the output column
+    // for CM_FWD, the input column for CM_BACK
+    const int k0 = MOP == CM_FWD ? col : sh0, k1 = MOP == CM_FWD ? col + 1 : sh1;
+    const float2 qa = cscale(__ldg(&a.qx[k0]), a.scale), qb = cscale(__ldg(&a.qx[k1]), a.scale);
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const float2 qy = __ldg(&a.qy[slot_index<N, RK>(t, j)]);
@@ -963,11 +972,14 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
     for (int j = 0; j < EPT; j++) {
       const int y = slot_index<N, RS>(t, j);
       const float2 m = __ldg(&a.cis_y[(my * y) % N]);
-      float2 r0 = cscale(cmulc(v[j], m), a.mode_w), r1 = cscale(cmulc(u[j], m), a.mode_w);
-      const size_t o0 = pb + sh0 + (size_t)y * ld, o1 = pb + sh1 + (size_t)y * ld;
-      if (a.accumulate) r0 = cadd(r0, a.out[o0]), r1 = cadd(r1, a.out[o1]);
-      a.out[o0] = r0;
-      a.out[o1] = r1;
+      const float2 r0 = cscale(cmulc(v[j], m), a.mode_w), r1 = cscale(cmulc(u[j], m), a.mode_w);
+      float4* o = reinterpret_cast<float4*>(a.out + pb + col + (size_t)y * ld);
+      float4 q = make_float4(r0.x, r0.y, r1.x, r1.y);
+      if (a.accumulate) {
+        const float4 old = *o;
+        q = make_float4(q.x + old.x, q.y + old.y, q.z + old.z, q.w + old.w);
+      }
+      *o = q;
     }
   }
 }

@@ -300,7 +300,7 @@ def pwf_state_load(plan, state, data: bytes):
     _check(load().pwf_state_load(plan, state, buf, len(data)), "pwf_state_load", plan)
 
 
-MAX_PASSES = 32
+MAX_PASSES = 256
 
 
 def pwf_plan_launch_count(plan) -> int:
