@@ -491,3 +491,27 @@ def test_joint_refinement_lowers_the_loss_from_a_perturbed_diffuser():
     joint = O.joint_pwf(y, t0, g, 25, 3e-3)
     assert joint.losses[-1] < 0.97 * fixed.losses[-1]
     assert not np.array_equal(joint.t, t0)
+
+
+def test_linear_pieces_are_adjoint_to_1e_12():
+    # <A x, y> = <x, A^H y> for every linear piece of Algorithm S2: the Filters
+    # with the real, even windows (IOTF, P^-1, Gamma^2; self-adjoint), the
+    # propagations (adjoint P(-L)), the multiplication by t (adjoint conj(t))
+    rng = np.random.default_rng(31)
+    g = geom(24, 20, xcoh=6e-6, ycoh=5e-6)
+    x, y = crandn(rng, (24, 20)), crandn(rng, (24, 20))
+    t = crandn(rng, (24, 20))
+
+    def check(A, AH):
+        lhs, rhs = np.vdot(y, A(x)), np.vdot(AH(y), x)
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0), (lhs, rhs)
+
+    for W in (O.iotf(g), O.precond_filter(g), O.reg_window(g)):
+        check(lambda v, W=W: O.Filter(v, W), lambda v, W=W: O.Filter(v, W))
+    for L in (g.L1, g.L2):
+        check(lambda v, L=L: O.FreePropagation(v, g, L), lambda v, L=L: O.FreePropagation(v, g, -L))
+    check(lambda v: t * v, lambda v: np.conj(t) * v)
+    # the chain of Algorithm S2's back-propagation is the adjoint of the forward chain
+    fwd = lambda v: O.FreePropagation(t * O.FreePropagation(v, g, g.L1), g, g.L2)
+    bwd = lambda v: O.FreePropagation(np.conj(t) * O.FreePropagation(v, g, -g.L2), g, -g.L1)
+    check(fwd, bwd)
