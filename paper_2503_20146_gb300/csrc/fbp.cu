@@ -17,7 +17,8 @@
 //     row without bounds checks and gets zero outside the detector; each
 //     column holds the record (q[o], q[o+1] - q[o]), so one 16-byte load gives
 //     both taps of the linear interpolation.
-//   * fbp_backproject_kernel: one thread per (x, 8 values of z) of one slice;
+//   * fbp_backproject_kernel: one thread per (x, 8 values of z) of one slice
+//     (warps laid out as 8 x 4 voxel patches);
 //     per angle, s = x cos(theta) + z sin(theta), linear interpolation
 //     q[j] + w (q[j+1] - q[j]) from one record, accumulation in FP32. The angle table sits in shared
 //     memory; the filtered rows of one slice are read through L1/L2 (a 32 x 64
@@ -127,8 +128,12 @@ __global__ void __launch_bounds__(BP_TX * BP_TY)
   const int tid = threadIdx.y * BP_TX + threadIdx.x;
   for (int i = tid; i < n_angles; i += BP_TX * BP_TY) scs[i] = cs[i];
   __syncthreads();
-  const int x = blockIdx.x * BP_TX + threadIdx.x;
-  const int zb = blockIdx.y * (BP_TY * BP_ZPT) + threadIdx.y;
+  // each warp covers a compact 8 (x) by 4 (z) patch per z step, so that its
+  // lanes' detector positions span at most 8|cos| + 4|sin| + 1 records (two
+  // 128-byte wavefronts) instead of the 32|cos| + 1 of a 32-voxel row
+  const int lane = tid & 31, warp = tid >> 5;
+  const int x = blockIdx.x * BP_TX + (warp & 3) * 8 + (lane & 7);
+  const int zb = blockIdx.y * (BP_TY * BP_ZPT) + (warp >> 2) * 4 + (lane >> 3);
   const int y = blockIdx.z;
   const float half = 0.5f * (float)nx - 0.5f;  // detector index of s = 0
   // voxels past the grid (tile overhang) compute on the last row / column,
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(BP_TX * BP_TY)
   float zc[BP_ZPT];
 #pragma unroll
   for (int m = 0; m < BP_ZPT; m++) {
-    const int z = zb + m * BP_TY;
+    const int z = zb + m * BP_TY;  // z steps of 8: the block's 8 rows of patches
     zc[m] = (float)(z < nx ? z : nx - 1) - half;
   }
   float2 acc[BP_ZPT];
