@@ -1,0 +1,76 @@
+"""Degenerate and limit cases on the CUDA path: zero iterations leave the
+state untouched, a single projection angle in FBP, and the largest supported
+grid (2048 x 2048) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fbp_oracle as F
+from oracle import pwf_oracle as O
+from paper_2503_20146_gb300 import synth as S
+
+from _cases import blob_batch, geometry, rel_l2, to_c64, to_f32
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+W2 = S.WORKLOADS["blob512_iotf"]
+
+
+@pytest.fixture(scope="module")
+def pwf():
+    from paper_2503_20146_gb300 import _build
+    _build.build()
+    from paper_2503_20146_gb300 import pwf as P
+    P.load()
+    return P
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def plan_for(P, g, batch):
+    return P.Plan(P.PlanDesc(batch, g.ny, g.nx, g.pixel, g.wavelength, g.L1, g.L2, g.xcoh, g.ycoh, g.gamma,
+                             g.alpha.real, g.alpha.imag, g.eta))
+
+
+def test_zero_iterations_change_nothing(pwf):
+    g = geometry(W2, 128, 96)
+    psi0, t = blob_batch(W2, 2, 128, 96)
+    y = dev(to_f32(np.ones((2, 128, 96))))
+    with plan_for(pwf, g, 2) as plan:
+        psi = dev(to_c64(psi0))
+        td = dev(to_c64(t))
+        before_psi, before_t = psi.clone(), td.clone()
+        it, _ = plan.solve(y, td, psi, 0)
+        assert list(it) == [0, 0]
+        plan.solve_joint(y, td, psi, 0, 1e-3)
+        torch.cuda.synchronize()
+        assert torch.equal(psi, before_psi) and torch.equal(td, before_t)
+
+
+def test_fbp_single_angle_matches_oracle(pwf):
+    rng = np.random.default_rng(11)
+    psi = (rng.standard_normal((1, 2, 64)) + 1j * rng.standard_normal((1, 2, 64))).astype(np.complex64)
+    angles = np.array([0.3])
+    vol = pwf.pwf_fbp(dev(psi), angles, S.WAVELENGTH_20KEV_M, S.PIXEL_M).cpu().numpy()
+    ref = F.fbp_volume(psi.astype(np.complex128), angles, S.WAVELENGTH_20KEV_M, S.PIXEL_M)
+    assert rel_l2(vol, ref) < max(1e-5, 64 * 2.0 ** -22)
+
+
+def test_largest_grid_forward_and_gradient_match_oracle(pwf):
+    n = 2048
+    g = geometry(W2, n, n)
+    psi, t = blob_batch(W2, 1, n, n)
+    psi, t = to_c64(psi), to_c64(t)
+    y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(2).standard_normal((1, n, n)), 0, None))
+    with plan_for(pwf, g, 1) as plan:
+        f = plan.forward(dev(psi), dev(t)).cpu().numpy()[0]
+        gr, _ = plan.gradient(dev(psi), dev(t), dev(y))
+        gr = gr.cpu().numpy()[0]
+    P64, T64 = psi[0].astype(np.complex128), t.astype(np.complex128)
+    assert rel_l2(f, O.PhysicalModel(P64, T64, g)[0]) <= 1e-5
+    assert rel_l2(gr, O.gradient(P64, T64, y[0].astype(np.float64), g)[0]) <= 1e-4
