@@ -338,14 +338,22 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.aux[rb + slot_index<N, RK>(t, j)] = v[j];
+    // The second transform runs on an opaque copy of the thread index and
+    // buffer pointer: left to itself the compiler shares the two transforms'
+    // address arithmetic, keeps it live through the first one and spills.
+    int t2;
+    float2* b2;
+    asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
+    asm volatile("mov.b64 %0, %1;" : "=l"(b2) : "l"(sm.base));
+    const RowLayout<TPF, ROWS * TPF> sm2{b2, sm.bar};
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const float2 p = a.psi[rb + slot_index<N, RS>(t, j)];
+      const float2 p = a.psi[rb + slot_index<N, RS>(t2, j)];
       v[j] = make_float2(a.alpha_re * p.x, a.alpha_im * p.y);
     }
-    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+    fft_run<N, FWD>(v, sm2, t2, a.tw_fwd);
 #pragma unroll
-    for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t, j)] = v[j];
+    for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t2, j)] = v[j];
   } else if constexpr (T::fft_out) {
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
