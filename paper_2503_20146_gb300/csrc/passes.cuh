@@ -131,10 +131,21 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// exp(z) for complex z. The phase z.y is reduced to [-pi, pi] by Cody and
+// Waite's two-constant scheme: C1 = float(2 pi), C2 = float(2 pi - C1), so
+// C1 + C2 is 2 pi to within 2^-47, and an FMA per product leaves the reduced
+// phase within half an ulp plus k 2^-47 after k turns. On [-pi, pi] the
+// hardware sine and cosine are accurate to 2^-21.4 absolute; the modulus uses
+// the hardware exponential (a few ulp for |z.x| of order 1).
 __device__ __forceinline__ float2 cexpf2(float2 z) {
+  constexpr float kInv2Pi = 0.159154943091895336f;
+  constexpr float kC1 = 6.28318548202514648f;
+  constexpr float kC2 = -1.74845553146951715e-07f;
+  const float k = rintf(z.y * kInv2Pi);
+  const float r = fmaf(-k, kC2, fmaf(-k, kC1, z.y));
   float s, c;
-  sincosf(z.y, &s, &c);
-  float m = expf(z.x);
+  __sincosf(r, &s, &c);
+  const float m = __expf(z.x);
   return make_float2(m * c, m * s);
 }
 

@@ -74,3 +74,26 @@ def test_largest_grid_forward_and_gradient_match_oracle(pwf):
     P64, T64 = psi[0].astype(np.complex128), t.astype(np.complex128)
     assert rel_l2(f, O.PhysicalModel(P64, T64, g)[0]) <= 1e-5
     assert rel_l2(gr, O.gradient(P64, T64, y[0].astype(np.float64), g)[0]) <= 1e-4
+
+
+def test_large_phase_and_strong_attenuation_match_oracle(pwf):
+    # phases wrapped many times over (|Im psi| up to ~400 rad) and log-amplitudes
+    # from about -4 to 1: the complex exponential's phase reduction and modulus
+    n = 256
+    g = geometry(W2, n, n)
+    psi, t = blob_batch(W2, 2, n, n)
+    yy, xx = np.mgrid[0:n, 0:n] / n
+    psi = (30.0 * psi.real - 2.0) + 1j * (psi.imag + 2.0 * np.pi * (40.0 * xx + 23.0 * yy))
+    psi[1] = np.conj(psi[1])
+    psi, t = to_c64(psi), to_c64(t)
+    assert np.abs(psi.imag).max() > 350 and psi.real.min() < -3
+    y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(4).standard_normal((2, n, n)), 0, None))
+    with plan_for(pwf, g, 2) as plan:
+        f = plan.forward(dev(psi), dev(t)).cpu().numpy()
+        gr, _ = plan.gradient(dev(psi), dev(t), dev(y))
+        gr = gr.cpu().numpy()
+    T64 = t.astype(np.complex128)
+    for b in range(2):
+        P64 = psi[b].astype(np.complex128)
+        assert rel_l2(f[b], O.PhysicalModel(P64, T64, g)[0]) <= 1e-5
+        assert rel_l2(gr[b], O.gradient(P64, T64, y[b].astype(np.float64), g)[0]) <= 1e-4
