@@ -57,6 +57,8 @@ PASS_BYTES_PER_PX = {
     "modal_resid": 12,      # intensity, y in; G out
     "row_mode_vg": 20,      # v_j, G in; field out
     "col_mode_back": 24,    # field in, spectrum accumulated
+    "col_fft": 16,          # F_row{x} -> 2-D spectrum, in place
+    "col_ifft": 16,         # accumulated spectrum -> F_row, in place
     "finalize": 0,
 }
 
@@ -194,7 +196,9 @@ def make_workload(P, S, w, batch, device, rank=0, world=1):
 # CM_BACK 24 (spectrum accumulated) = 164 B/px; once per iteration the residual
 # 12 and ROW_GRAD_PACK + COL_PRECOND_REG + ROW_NESTEROV_FFT 112.
 def modal_bytes_per_px(k: int) -> int:
-    return 164 * k + 12 + 112
+    # per mode 164; residual 12; COL_FFT of F_row{x} and COL_IFFT of the
+    # accumulated spectrum 16 each; GRAD_PACK, PRECOND_REG, NESTEROV 112
+    return 164 * k + 12 + 32 + 112
 
 
 def plan_desc(P, w, batch, flags=0, n_modes=None):

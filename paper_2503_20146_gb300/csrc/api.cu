@@ -324,7 +324,6 @@ struct AxisTables {
   float* iotf = nullptr;
   float* u2 = nullptr;   // squared frequency, cycles per pixel
   float* stf = nullptr;  // pi gamma u^2 coh^2
-  float2* cis = nullptr; // exp(2 pi i k / n)
 };
 
 struct Mode {
@@ -450,7 +449,7 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
   if (!host_twiddles(n, FWD, twf) || !host_twiddles(n, INV, twi))
     return fail(p, PWF_ERR_UNSUPPORTED, "twiddle table layout");
   const int tlf = (int)twf.size(), tli = (int)twi.size();
-  std::vector<float2> q1(n), q2(n), cs(n);
+  std::vector<float2> q1(n), q2(n);
   std::vector<float> io(n), u2(n), st(n);
   for (int k = 0; k < n; k++) {
     const double f = fftfreq(k, n);  // cycles per pixel
@@ -462,14 +461,12 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
     io[k] = (float)std::exp(-0.5 * M_PI * u * u * coh * coh);
     u2[k] = (float)(f * f);
     st[k] = (float)(M_PI * d.gamma * u * u * coh * coh);
-    cs[k] = make_float2((float)std::cos(2.0 * M_PI * k / n), (float)std::sin(2.0 * M_PI * k / n));
   }
   pwf_status r;
   if ((r = dalloc(p, &A.tw_fwd, tlf)) || (r = dalloc(p, &A.tw_inv, tli)) || (r = dalloc(p, &A.q1, n)) ||
       (r = dalloc(p, &A.q2, n)) || (r = dalloc(p, &A.iotf, n)) || (r = dalloc(p, &A.u2, n)) ||
-      (r = dalloc(p, &A.stf, n)) || (r = dalloc(p, &A.cis, n)))
+      (r = dalloc(p, &A.stf, n)))
     return r;
-  PWF_CUDA(p, cudaMemcpy(A.cis, cs.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.tw_fwd, twf.data(), tlf * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.tw_inv, twi.data(), tli * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.q1, q1.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
@@ -684,7 +681,6 @@ cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumu
   a.tw_inv = p->ay.tw_inv;
   a.qx = p->ax.q1;
   a.qy = p->ay.q1;
-  a.cis_y = p->ay.cis;
   a.mode_mx = md.mx;
   a.mode_my = md.my;
   a.mode_w = md.w;
@@ -693,21 +689,41 @@ cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumu
                  [&] { return p->kcol->colmode[mop](a, nproj, p->stream); });
 }
 
+// X (F_row{x}) -> X^ = F_y F_row{x} in place: the modes read shifted spectra
+pwf_status spectrum_for_modes(pwf_plan* p, PassArgs a, int nproj) {
+  a.in = p->X;
+  a.out = p->X;
+  LAUNCH(p, col(p, COL_FFT, a, nproj));
+  return PWF_OK;
+}
+
+// the spectra CM_BACK accumulated in ACC -> F_y^-1 in place (the scale was
+// applied per mode)
+pwf_status accumulated_from_spectrum(pwf_plan* p, PassArgs a, int nproj) {
+  a.in = p->ACC;
+  a.out = p->ACC;
+  a.scale = 1.0f;
+  LAUNCH(p, col(p, COL_IFFT, a, nproj));
+  return PWF_OK;
+}
+
 pwf_status ensure_vstack(pwf_plan* p) {
   if (p->VSTACK) return PWF_OK;
   return dalloc(p, &p->VSTACK, p->modes.size() * (size_t)p->d.batch * p->d.ny * p->d.nx);
 }
 
-// X holds F_row{exp psi}. For every mode: propagate, store v_j (if vstack),
-// and accumulate I = sum_j w_j |v_j|^2 into `intensity`.
+// X holds F_row{exp psi} (turned into its 2-D spectrum in place: X is
+// consumed). For every mode: propagate, store v_j (if vstack), and accumulate
+// I = sum_j w_j |v_j|^2 into `intensity`.
 pwf_status modal_forward(pwf_plan* p, PassArgs a, const float2* t, float* intensity, bool store_v) {
   const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
+  if (pwf_status r = spectrum_for_modes(p, a, nproj_of(p))) return r;
   for (size_t j = 0; j < p->modes.size(); j++) {
     const Mode& md = p->modes[j];
     PassArgs b = a;
     b.in = p->X;
     b.out = p->M;
-    LAUNCH(p, colmode(p, CM_FWD, b, md, 0, nproj_of(p)));  // tilt, P1
+    LAUNCH(p, colmode(p, CM_FWD, b, md, 0, nproj_of(p)));  // tilt (a spectral shift), P1
     b.in = p->M;
     b.t = t;
     b.conj_t = 0;
@@ -724,7 +740,8 @@ pwf_status modal_forward(pwf_plan* p, PassArgs a, const float2* t, float* intens
 }
 
 // G (real, f - y or dL/df) in `G`; back-propagate every stored mode and
-// accumulate sum_j w_j F_row{conj(s_j) P1^H{conj(t) P2^H{v_j G}}} into ACC.
+// accumulate sum_j w_j F_row{conj(s_j) P1^H{conj(t) P2^H{v_j G}}} into ACC
+// (as 2-D spectra, then one inverse column pass).
 pwf_status modal_backward(pwf_plan* p, PassArgs a, const float2* t, const float* G) {
   const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
   for (size_t j = 0; j < p->modes.size(); j++) {
@@ -740,9 +757,9 @@ pwf_status modal_backward(pwf_plan* p, PassArgs a, const float2* t, const float*
     b.conj_t = 1;
     LAUNCH(p, row(p, ROW_MUL_T, b, nproj_of(p)));
     b.out = p->ACC;
-    LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, nproj_of(p)));  // P1^H, untilt, accumulate
+    LAUNCH(p, colmode(p, CM_BACK, b, md, j > 0, nproj_of(p)));  // P1^H, untilt, accumulate (spectra)
   }
-  return PWF_OK;
+  return accumulated_from_spectrum(p, a, nproj_of(p));
 }
 
 pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
@@ -1246,6 +1263,7 @@ pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const fl
     a.psi = P;
     a.out = p->X;
     LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    if ((r = spectrum_for_modes(p, a, a.B))) return r;
     for (size_t j = 0; j < p->modes.size(); j++) {
       const Mode& md = p->modes[j];
       PassArgs b = a;
@@ -1286,6 +1304,7 @@ pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const fl
       PWF_CUDA(p, cudaGetLastError());
     }
     if (grad_psi) {
+      if ((r = accumulated_from_spectrum(p, a, a.B))) return r;
       a.in = p->ACC;
       a.g_out = (float2*)grad_psi;
       a.div_maxt2 = 0;

@@ -77,11 +77,10 @@ struct PassArgs {
   int div_maxt2;           // ROW_GRAD_OUT / PACK: divide by max|t|^2
   int no_precond;          // P^-1 := 1
   int proj0;               // first projection of this launch (plain path)
-  // source-mode variant: tilt bins, weight, accumulate flag, e^(2 pi i k / n) tables
+  // source-mode variant: tilt bins, weight, accumulate flag
   int mode_mx, mode_my;
   float mode_w;
   int accumulate;
-  const float2* cis_y;     // exp(2 pi i k / ny), k = 0..ny-1
 };
 
 enum RowOp : int {
@@ -860,12 +859,18 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 // ---------------------------------------------------------------------------
 // column passes of the source-mode variant
 // ---------------------------------------------------------------------------
-// A mode s(r) = exp(2 pi i (mx x / nx + my y / ny)) shifts the row spectrum:
-// F_row{x s}(kx, y) = exp(2 pi i my y / ny) F_row{x}(kx - mx, y).
-//   CM_FWD : out column kx = F_y^-1{ Q1 scale F_y{ e^(2 pi i my y/ny) in column (kx - mx) } }
-//   CM_BACK: out column (kx - mx) (+)= w e^(-2 pi i my y/ny) F_y^-1{ conj(Q1) scale F_y{ in column kx } }
-// (indices mod nx). Reads and writes go to different buffers.
+// A mode s(r) = exp(2 pi i (mx x / nx + my y / ny)) shifts the spectrum: with
+// X^ = F_y F_row{x}, F_y F_row{x s}(kx, ky) = X^(kx - mx, ky - my). Both passes
+// therefore work on 2-D spectra, and the tilt is an index shift:
+//   CM_FWD : out column kx = F_y^-1{ Q1 scale X^(kx - mx, . - my) }      (in = X^)
+//   CM_BACK: A^(kx - mx, ky - my) (+)= w conj(Q1(kx, ky)) scale F_y{in column kx}(ky)
+// (indices mod nx, ny). CM_BACK leaves the accumulated A^ in the column
+// spectral domain; one inverse column pass after the last mode replaces the
+// per-mode inverse transforms and modulations. Reads and writes go to
+// different buffers.
 enum ColModeOp : int { CM_FWD = 0, CM_BACK = 1 };
+
+__device__ __forceinline__ int wrap_sub(int k, int m, int n) { return k >= m ? k - m : k - m + n; }
 
 template <int N, int MOP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
@@ -886,35 +891,25 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
   const int my = ((a.mode_my % N) + N) % N;
   float2 v[EPT];
   if constexpr (MOP == CM_FWD) {
+    const float2 qx = cscale(__ldg(&a.qx[col]), a.scale);
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int y = slot_index<N, RS>(t, j);
-      v[j] = cmul(a.in[pb + shifted + (size_t)y * ld], __ldg(&a.cis_y[(my * y) % N]));
+      const int ky = slot_index<N, RK>(t, j);
+      v[j] = cmul(a.in[pb + shifted + (size_t)wrap_sub(ky, my, N) * ld], cmul(qx, __ldg(&a.qy[ky])));
     }
-  } else {
-#pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = a.in[pb + col + (size_t)slot_index<N, RS>(t, j) * ld];
-  }
-  fft_run<N, FWD>(v, sm, t, a.tw_fwd);
-  {
-    const float2 qx = __ldg(&a.qx[col]);
-#pragma unroll
-    for (int j = 0; j < EPT; j++) {
-      float2 q = cmul(qx, __ldg(&a.qy[slot_index<N, RK>(t, j)]));
-      if constexpr (MOP == CM_BACK) q = cconj(q);
-      v[j] = cscale(cmul(v[j], q), a.scale);
-    }
-  }
-  fft_run<N, INV>(v, sm, t, a.tw_inv);
-  if constexpr (MOP == CM_FWD) {
+    fft_run<N, INV>(v, sm, t, a.tw_inv);
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[pb + col + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
   } else {
 #pragma unroll
+    for (int j = 0; j < EPT; j++) v[j] = a.in[pb + col + (size_t)slot_index<N, RS>(t, j) * ld];
+    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+    const float2 qx = cscale(__ldg(&a.qx[col]), a.scale * a.mode_w);
+#pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int y = slot_index<N, RS>(t, j);
-      float2 r = cscale(cmulc(v[j], __ldg(&a.cis_y[(my * y) % N])), a.mode_w);
-      const size_t o = pb + shifted + (size_t)y * ld;
+      const int ky = slot_index<N, RK>(t, j);
+      float2 r = cmulc(v[j], cmul(qx, __ldg(&a.qy[ky])));
+      const size_t o = pb + shifted + (size_t)wrap_sub(ky, my, N) * ld;
       if (a.accumulate) r = cadd(r, a.out[o]);
       a.out[o] = r;
     }
@@ -950,38 +945,17 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
   const int my = ((a.mode_my % N) + N) % N;
   float2 v[EPT], u[EPT];
   if constexpr (MOP == CM_FWD) {
+    // Q1 at the output columns (the mode's own frame)
+    const float2 qa = cscale(__ldg(&a.qx[col]), a.scale), qb = cscale(__ldg(&a.qx[col + 1]), a.scale);
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int y = slot_index<N, RS>(t, j);
-      const float2 m = __ldg(&a.cis_y[(my * y) % N]);
-      v[j] = cmul(a.in[pb + sh0 + (size_t)y * ld], m);
-      u[j] = cmul(a.in[pb + sh1 + (size_t)y * ld], m);
+      const int ky = slot_index<N, RK>(t, j);
+      const float2 qy = __ldg(&a.qy[ky]);
+      const size_t o = pb + (size_t)wrap_sub(ky, my, N) * ld;
+      v[j] = cmul(a.in[o + sh0], cmul(qa, qy));
+      u[j] = cmul(a.in[o + sh1], cmul(qb, qy));
     }
-  } else {
-#pragma unroll
-    for (int j = 0; j < EPT; j++) {
-      const size_t o = pb + (size_t)slot_index<N, RS>(t, j) * ld;
-      v[j] = a.in[o + sh0];
-      u[j] = a.in[o + sh1];
-    }
-  }
-  fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
-  {
-    // Q1 is indexed by the column in the mode's own frame: the output column
-    // for CM_FWD, the input column for CM_BACK
-    const int k0 = MOP == CM_FWD ? col : sh0, k1 = MOP == CM_FWD ? col + 1 : sh1;
-    const float2 qa = cscale(__ldg(&a.qx[k0]), a.scale), qb = cscale(__ldg(&a.qx[k1]), a.scale);
-#pragma unroll
-    for (int j = 0; j < EPT; j++) {
-      const float2 qy = __ldg(&a.qy[slot_index<N, RK>(t, j)]);
-      float2 q0 = cmul(qa, qy), q1 = cmul(qb, qy);
-      if constexpr (MOP == CM_BACK) q0 = cconj(q0), q1 = cconj(q1);
-      v[j] = cmul(v[j], q0);
-      u[j] = cmul(u[j], q1);
-    }
-  }
-  fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
-  if constexpr (MOP == CM_FWD) {
+    fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
 #pragma unroll
     for (int j = 0; j < EPT; j++)
       *reinterpret_cast<float4*>(a.out + pb + col + (size_t)slot_index<N, RS>(t, j) * ld) =
@@ -989,10 +963,20 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
   } else {
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int y = slot_index<N, RS>(t, j);
-      const float2 m = __ldg(&a.cis_y[(my * y) % N]);
-      const float2 r0 = cscale(cmulc(v[j], m), a.mode_w), r1 = cscale(cmulc(u[j], m), a.mode_w);
-      float4* o = reinterpret_cast<float4*>(a.out + pb + col + (size_t)y * ld);
+      const size_t o = pb + (size_t)slot_index<N, RS>(t, j) * ld;
+      v[j] = a.in[o + sh0];
+      u[j] = a.in[o + sh1];
+    }
+    fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
+    // Q1 at the input columns (the mode's own frame), weight folded in
+    const float ws = a.scale * a.mode_w;
+    const float2 qa = cscale(__ldg(&a.qx[sh0]), ws), qb = cscale(__ldg(&a.qx[sh1]), ws);
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int ky = slot_index<N, RK>(t, j);
+      const float2 qy = __ldg(&a.qy[ky]);
+      const float2 r0 = cmulc(v[j], cmul(qa, qy)), r1 = cmulc(u[j], cmul(qb, qy));
+      float4* o = reinterpret_cast<float4*>(a.out + pb + col + (size_t)wrap_sub(ky, my, N) * ld);
       float4 q = make_float4(r0.x, r0.y, r1.x, r1.y);
       if (a.accumulate) {
         const float4 old = *o;
