@@ -249,6 +249,9 @@ def peaks():
 # ----------------------------------------------------------------------------
 # oracle timing on the host (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
+CPU_SAMPLE_ITERS = 24  # ~0.5 s per 1024^2 iteration on one host core
+
+
 def oracle_sample(w, n_proj, seed_iters):
     """Times the FP64 oracle on n_proj projections of the workload's size
     (blob objects stand in for the phantom: the oracle's cost does not depend
@@ -610,10 +613,11 @@ def main():
             del series
 
         if leg("cpu"):
-            # FP64 oracle on the host cores, bounded sample
-            dt, work = oracle_sample(w, 1, 3)
+            # FP64 oracle on the host cores, bounded sample (~10 s of CPU work)
+            dt, work = oracle_sample(w, 1, CPU_SAMPLE_ITERS)
             extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                      "sample": f"1 projection of {w.ny}x{w.nx}, 3 iterations, numpy FP64 (single thread)",
+                                      "sample": f"1 projection of {w.ny}x{w.nx}, {CPU_SAMPLE_ITERS} iterations, "
+                                                "numpy FP64 (single thread)",
                                       "seconds": dt}
 
     if rank == 0:
