@@ -163,6 +163,25 @@ pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_h
 pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
                      double corr_tol, int32_t* iters_host, double* loss_host);
 
+/* Algorithm S1 (as pwf_solve) on HOST buffers: y (float32 [B][ny][nx]), t
+ * (complex64 [ny][nx]) and psi (complex64 [B][ny][nx]; the initial guess when
+ * psi_is_input != 0, else Algorithm S1's psi = 0 and psi_host is output only;
+ * the result on return). The batch streams through the device in chunks of
+ * `chunk` projections (0: the largest divisor of B not above B/4, rounded up;
+ * otherwise chunk must divide B, else PWF_ERR_INVALID_ARG): the host-to-device
+ * copy of chunk k + 1 and the device-to-host copy of chunk k - 1 overlap the
+ * solve of chunk k. Each projection's iterates are those of pwf_solve on the
+ * same inputs up to the column-pass shapes the chunk-sized plans pick.
+ * Host buffers should be page-locked (cudaHostAlloc, or torch's pin_memory())
+ * for the copies to overlap; pageable memory works but serialises them.
+ * iters_host / loss_host: HOST arrays of length B (may be NULL). Returns after
+ * the results are on the host; ordered after the work queued on the plan's
+ * stream. The first call (and a call with another chunk) allocates two
+ * chunk-sized plans and device slots: two chunks of y and psi, one t. */
+pwf_status pwf_solve_host(pwf_plan* plan, const float* y_host, const void* t_host, void* psi_host,
+                          int32_t psi_is_input, int32_t max_iter, double corr_tol, int32_t chunk,
+                          int32_t* iters_host, double* loss_host);
+
 /* Joint refinement of the shared diffuser (Methods, "Diffuser transmission
  * function", and Fig. S12: t is updated across all projections). Runs
  * max_iter iterations of Algorithm S1 over the batch (no stopping rule) and,

@@ -341,6 +341,8 @@ struct pwf_state {
   DevIter* it = nullptr;
 };
 
+struct HostPipe;  // solve from host buffers (pwf_solve_host)
+
 struct pwf_plan {
   pwf_plan_desc d{};
   cudaStream_t stream = nullptr;
@@ -391,6 +393,7 @@ struct pwf_plan {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<const char*> prof_names;
   size_t prof_n = 0;
+  HostPipe* pipe = nullptr;  // created by the first pwf_solve_host
 };
 
 namespace {
@@ -1148,8 +1151,11 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   return PWF_OK;
 }
 
+static void host_pipe_destroy(HostPipe* hp);
+
 pwf_status pwf_plan_destroy(pwf_plan* p) {
   if (!p) return PWF_ERR_INVALID_ARG;
+  if (p->pipe) host_pipe_destroy(p->pipe);
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->solve_state) pwf_state_destroy(p->solve_state);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -1537,6 +1543,149 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
     }
   }
   if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
+  return PWF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve from host buffers
+// ---------------------------------------------------------------------------
+// The batch streams through the device in chunks of `chunk` projections and
+// two device slots, each with a plan of batch `chunk` (its own workspace and
+// captured iteration graph): while chunk k is solved on the run stream, the
+// inputs of chunk k + 1 arrive on the copy-in stream and the result of chunk
+// k - 1 leaves on the copy-out stream. Per-projection results and each
+// chunk's status word go to pinned staging on the run stream.
+struct HostPipe {
+  int chunk = 0;
+  pwf_plan* sub[2] = {nullptr, nullptr};
+  float* y[2] = {nullptr, nullptr};
+  float2* psi[2] = {nullptr, nullptr};
+  float2* t = nullptr;
+  cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+  cudaEvent_t start = nullptr, in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
+  int* h_iters = nullptr;   // pinned, [B]
+  double* h_loss = nullptr; // pinned, [B]
+  DevIter* h_it = nullptr;  // pinned, one per chunk
+};
+
+static void host_pipe_destroy(HostPipe* hp) {
+  if (!hp) return;
+  for (int s = 0; s < 2; s++) {
+    if (hp->sub[s]) pwf_plan_destroy(hp->sub[s]);
+    if (hp->y[s]) cudaFree(hp->y[s]);
+    if (hp->psi[s]) cudaFree(hp->psi[s]);
+    for (cudaEvent_t e : {hp->in_done[s], hp->run_done[s], hp->out_done[s]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (hp->t) cudaFree(hp->t);
+  if (hp->start) cudaEventDestroy(hp->start);
+  for (cudaStream_t st : {hp->s_in, hp->s_run, hp->s_out})
+    if (st) cudaStreamDestroy(st);
+  if (hp->h_iters) cudaFreeHost(hp->h_iters);
+  if (hp->h_loss) cudaFreeHost(hp->h_loss);
+  if (hp->h_it) cudaFreeHost(hp->h_it);
+  delete hp;
+}
+
+// the largest divisor of B that is at most ceil(B / 4): four chunks when B allows
+static int default_chunk(int B) {
+  const int cap = (B + 3) / 4;
+  for (int c = cap; c > 1; c--)
+    if (B % c == 0) return c;
+  return 1;
+}
+
+static pwf_status host_pipe_ensure(pwf_plan* p, int chunk) {
+  if (p->pipe && p->pipe->chunk == chunk) return PWF_OK;
+  if (p->pipe) {
+    host_pipe_destroy(p->pipe);
+    p->pipe = nullptr;
+  }
+  HostPipe* hp = new HostPipe();
+  hp->chunk = chunk;
+  const size_t npx = (size_t)p->d.ny * p->d.nx, per = (size_t)chunk * npx;
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t* st : {&hp->s_in, &hp->s_run, &hp->s_out})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
+  for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+    for (cudaEvent_t* ev : {&hp->in_done[s], &hp->run_done[s], &hp->out_done[s]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&hp->y[s], per * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&hp->psi[s], per * sizeof(float2));
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&hp->t, npx * sizeof(float2));
+  if (e == cudaSuccess) e = cudaHostAlloc(&hp->h_iters, p->d.batch * sizeof(int), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&hp->h_loss, p->d.batch * sizeof(double), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&hp->h_it, p->d.batch * sizeof(DevIter), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    host_pipe_destroy(hp);
+    return e == cudaErrorMemoryAllocation ? fail(p, PWF_ERR_NOMEM, "host pipeline buffers")
+                                          : cuda_fail(p, e, "host pipeline setup");
+  }
+  pwf_plan_desc d = p->d;
+  d.batch = chunk;
+  d.stream = hp->s_run;
+  for (int s = 0; s < 2; s++) {
+    pwf_status r = pwf_plan_create(&d, &hp->sub[s]);
+    if (r) {
+      host_pipe_destroy(hp);
+      return fail(p, r, "host pipeline: plan for one chunk");
+    }
+  }
+  p->pipe = hp;
+  return PWF_OK;
+}
+
+pwf_status pwf_solve_host(pwf_plan* p, const float* y_host, const void* t_host, void* psi_host, int32_t psi_is_input,
+                          int32_t max_iter, double corr_tol, int32_t chunk, int32_t* iters_host, double* loss_host) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!y_host || !t_host || !psi_host || max_iter < 0 || chunk < 0) return PWF_ERR_INVALID_ARG;
+  const int B = p->d.batch;
+  if (chunk == 0) chunk = default_chunk(B);
+  if (chunk > B || B % chunk != 0) return fail(p, PWF_ERR_INVALID_ARG, "chunk must divide the batch");
+  if ((r = host_pipe_ensure(p, chunk))) return r;
+  HostPipe& hp = *p->pipe;
+  const size_t npx = (size_t)p->d.ny * p->d.nx, per = (size_t)chunk * npx;
+  const float* yh = y_host;
+  float2* ph = static_cast<float2*>(psi_host);
+  const int nch = B / chunk;
+  // after whatever the caller queued on the plan's stream
+  PWF_CUDA(p, cudaEventRecord(hp.start, p->stream));
+  PWF_CUDA(p, cudaStreamWaitEvent(hp.s_in, hp.start, 0));
+  PWF_CUDA(p, cudaStreamWaitEvent(hp.s_run, hp.start, 0));
+  PWF_CUDA(p, cudaMemcpyAsync(hp.t, t_host, npx * sizeof(float2), cudaMemcpyHostToDevice, hp.s_in));
+  for (int k = 0; k < nch; k++) {
+    const int s = k & 1;
+    if (k >= 2) PWF_CUDA(p, cudaStreamWaitEvent(hp.s_in, hp.out_done[s], 0));  // slot s is free again
+    PWF_CUDA(p, cudaMemcpyAsync(hp.y[s], yh + k * per, per * sizeof(float), cudaMemcpyHostToDevice, hp.s_in));
+    if (psi_is_input)
+      PWF_CUDA(p, cudaMemcpyAsync(hp.psi[s], ph + k * per, per * sizeof(float2), cudaMemcpyHostToDevice, hp.s_in));
+    else
+      PWF_CUDA(p, cudaMemsetAsync(hp.psi[s], 0, per * sizeof(float2), hp.s_in));
+    PWF_CUDA(p, cudaEventRecord(hp.in_done[s], hp.s_in));
+    PWF_CUDA(p, cudaStreamWaitEvent(hp.s_run, hp.in_done[s], 0));
+    pwf_plan* q = hp.sub[s];
+    if ((r = solve_impl(q, hp.y[s], hp.t, hp.psi[s], max_iter, corr_tol, nullptr, nullptr, -1.0)))
+      return fail(p, r, q->err);
+    const pwf_state* st = q->solve_state;
+    PWF_CUDA(p, cudaMemcpyAsync(hp.h_iters + k * chunk, st->iters, chunk * sizeof(int), cudaMemcpyDeviceToHost,
+                                hp.s_run));
+    PWF_CUDA(p, cudaMemcpyAsync(hp.h_loss + k * chunk, st->loss, chunk * sizeof(double), cudaMemcpyDeviceToHost,
+                                hp.s_run));
+    PWF_CUDA(p, cudaMemcpyAsync(hp.h_it + k, st->it, sizeof(DevIter), cudaMemcpyDeviceToHost, hp.s_run));
+    PWF_CUDA(p, cudaEventRecord(hp.run_done[s], hp.s_run));
+    PWF_CUDA(p, cudaStreamWaitEvent(hp.s_out, hp.run_done[s], 0));
+    PWF_CUDA(p, cudaMemcpyAsync(ph + k * per, hp.psi[s], per * sizeof(float2), cudaMemcpyDeviceToHost, hp.s_out));
+    PWF_CUDA(p, cudaEventRecord(hp.out_done[s], hp.s_out));
+  }
+  PWF_CUDA(p, cudaStreamSynchronize(hp.s_out));
+  PWF_CUDA(p, cudaStreamSynchronize(hp.s_run));
+  if (iters_host) std::memcpy(iters_host, hp.h_iters, B * sizeof(int));
+  if (loss_host) std::memcpy(loss_host, hp.h_loss, B * sizeof(double));
+  for (int k = 0; k < nch; k++)
+    if (hp.h_it[k].nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss");
   return PWF_OK;
 }
 

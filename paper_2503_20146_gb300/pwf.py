@@ -103,6 +103,7 @@ def load(path: str | None = None):
         "pwf_group_solve": ([_P, _P, _P, _P, _P, i32, f64], i32),
         "pwf_group_read": ([_P, i32, _P, _P], i32),
         "pwf_solve_joint": ([_P, _P, _P, _P, i32, f64, _P, _P], i32),
+        "pwf_solve_host": ([_P, _P, _P, _P, i32, i32, f64, i32, _P, _P], i32),
         "pwf_fbp_workspace_bytes": ([i32, i32, i32], ctypes.c_size_t),
         "pwf_fbp": ([_P, i32, i32, i32, ctypes.POINTER(f64), f64, f64, _P, _P, ctypes.c_size_t, _P], i32),
         "pwf_calibrate_coherence": ([_P, _P, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)], i32),
@@ -129,6 +130,22 @@ def _ptr(x):
         raise ValueError("libpwf takes CUDA device tensors")
     if not x.is_contiguous():
         raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _host_ptr(x, dtype: str, numel: int):
+    """Pointer to a contiguous HOST array (torch CPU tensor or numpy array) of
+    `numel` elements of `dtype` ("float32" or "complex64")."""
+    import numpy as np
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.dtype(dtype) or not x.flags.c_contiguous or x.size != numel:
+            raise ValueError(f"expected a C-contiguous {dtype} numpy array of {numel} elements")
+        return ctypes.c_void_p(x.ctypes.data)
+    import torch
+    if not isinstance(x, torch.Tensor) or x.is_cuda:
+        raise TypeError("expected a host (CPU) torch.Tensor or numpy array")
+    if x.dtype != getattr(torch, dtype) or not x.is_contiguous() or x.numel() != numel:
+        raise ValueError(f"expected a contiguous {dtype} tensor of {numel} elements")
     return ctypes.c_void_p(x.data_ptr())
 
 
@@ -265,6 +282,24 @@ def pwf_solve(plan, y, t, psi, max_iter: int, corr_tol: float = 0.0, batch: int 
                             None if it is None else it.ctypes.data_as(_P),
                             None if loss is None else loss.ctypes.data_as(_P)), "pwf_solve", plan)
     return (it, loss) if batch is not None else None
+
+
+def pwf_solve_host(plan, desc: "PlanDesc", y, t, psi, max_iter: int, corr_tol: float = 0.0,
+                   psi_is_input: bool = True, chunk: int = 0):
+    """Algorithm S1 on host buffers (torch CPU tensors, ideally pinned, or numpy
+    arrays): psi is read (psi_is_input) and written in place. Chunks of the
+    batch stream through the device with the copies overlapping the solve.
+    Returns (iters, loss) numpy arrays."""
+    import numpy as np
+    B, n = desc.batch, desc.ny * desc.nx
+    it = np.zeros(B, np.int32)
+    loss = np.zeros(B, np.float64)
+    _on_current_stream(plan)
+    _check(load().pwf_solve_host(plan, _host_ptr(y, "float32", B * n), _host_ptr(t, "complex64", n),
+                                 _host_ptr(psi, "complex64", B * n), int(bool(psi_is_input)), int(max_iter),
+                                 float(corr_tol), int(chunk), it.ctypes.data_as(_P), loss.ctypes.data_as(_P)),
+           "pwf_solve_host", plan)
+    return it, loss
 
 
 def pwf_solve_joint(plan, y, t, psi, max_iter: int, eta_t: float, batch: int | None = None):
@@ -467,6 +502,9 @@ class Plan:
 
     def solve(self, y, t, psi, max_iter, corr_tol=0.0, read_back=True):
         return pwf_solve(self.handle, y, t, psi, max_iter, corr_tol, self.desc.batch if read_back else None)
+
+    def solve_host(self, y, t, psi, max_iter, corr_tol=0.0, psi_is_input=True, chunk=0):
+        return pwf_solve_host(self.handle, self.desc, y, t, psi, max_iter, corr_tol, psi_is_input, chunk)
 
     def solve_joint(self, y, t, psi, max_iter, eta_t, read_back=True):
         return pwf_solve_joint(self.handle, y, t, psi, max_iter, eta_t, self.desc.batch if read_back else None)

@@ -59,5 +59,6 @@ def test_null_arguments(lib):
     plan = ctypes.c_void_p()
     assert lib.pwf_plan_create(None, ctypes.byref(plan)) == 1
     assert lib.pwf_forward(None, None, None, None) == 1
+    assert lib.pwf_solve_host(None, None, None, None, 0, 1, 0.0, 0, None, None) == 1
     assert lib.pwf_plan_destroy(None) == 1
     assert lib.pwf_state_bytes(None) == 0
