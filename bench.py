@@ -41,6 +41,8 @@ UNIT = "Mpx*it/s"
 
 # Algorithmic DRAM bytes per pixel of each pass of the fused iteration (reads +
 # writes of the fields the pass must touch; complex64 = 8 B, float32 = 4 B).
+STATE_FLOOR_BYTES_PER_PX = 44  # psi r/w 16, phi r 8 + w 8, t 8, y 4
+
 PASS_BYTES_PER_PX = {
     "col_q": 16,            # field in, field out
     "row_mul_t": 24,        # field in, t in, field out
@@ -508,7 +510,12 @@ def main():
                  "eager_iteration_ms": iter_ms,
                  "model_bytes_per_px": sum(PASS_BYTES_PER_PX.get(n, 0) for n, _ in passes),
                  "model_gbs_timed": model_bytes / (ms / args.steps / 1e3) / 1e9,
-                 "model_frac_timed": model_bytes / (ms / args.steps / 1e3) / 1e9 / hbm}
+                 "model_frac_timed": model_bytes / (ms / args.steps / 1e3) / 1e9 / hbm,
+                 # what the method must touch once per iteration (psi r/w, phi r/w, t, y):
+                 # the bound if a whole field stayed on chip
+                 "state_floor_bytes_per_px": STATE_FLOOR_BYTES_PER_PX,
+                 "state_floor_frac_timed": STATE_FLOOR_BYTES_PER_PX * batch * w.ny * w.nx
+                 / (ms / args.steps / 1e3) / 1e9 / hbm}
 
     extras = {}
     if not args.no_extras and rank == 0:

@@ -1637,20 +1637,12 @@ static pwf_status host_pipe_ensure(pwf_plan* p, int chunk) {
   return PWF_OK;
 }
 
-pwf_status pwf_solve_host(pwf_plan* p, const float* y_host, const void* t_host, void* psi_host, int32_t psi_is_input,
-                          int32_t max_iter, double corr_tol, int32_t chunk, int32_t* iters_host, double* loss_host) {
-  pwf_status r = check_plan(p);
-  if (r) return r;
-  if (!y_host || !t_host || !psi_host || max_iter < 0 || chunk < 0) return PWF_ERR_INVALID_ARG;
-  const int B = p->d.batch;
-  if (chunk == 0) chunk = default_chunk(B);
-  if (chunk > B || B % chunk != 0) return fail(p, PWF_ERR_INVALID_ARG, "chunk must divide the batch");
-  if ((r = host_pipe_ensure(p, chunk))) return r;
-  HostPipe& hp = *p->pipe;
+// Enqueues the chunks of one pwf_solve_host call on the pipeline's streams.
+static pwf_status host_pipe_enqueue(pwf_plan* p, HostPipe& hp, const float* yh, const void* t_host, float2* ph,
+                                    int32_t psi_is_input, int32_t max_iter, double corr_tol) {
+  const int chunk = hp.chunk, nch = p->d.batch / chunk;
   const size_t npx = (size_t)p->d.ny * p->d.nx, per = (size_t)chunk * npx;
-  const float* yh = y_host;
-  float2* ph = static_cast<float2*>(psi_host);
-  const int nch = B / chunk;
+  pwf_status r;
   // after whatever the caller queued on the plan's stream
   PWF_CUDA(p, cudaEventRecord(hp.start, p->stream));
   PWF_CUDA(p, cudaStreamWaitEvent(hp.s_in, hp.start, 0));
@@ -1680,11 +1672,31 @@ pwf_status pwf_solve_host(pwf_plan* p, const float* y_host, const void* t_host, 
     PWF_CUDA(p, cudaMemcpyAsync(ph + k * per, hp.psi[s], per * sizeof(float2), cudaMemcpyDeviceToHost, hp.s_out));
     PWF_CUDA(p, cudaEventRecord(hp.out_done[s], hp.s_out));
   }
-  PWF_CUDA(p, cudaStreamSynchronize(hp.s_out));
-  PWF_CUDA(p, cudaStreamSynchronize(hp.s_run));
+  return PWF_OK;
+}
+
+pwf_status pwf_solve_host(pwf_plan* p, const float* y_host, const void* t_host, void* psi_host, int32_t psi_is_input,
+                          int32_t max_iter, double corr_tol, int32_t chunk, int32_t* iters_host, double* loss_host) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+  if (!y_host || !t_host || !psi_host || max_iter < 0 || chunk < 0) return PWF_ERR_INVALID_ARG;
+  const int B = p->d.batch;
+  if (chunk == 0) chunk = default_chunk(B);
+  if (chunk > B || B % chunk != 0) return fail(p, PWF_ERR_INVALID_ARG, "chunk must divide the batch");
+  if ((r = host_pipe_ensure(p, chunk))) return r;
+  HostPipe& hp = *p->pipe;
+  r = host_pipe_enqueue(p, hp, y_host, t_host, static_cast<float2*>(psi_host), psi_is_input, max_iter, corr_tol);
+  // wait for every stream even after an error: no copy may still be writing
+  // the caller's host buffers when the call returns
+  const cudaError_t e_out = cudaStreamSynchronize(hp.s_out);
+  const cudaError_t e_run = cudaStreamSynchronize(hp.s_run);
+  const cudaError_t e_in = cudaStreamSynchronize(hp.s_in);
+  if (r) return r;
+  for (cudaError_t e : {e_out, e_run, e_in})
+    if (e != cudaSuccess) return cuda_fail(p, e, "pwf_solve_host");
   if (iters_host) std::memcpy(iters_host, hp.h_iters, B * sizeof(int));
   if (loss_host) std::memcpy(loss_host, hp.h_loss, B * sizeof(double));
-  for (int k = 0; k < nch; k++)
+  for (int k = 0; k < B / chunk; k++)
     if (hp.h_it[k].nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss");
   return PWF_OK;
 }
