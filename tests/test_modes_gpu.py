@@ -37,7 +37,9 @@ def modal_plan(P, geom, batch, K):
 
 
 CASES = [("k9_128", 9, 2, 128, 128), ("k25_96x128", 25, 2, 96, 128), ("k9_256x1024", 9, 1, 256, 1024),
-         ("k9_1024x64", 9, 2, 1024, 64), ("k9_2048x32", 9, 1, 2048, 32)]
+         ("k9_1024x64", 9, 2, 1024, 64), ("k9_2048x32", 9, 1, 2048, 32),
+         # radix-3 column lengths (24 values per thread: the one-column mode kernels)
+         ("k9_768x96", 9, 1, 768, 96), ("k25_1536x32", 25, 1, 1536, 32)]
 
 
 @pytest.mark.parametrize("name,K,batch,ny,nx", CASES, ids=[c[0] for c in CASES])
