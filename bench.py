@@ -518,12 +518,40 @@ def main():
                  / (ms / args.steps / 1e3) / 1e9 / hbm}
 
     extras = {}
+    legs = set(args.legs.split(",")) if args.legs != "all" else None
+
+    def leg(name):
+        return legs is None or name in legs
+
+    if not args.no_extras and leg("e2e"):
+        # end to end through the host-buffer entry point, every rank on its own
+        # series: y and t from pinned host memory, psi (from 0) back to it;
+        # chunks of the series stream through the device with the copies
+        # overlapping the solve. Barrier before each call, max over ranks.
+        e2e_iters = 10
+        y_h = y.cpu().pin_memory()
+        t_h = t.cpu().pin_memory()
+        psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
+        times = []
+        for rep in range(3):  # the first call builds the chunk plans
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            plan.solve_host(y_h, t_h, psi_h, e2e_iters, psi_is_input=False)
+            dt = max_over_ranks(time.perf_counter() - t0, world)
+            if rep > 0:
+                times.append(dt * 1e3)
+        ems = sum(times) / len(times)
+        chunk = [c for c in range(-(-batch // 4), 0, -1) if batch % c == 0][0]
+        extras["e2e"] = {"value": world * mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(world * (y.numel() * 4 + t.numel() * 8)),
+                         "d2h_bytes_per_step": int(world * psi.numel() * 8),
+                         "step": f"one pwf_solve_host call of {e2e_iters} iterations per rank (pinned host "
+                                 f"buffers, chunks of {chunk} projections, copies overlapping the solve)",
+                         "ms_per_call": ems}
+        del y_h, t_h, psi_h
+
     if not args.no_extras and rank == 0:
-        legs = set(args.legs.split(",")) if args.legs != "all" else None
-
-        def leg(name):
-            return legs is None or name in legs
-
         if leg("plain"):
             # plain per-projection baseline (unfused, Algorithm S2 step by step) on a sample
             nplain, iplain = 4, 2
@@ -543,32 +571,6 @@ def main():
                                    "fused_over_plain": value / world / pv}
             plain.close()
             del yp, pp
-
-        if leg("e2e"):
-            # end to end through the host-buffer entry point: y and t from pinned
-            # host memory, psi (from 0) back to it; chunks of the series stream
-            # through the device with the copies overlapping the solve
-            e2e_iters = 10
-            y_h = y.cpu().pin_memory()
-            t_h = t.cpu().pin_memory()
-            psi_h = torch.empty(psi.shape, dtype=psi.dtype).pin_memory()
-            times = []
-            for rep in range(3):  # the first call builds the chunk plans
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                plan.solve_host(y_h, t_h, psi_h, e2e_iters, psi_is_input=False)
-                dt = time.perf_counter() - t0
-                if rep > 0:
-                    times.append(dt * 1e3)
-            ems = sum(times) / len(times)
-            chunk = [c for c in range(-(-batch // 4), 0, -1) if batch % c == 0][0]
-            extras["e2e"] = {"value": mpx_iter * e2e_iters / (ems / 1e3), "unit": UNIT,
-                             "h2d_bytes_per_step": int(y.numel() * 4 + t.numel() * 8),
-                             "d2h_bytes_per_step": int(psi.numel() * 8),
-                             "step": f"one pwf_solve_host call of {e2e_iters} iterations (pinned host buffers, "
-                                     f"chunks of {chunk} projections, copies overlapping the solve)",
-                             "ms_per_call": ems}
-            del y_h, t_h, psi_h
 
         # the same series with partial coherence as 9 tilted source modes
         if leg("modal") and w.name == "tomo180x1024_iotf":
