@@ -323,6 +323,18 @@ def test_single_mode_is_the_coherent_model():
     assert np.max(np.abs(f1 - O.PhysicalModel(psi, t, g)[0])) < 1e-13
 
 
+@pytest.mark.parametrize("mx,my", [(3, -2), (-5, 7), (0, 31), (47, 0)])
+def test_a_mode_shifts_the_2d_spectrum_by_its_bins(mx, my):
+    # DFT shift theorem: F{x s}(kx, ky) = F{x}(kx - mx, ky - my), indices mod (nx, ny);
+    # the product with a tilted mode is an index shift of the exit wave's spectrum
+    rng = np.random.default_rng(abs(mx) * 100 + abs(my))
+    g = geom(32, 48)
+    x = crandn(rng, (32, 48))
+    lhs = np.fft.fft2(x * O.mode_wave(g, mx, my))
+    rhs = np.roll(np.fft.fft2(x), (my, mx), axis=(0, 1))
+    assert np.max(np.abs(lhs - rhs)) < 1e-10 * np.max(np.abs(rhs))
+
+
 def test_tilted_modes_shift_the_field_by_lambda_L2_q():
     """With L1 = 0, a mode tilted by m bins propagates to
     v_m(r) = s_m(r) exp(-i pi lambda L2 |q|^2) v_0(r - lambda L2 q), q = m/(N p)
