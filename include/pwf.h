@@ -11,9 +11,12 @@
  * Conventions shared by every entry point
  *  - Arrays are caller-owned DEVICE memory unless a parameter says "host".
  *    Complex arrays are interleaved complex64 (float re, float im), row-major
- *    [batch][ny][nx], 8-byte aligned at least (16-byte recommended). Real
- *    arrays are float32 [batch][ny][nx]. The diffuser t is one complex64
- *    [ny][nx] field shared by every projection of the batch.
+ *    [batch][ny][nx]. Real arrays are float32 [batch][ny][nx]. The diffuser t
+ *    is one complex64 [ny][nx] field shared by every projection of the batch.
+ *    Device arrays passed to plan calls must be 16-byte aligned (rows are read
+ *    with 16-byte loads and L2 bulk prefetches); a misaligned one returns
+ *    PWF_ERR_INVALID_ARG before any work is queued. Fresh cudaMalloc and
+ *    PyTorch allocations are 256-byte aligned. pwf_fbp's own rules are below.
  *  - ny and nx are each one of 16, 32, 64, 96, 128, 256, 512, 768, 1024, 1536,
  *    2048 (other sizes return PWF_ERR_UNSUPPORTED).
  *  - Work is enqueued on the plan's stream (pwf_plan_desc.stream, a

@@ -586,6 +586,11 @@ cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
     if (e__ != cudaSuccess) return cuda_fail((p), e__, #expr); \
   } while (0)
 
+// Device arrays are read with 16-byte vector loads and 16-byte L2 bulk
+// prefetches of whole rows, which need 16-byte aligned bases.
+bool a16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+pwf_status misaligned(pwf_plan* p) { return fail(p, PWF_ERR_INVALID_ARG, "device arrays must be 16-byte aligned"); }
+
 pwf_status compute_maxt2(pwf_plan* p, const float2* t) {
   const size_t n = (size_t)p->d.ny * p->d.nx;
   PWF_CUDA(p, cudaMemsetAsync(p->maxt2, 0, sizeof(float), p->stream));
@@ -1180,6 +1185,7 @@ pwf_status pwf_forward(pwf_plan* p, const void* psi, const void* t, float* f) {
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!psi || !t || !f) return PWF_ERR_INVALID_ARG;
+  if (!a16(psi) || !a16(t) || !a16(f)) return misaligned(p);
   PassArgs a = base_args(p);
   if (!p->modes.empty()) {
     a.psi = (const float2*)psi;
@@ -1206,6 +1212,7 @@ pwf_status pwf_gradient(pwf_plan* p, const void* psi, const void* t, const float
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!psi || !t || !y || !g) return PWF_ERR_INVALID_ARG;
+  if (!a16(psi) || !a16(t) || !a16(y) || !a16(g)) return misaligned(p);
   const float2* P = (const float2*)psi;
   if ((r = compute_maxt2(p, (const float2*)t))) return r;
   PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)p->d.batch * NACC * sizeof(double), p->stream));
@@ -1260,6 +1267,7 @@ pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const fl
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!psi || !t || !grad_f) return PWF_ERR_INVALID_ARG;
+  if (!a16(psi) || !a16(t) || !a16(grad_f) || !a16(grad_psi) || !a16(grad_t)) return misaligned(p);
   if (!grad_psi && !grad_t) return PWF_OK;
   const float2* P = (const float2*)psi;
   PassArgs a = base_args(p);
@@ -1409,6 +1417,7 @@ pwf_status pwf_step(pwf_plan* p, pwf_state* st, const float* y, const void* t, v
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!st || !y || !t || !psi) return PWF_ERR_INVALID_ARG;
+  if (!a16(y) || !a16(t) || !a16(psi)) return misaligned(p);
   if (st->B != p->d.batch || st->ny != p->d.ny || st->nx != p->d.nx) return PWF_ERR_STATE;
   float2* P = (float2*)psi;
   if (!p->modes.empty() && (r = ensure_vstack(p))) return r;
@@ -1474,6 +1483,7 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!y || !t || !psi || max_iter < 0) return PWF_ERR_INVALID_ARG;
+  if (!a16(y) || !a16(t) || !a16(psi)) return misaligned(p);
   const bool joint = eta_t >= 0.0;
   if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
   if (!p->modes.empty() && (r = ensure_vstack(p))) return r;  // before the graph capture
@@ -1748,6 +1758,7 @@ pwf_status pwf_profile_iteration(pwf_plan* p, const float* y, const void* t, voi
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!y || !t || !psi || iters < 1 || !pass_ms || !pass_names || !n_passes) return PWF_ERR_INVALID_ARG;
+  if (!a16(y) || !a16(t) || !a16(psi)) return misaligned(p);
   if (p->d.flags & PWF_FLAG_PLAIN) return PWF_ERR_UNSUPPORTED;
   if (!p->solve_state && (r = pwf_state_create(p, &p->solve_state))) return r;
   if (!p->modes.empty() && (r = ensure_vstack(p))) return r;
@@ -1857,6 +1868,7 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
     pwf_plan* p = g->plans[i];
     if ((r = check_plan(p))) return r;
     if (!y[i] || !t[i] || !psi[i]) return PWF_ERR_INVALID_ARG;
+    if (!a16(y[i]) || !a16(t[i]) || !a16(psi[i])) return misaligned(p);
   }
   if (max_iter == 0) return PWF_OK;
   // set-up of every class on the caller's stream (Algorithm S1 initialisation)
@@ -1973,6 +1985,7 @@ pwf_status pwf_calibrate_coherence(pwf_plan* p, const float* I_ref, int32_t max_
   const int ny = p->d.ny, nx = p->d.nx;
   if (!I_ref || !xcoh_m || !ycoh_m || max_lag < 1 || max_lag >= nx / 2 || max_lag >= ny / 2)
     return PWF_ERR_INVALID_ARG;
+  if (!a16(I_ref)) return misaligned(p);
   const size_t n = (size_t)ny * nx;
   if (!p->calib && (r = dalloc(p, &p->calib, (size_t)nx + ny + 1))) return r;  // released with the plan
   double* d = p->calib;
@@ -2027,6 +2040,7 @@ pwf_status pwf_diffuser_from_reference(pwf_plan* p, const float* I_ref, double w
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!I_ref || !t_out || !(wiener_eps >= 0)) return PWF_ERR_INVALID_ARG;
+  if (!a16(I_ref) || !a16(t_out)) return misaligned(p);
   const size_t n = (size_t)p->d.ny * p->d.nx;
   const int G = grid_for(n);
   k_real_to_complex<<<G, 256, 0, p->stream>>>(I_ref, p->X, n);

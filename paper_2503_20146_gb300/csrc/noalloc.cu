@@ -146,6 +146,9 @@ pwf_status setup_device(DevPtrs** out) {
 
 extern "C" pwf_status pwf_forward_noalloc(const pwf_plan_desc* desc, const void* psi, const void* t, float* f) {
   if (!desc || !psi || !t || !f) return PWF_ERR_INVALID_ARG;
+  // rows are read with 16-byte vector loads and L2 bulk prefetches
+  for (const void* q : {psi, t, static_cast<const void*>(f)})
+    if (reinterpret_cast<uintptr_t>(q) & 15) return PWF_ERR_INVALID_ARG;
   const pwf_plan_desc& d = *desc;
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0)

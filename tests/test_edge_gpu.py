@@ -97,3 +97,24 @@ def test_large_phase_and_strong_attenuation_match_oracle(pwf):
         P64 = psi[b].astype(np.complex128)
         assert rel_l2(f[b], O.PhysicalModel(P64, T64, g)[0]) <= 1e-5
         assert rel_l2(gr[b], O.gradient(P64, T64, y[b].astype(np.float64), g)[0]) <= 1e-4
+
+
+def test_misaligned_device_arrays_are_rejected_before_any_work(pwf):
+    g = geometry(W2, 64, 64)
+    _, t = blob_batch(W2, 1, 64, 64)
+    n = 64 * 64
+    with plan_for(pwf, g, 1) as plan:
+        td = dev(to_c64(t))
+        psi_bad = torch.zeros(n + 1, dtype=torch.complex64, device="cuda")[1:].view(1, 64, 64)  # 8 B off
+        y = torch.ones((1, 64, 64), dtype=torch.float32, device="cuda")
+        with pytest.raises(pwf.PWFError):
+            plan.forward(psi_bad, td)
+        with pytest.raises(pwf.PWFError):
+            plan.solve(y, td, psi_bad, 2)
+        y_bad = torch.ones(n + 1, dtype=torch.float32, device="cuda")[1:].view(1, 64, 64)  # 4 B off
+        psi = torch.zeros((1, 64, 64), dtype=torch.complex64, device="cuda")
+        with pytest.raises(pwf.PWFError):
+            plan.gradient(psi, td, y_bad)
+        # nothing was queued: the plan still solves
+        it, _ = plan.solve(y, td, psi, 2)
+        assert list(it) == [2]
