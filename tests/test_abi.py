@@ -62,3 +62,22 @@ def test_null_arguments(lib):
     assert lib.pwf_solve_host(None, None, None, None, 0, 1, 0.0, 0, None, None) == 1
     assert lib.pwf_plan_destroy(None) == 1
     assert lib.pwf_state_bytes(None) == 0
+
+
+def test_host_buffer_marshalling_checks_dtype_size_and_layout():
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    a = np.zeros((2, 4, 4), np.complex64)
+    assert pwf._host_ptr(a, "complex64", 32).value == a.ctypes.data
+    t = torch.zeros((2, 4, 4), dtype=torch.float32)
+    assert pwf._host_ptr(t, "float32", 32).value == t.data_ptr()
+    with pytest.raises(ValueError):
+        pwf._host_ptr(a, "float32", 32)                       # dtype
+    with pytest.raises(ValueError):
+        pwf._host_ptr(a, "complex64", 31)                     # size
+    with pytest.raises(ValueError):
+        pwf._host_ptr(a[:, :, ::2], "complex64", 16)          # not contiguous
+    with pytest.raises(ValueError):
+        pwf._host_ptr(t.transpose(1, 2), "float32", 32)
+    with pytest.raises(TypeError):
+        pwf._host_ptr([0.0] * 4, "float32", 4)
