@@ -1,0 +1,30 @@
+"""The byte model bench.py reports (host logic, CPU): the per-pass table adds
+up to the iteration totals the roofline fractions are quoted on."""
+import bench
+
+
+def iotf_passes():
+    return (["col_q", "row_mul_t", "col_q", "row_intensity", "col_resid_iotf2", "row_mul_v", "col_q",
+             "row_mul_t", "col_q", "row_grad_pack", "col_precond_reg", "row_nesterov_fft"])
+
+
+def modal_passes(k):
+    fwd = ["col_mode_fwd", "row_mul_t", "col_q", "row_mode_int"]
+    back = ["row_mode_vg", "col_q", "row_mul_t", "col_mode_back"]
+    return (["col_fft"] + fwd * k + ["modal_resid"] + back * k + ["col_ifft", "row_grad_pack", "col_precond_reg",
+                                                                     "row_nesterov_fft"])
+
+
+def test_iotf_iteration_is_296_bytes_per_pixel():
+    assert sum(bench.PASS_BYTES_PER_PX[p] for p in iotf_passes()) == 296
+
+
+def test_modal_iteration_matches_the_closed_form():
+    for k in (1, 9, 25):
+        assert sum(bench.PASS_BYTES_PER_PX[p] for p in modal_passes(k)) == bench.modal_bytes_per_px(k)
+    assert bench.modal_bytes_per_px(9) == 1632 and bench.modal_bytes_per_px(25) == 4256
+
+
+def test_state_floor_is_what_an_iteration_must_touch():
+    # psi read and written, phi read and written, t and y read
+    assert bench.STATE_FLOOR_BYTES_PER_PX == 8 + 8 + 8 + 8 + 8 + 4
