@@ -23,7 +23,7 @@ Computerized Tomographic Imaging", ch. 3):
     the detector; the reconstruction grid has the detector's pixel pitch and
     centring, x along the detector row and z along the beam at theta = 0.
 
-Readings (listed in DESIGN.md as R15):
+Readings (R15 in the design notes' numbering):
   * angles cover [0, pi) uniformly (the tomographic workload's 0..179 degrees);
   * psi = -k int beta - i k int delta, so FBP of psi scaled by
     -lambda / (2 pi p) gives beta + i delta (both parts at once, because the

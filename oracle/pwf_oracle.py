@@ -17,7 +17,7 @@ What it computes, in the paper's order and notation:
 Every array is complex128 / float64; numpy's FFT is the one library primitive
 (Filter of Algorithm S2 is F^-1{F{x} W}, circular, no padding).
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous (R1 onwards, the numbering the design notes use):
   R1  FreePropagation: Q = exp(i 2 pi w L) carries the constant piston
       exp(i 2 pi L / lambda). It is a global phase that cancels in |v|^2 and in
       the back-propagation, so it is dropped, and w - 1/lambda is evaluated in
