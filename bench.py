@@ -241,6 +241,44 @@ def measured_traffic(kernel):
     return None if k is None else k.get("dram_bytes_per_launch_full")
 
 
+SCHEDULERS_PER_SM = 4  # warp schedulers (SM sub-partitions) per SM, one instruction each per cycle
+
+
+def issue_roofline(inst_per_px, px, launch_ms, sms, sm_mhz):
+    """Warp-instruction issue rate of one launch against the SMs' peak issue
+    rate (every scheduler issuing every cycle at sm_mhz)."""
+    achieved = inst_per_px * px / 32.0 / (launch_ms / 1e3) / 1e9
+    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "thread_instructions_per_px": inst_per_px, "sm_mhz": sm_mhz}
+
+
+def measured_instructions_per_px(kernel):
+    """Thread instructions per pixel of `kernel` from the committed ncu summary
+    (smsp__inst_executed.sum x 32 / captured pixels), or None when the summary
+    was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel) or {}
+    if "warp_instructions" not in k or "captured_px" not in k:
+        return None
+    return k["warp_instructions"] * 32.0 / k["captured_px"]
+
+
+def max_sm_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -508,6 +546,16 @@ def main():
                 "frac": achieved / hbm, "traffic": measured_traffic(dom), "peak_kind": peak_kind,
                 "bytes_per_px": PASS_BYTES_PER_PX.get(dom, 0), "launch_ms": dom_avg,
                 "share_of_iteration": sum(dom_ms) / iter_ms}
+    # the same launch against the instruction issue rate (the column passes are
+    # issue-bound): instruction count from the ncu capture, clock sampled above
+    try:
+        ipx = measured_instructions_per_px(dom)
+        clk_mhz = clk.summary().get("sm_mhz") or max_sm_mhz()
+        if ipx is not None and clk_mhz:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            roofline["issue"] = issue_roofline(ipx, batch * w.ny * w.nx, dom_avg, sms, clk_mhz)
+    except Exception as exc:  # an auxiliary figure never costs the bench line
+        roofline["issue"] = {"unavailable": repr(exc)}
     model_bytes = sum(PASS_BYTES_PER_PX.get(n, 0) for n, _ in passes) * batch * w.ny * w.nx
     iteration = {"passes": [[n, round(p, 4)] for n, p in passes],
                  "eager_iteration_ms": iter_ms,

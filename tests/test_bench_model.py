@@ -28,3 +28,20 @@ def test_modal_iteration_matches_the_closed_form():
 def test_state_floor_is_what_an_iteration_must_touch():
     # psi read and written, phi read and written, t and y read
     assert bench.STATE_FLOOR_BYTES_PER_PX == 8 + 8 + 8 + 8 + 8 + 4
+
+
+def test_issue_roofline_arithmetic():
+    # 32 thread instructions per pixel over 1 Gpx in 1 s: 1 G warp-instructions/s;
+    # 100 SMs x 4 schedulers at 1000 MHz issue 400 G warp-instructions/s
+    r = bench.issue_roofline(32.0, 1e9, 1000.0, 100, 1000.0)
+    assert abs(r["achieved"] - 1.0) < 1e-12 and abs(r["peak"] - 400.0) < 1e-9
+    assert abs(r["frac"] - 1.0 / 400.0) < 1e-15
+
+
+def test_instruction_count_only_for_the_captured_sources(monkeypatch):
+    ipx = bench.measured_instructions_per_px("col_q")
+    if ipx is not None:  # the committed capture matches the current kernel sources
+        assert 50 < ipx < 200
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    assert bench.measured_instructions_per_px("col_q") is None
+    assert bench.measured_traffic("col_q") is None
