@@ -16,13 +16,21 @@ import torch
 from . import pwf as _pwf
 
 
+def _aligned(x: torch.Tensor) -> torch.Tensor:
+    """x as a contiguous tensor whose data starts on a 16-byte boundary (the
+    library's rule for device arrays): a fresh copy when a view starts in
+    between. Inputs only: the copy is never written back."""
+    x = x.contiguous()
+    return x if x.data_ptr() % 16 == 0 else x.clone()
+
+
 class PWFForward(torch.autograd.Function):
     @staticmethod
     def forward(ctx, psi: torch.Tensor, t: torch.Tensor, plan: "_pwf.Plan"):
         if psi.dtype != torch.complex64 or t.dtype != torch.complex64:
             raise TypeError("psi and t must be complex64")
-        psi = psi.contiguous()
-        t = t.contiguous()
+        psi = _aligned(psi)
+        t = _aligned(t)
         f = plan.forward(psi, t)
         ctx.save_for_backward(psi, t)
         ctx.plan = plan
@@ -32,7 +40,7 @@ class PWFForward(torch.autograd.Function):
     def backward(ctx, grad_f: torch.Tensor):
         psi, t = ctx.saved_tensors
         want_psi, want_t = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        gp, gt = ctx.plan.vjp(psi, t, grad_f.to(torch.float32).contiguous(), want_psi=want_psi, want_t=want_t)
+        gp, gt = ctx.plan.vjp(psi, t, _aligned(grad_f.to(torch.float32)), want_psi=want_psi, want_t=want_t)
         return gp, gt, None
 
 

@@ -81,3 +81,17 @@ def test_host_buffer_marshalling_checks_dtype_size_and_layout():
         pwf._host_ptr(t.transpose(1, 2), "float32", 32)
     with pytest.raises(TypeError):
         pwf._host_ptr([0.0] * 4, "float32", 4)
+
+
+def test_autograd_inputs_are_realigned_by_copy():
+    torch = pytest.importorskip("torch")
+    from paper_2503_20146_gb300.autograd import _aligned
+    base = torch.arange(18, dtype=torch.float32).view(torch.complex64)
+    view = base[1:]                                  # starts 8 bytes into the allocation
+    assert view.data_ptr() % 16 == 8
+    fixed = _aligned(view)
+    assert fixed.data_ptr() % 16 == 0 and torch.equal(fixed, view)
+    whole = base[:8]
+    assert _aligned(whole).data_ptr() == whole.data_ptr()   # aligned input: no copy
+    nc = torch.arange(16, dtype=torch.float32).view(4, 4).t()
+    assert _aligned(nc).is_contiguous()
