@@ -13,7 +13,9 @@ Arms:
                      unfused per-projection baseline (PWF_FLAG_PLAIN) on a
                      sample, the roofline of the dominant kernel, the FP64
                      oracle on the host cores (cpu_baseline) and an
-                     end-to-end number through host buffers.
+                     end-to-end number through host buffers (pwf_solve_host:
+                     pinned y and t in, psi out, copies overlapping the
+                     solve; every rank, max over ranks).
   --impl reference   the FP64 oracle on the host cores, timed per step on a
                      bounded sample of the same workload.
 
