@@ -81,6 +81,12 @@ def mode_wave_conj(geom, mx, my):
     return np.conj(_mwave(geom, mx, my))
 
 
+def mode_wave_axes_swapped(geom, mx, my):
+    y = np.arange(geom.ny)[:, None]
+    x = np.arange(geom.nx)[None, :]
+    return np.exp(2j * np.pi * (my * x / geom.nx + mx * y / geom.ny))
+
+
 def diffuser_gradient_without_conj_u1(psi, t, y, geom):
     f, x, v = O.PhysicalModel(psi, t, geom)
     G = O.Filter(-(y - f), O.iotf(geom)).real
@@ -102,6 +108,8 @@ MUTATIONS = [
     ("Regularizer", regularizer_swapped, ["test_regularizer_special_cases"]),
     ("nesterov_mu", mu_without_sqrt, ["test_nesterov_sequence_and_first_step"]),
     ("mode_wave", mode_wave_conj, ["test_tilted_modes_shift_the_field_by_lambda_L2_q"]),
+    ("mode_wave", mode_wave_conj, ["test_a_mode_shifts_the_2d_spectrum_by_its_bins"]),
+    ("mode_wave", mode_wave_axes_swapped, ["test_a_mode_shifts_the_2d_spectrum_by_its_bins"]),
     ("diffuser_gradient", diffuser_gradient_without_conj_u1, ["test_diffuser_gradient_matches_central_differences"]),
 ]
 
@@ -110,6 +118,8 @@ def _run_pin(name):
     fn = getattr(pins, name)
     if name in ("test_filter_matches_bruteforce_dft",):
         fn(12, 16)
+    elif name == "test_a_mode_shifts_the_2d_spectrum_by_its_bins":
+        fn(3, -2)
     elif name in ("test_gradient_matches_central_differences", "test_diffuser_gradient_matches_central_differences"):
         fn(False)
     else:
