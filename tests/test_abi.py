@@ -95,3 +95,10 @@ def test_autograd_inputs_are_realigned_by_copy():
     assert _aligned(whole).data_ptr() == whole.data_ptr()   # aligned input: no copy
     nc = torch.arange(16, dtype=torch.float32).view(4, 4).t()
     assert _aligned(nc).is_contiguous()
+
+
+def test_every_declared_function_has_a_binding_signature(lib):
+    # the binding sets argtypes/restype for exactly the functions the header declares
+    names = set(pwf.header_functions())
+    typed = {n for n in names if getattr(lib, n).argtypes is not None}
+    assert typed == names, sorted(names - typed)
