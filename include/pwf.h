@@ -235,11 +235,11 @@ pwf_status pwf_diffuser_from_reference(pwf_plan* plan, const float* I_ref, doubl
  * standard parallel-beam FBP with the Ram-Lak filter, one slice per detector
  * row, then the factor -lambda / (2 pi p), which turns the retrieved
  * psi = -k int beta - i k int delta into beta + i delta.
- *   psi      complex64 [n_angles][ny][nx], device; detector pixel j sits at
- *            s = j - nx/2 + 1/2 pixels from the rotation axis
+ *   psi      complex64 [n_angles][ny][nx], device, 8-byte aligned; detector
+ *            pixel j sits at s = j - nx/2 + 1/2 pixels from the rotation axis
  *   angles_rad_host  n_angles projection angles (host), normally [0, pi)
- *   vol_out  complex64 [ny][nx][nx], device: slice y, row z (beam direction at
- *            angle 0), column x; Re = beta, Im = delta
+ *   vol_out  complex64 [ny][nx][nx], device, 8-byte aligned: slice y, row z
+ *            (beam direction at angle 0), column x; Re = beta, Im = delta
  *   workspace  device memory of pwf_fbp_workspace_bytes(...) bytes, 256-byte
  *            aligned (filtered rows zero-padded to 2 nx as 16-byte
  *            interpolation records, filter and angle tables; about
@@ -251,7 +251,8 @@ pwf_status pwf_diffuser_from_reference(pwf_plan* plan, const float* I_ref, doubl
  * linear interpolation, zero outside the detector. Sizes: 1 <= n_angles <=
  * PWF_FBP_MAX_ANGLES, ny <= 65535, 2 nx one of 32, 64, 96, 128, 192, 256, 384,
  * 512, 768, 1024, 1536, 2048; otherwise PWF_ERR_INVALID_ARG (workspace_bytes
- * returns 0).
+ * returns 0). A short or misaligned workspace, or misaligned psi / vol_out,
+ * also returns PWF_ERR_INVALID_ARG before anything is queued.
  * The tables are copied from the host synchronously on the stream; the two
  * kernels are then enqueued asynchronously. */
 #define PWF_FBP_MAX_ANGLES 4096
