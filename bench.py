@@ -311,7 +311,7 @@ def oracle_sample(w, n_proj, seed_iters):
           for b in range(n_proj)]
     t0 = time.perf_counter()
     for y in ys:
-        O.pwf(y, t, geom, seed_iters)
+        O.solve(y, t, geom, seed_iters)
     dt = time.perf_counter() - t0
     return dt, n_proj * w.ny * w.nx * seed_iters / 1e6
 

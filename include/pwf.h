@@ -3,10 +3,12 @@
  *
  * Method: K. Lee, H. Hugonnet, J.-H. Lim, Y. Park, "Speckle-based X-ray
  * microtomography via preconditioned Wirtinger flow", arXiv 2503.20146.
- * Algorithm S1 (PWF) and Algorithm S2 (PhysicalModel, WirtingerDerivative,
- * Preconditioner, Regularizer, FreePropagation, Filter); forward model Eq. (1);
- * loss Eq. (2); IOTF Eq. (5); preconditioning filter Eq. (11); sample transfer
- * function and regularization window Eqs. (14)-(15).
+ * Algorithms S1 (the PWF iteration) and S2 (its forward model, Wirtinger
+ * derivative, preconditioner, regularizer and angular-spectrum propagation);
+ * forward model Eq. (1); loss Eq. (2); IOTF Eq. (5); preconditioning filter
+ * Eq. (11); sample transfer function and regularization window Eqs. (14)-(15).
+ * Notation: F, F^-1 the 2-D DFT pair; P(L){x} = F^-1{Q F{x}} propagation over
+ * L; P1, P2 over L1, L2; P^H the adjoint (propagation over -L).
  *
  * Conventions shared by every entry point
  *  - Arrays are caller-owned DEVICE memory unless a parameter says "host".
@@ -54,7 +56,7 @@ typedef struct pwf_state pwf_state;
 
 /* plan flags (ablations of Figs. S3-S5 and the unfused baseline) */
 #define PWF_FLAG_NO_PRECOND 0x1u /* P^-1 := 1 (Preconditioner off, Fig. S3)        */
-#define PWF_FLAG_NO_REG 0x2u     /* alpha := 0 (Regularizer off)                   */
+#define PWF_FLAG_NO_REG 0x2u     /* alpha := 0 (regularizer off)                   */
 #define PWF_FLAG_PLAIN 0x4u      /* unfused per-operation kernels, one projection at
                                     a time: Algorithm S2 executed step by step     */
 #define PWF_FLAG_NO_TUNE 0x8u    /* skip the plan-time column-pass autotuning      */
@@ -97,7 +99,7 @@ typedef struct {
  * its own zeroed workspace, on desc->stream, and keeps the fastest per pass
  * (a few launches per shape; the call synchronises that stream).
  * Builds the 1-D frequency tables of Q_k = exp(i 2 pi (w - 1/lambda) L)
- * (FreePropagation of Algorithm S2, constant piston dropped), IOTF (Eq. (5)),
+ * (angular-spectrum propagation, Algorithm S2, constant piston dropped), IOTF (Eq. (5)),
  * P^-1 = 1/(u^2 + v^2) in cycles per pixel with P^-1(0) = 0 (Eq. (11)) and
  * Gamma^2 = 1 - STF (Eqs. (14)-(15)). The propagator phase is applied as the sum
  * of its two axis restrictions; the plan checks, in double precision, that the
@@ -112,22 +114,24 @@ pwf_status pwf_plan_set_stream(pwf_plan* plan, void* stream);
 /* Bytes of device workspace the plan holds. */
 size_t pwf_plan_workspace_bytes(const pwf_plan* plan);
 
-/* f = PhysicalModel(psi, t) of Algorithm S2 / Eq. (1):
- *   x = exp(psi); v = P2{ t P1{x} }; f = Re Filter(|v|^2, IOTF).
+/* The forward model f(psi) of Eq. (1) (Algorithm S2):
+ *   x = exp(psi); v = P2{ t P1{x} }; f = Re F^-1{ IOTF F{|v|^2} }.
  * psi: complex64 [B][ny][nx]; t: complex64 [ny][nx]; f: float32 [B][ny][nx]. */
 pwf_status pwf_forward(pwf_plan* plan, const void* psi, const void* t, float* f);
 
-/* g = WirtingerDerivative(y - f(psi), x, v, t) of Algorithm S2 (the raw,
- * unpreconditioned gradient, divided by max |t|^2) and the loss of Eq. (2).
+/* The Wirtinger derivative g of Algorithm S2 at psi (the raw, unpreconditioned
+ * gradient with the factor 2 dropped, divided by max |t|^2):
+ *   g = conj(x) P1^H{ conj(t) P2^H{ v F^-1{IOTF F{f - y}} } } / max|t|^2,
+ * and the loss of Eq. (2).
  * g: complex64 [B][ny][nx]; loss: device float64 [B] (may be NULL).
  * The gradient of the loss w.r.t. Re psi and Im psi is 4 max|t|^2 (Re g, Im g). */
 pwf_status pwf_gradient(pwf_plan* plan, const void* psi, const void* t, const float* y,
                         void* g, double* loss);
 
-/* Vector-Jacobian product of f = PhysicalModel(psi, t) for a real cotangent
+/* Vector-Jacobian product of the forward model f(psi, t) for a real cotangent
  * grad_f = dL/df (float32 [B][ny][nx]), in the convention dL/dRe + i dL/dIm:
- *   grad_psi = 2 conj(x) P1^H{ conj(t) P2^H{ v Filter(grad_f, IOTF) } }
- *   grad_t   = sum over the batch of 2 conj(P1{x}) P2^H{ v Filter(grad_f, IOTF) }
+ *   grad_psi = 2 conj(x) P1^H{ conj(t) P2^H{ v F^-1{IOTF F{grad_f}} } }
+ *   grad_t   = sum over the batch of 2 conj(P1{x}) P2^H{ v F^-1{IOTF F{grad_f}} }
  * (the second is the diffuser gradient of the simultaneous retrieval of
  * Methods / Fig. S12). grad_psi: complex64 [B][ny][nx] (may be NULL);
  * grad_t: complex64 [ny][nx] (may be NULL). Intermediate fields are recomputed
@@ -189,7 +193,7 @@ pwf_status pwf_solve_host(pwf_plan* plan, const float* y_host, const void* t_hos
  * function", and Fig. S12: t is updated across all projections). Runs
  * max_iter iterations of Algorithm S1 over the batch (no stopping rule) and,
  * after each, t <- t - eta_t sum_b g_t,b with g_t = conj(P1{x})
- * P2^H{v Filter(-e, IOTF)} / max|t|^2 evaluated at the same point as the
+ * P2^H{v F^-1{IOTF F{f - y}}} / max|t|^2 evaluated at the same point as the
  * sample gradient (a plain gradient step; max|t|^2 is recomputed from the new
  * t). t (complex64 [ny][nx], device) is updated in place, as is psi.
  * eta_t = 0 reproduces pwf_solve with corr_tol = 0. Keeps B extra fields of
@@ -223,8 +227,8 @@ pwf_status pwf_group_read(pwf_group* group, int32_t index, double* loss_host, in
  * model g2 = 1 + A exp(-pi D^2 / coh^2) fitted by least squares on
  * ln(g2 - 1) over lags 1..max_lag; HOST outputs x_coh, y_coh in metres.
  * Synchronises. PWF_ERR_NONFINITE if g2 - 1 is not positive and decreasing
- * over the lags. pwf_diffuser_from_reference: I_coh = Re Filter(I_ref,
- * IOTF/(IOTF^2 + wiener_eps)) with the plan's IOTF, then
+ * over the lags. pwf_diffuser_from_reference: I_coh = Re F^-1{W F{I_ref}},
+ * W = IOTF/(IOTF^2 + wiener_eps) with the plan's IOTF, then
  * t = P(-L2){sqrt(max(I_coh, 0))} (phase zero at the detector); t_out is
  * complex64 [ny][nx] device memory. */
 pwf_status pwf_calibrate_coherence(pwf_plan* plan, const float* I_ref, int32_t max_lag, double* xcoh_m_host,
@@ -302,13 +306,17 @@ pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, 
  * allocator or reserved up front (a framework's caching pool, a fixed budget of
  * an acquisition pipeline), and code that cannot take the device-wide
  * synchronisation cudaMalloc/cudaFree imply. This call computes the same f as
- * pwf_forward (x = exp(psi); v = P2{t P1{x}}; f = Re Filter(|v|^2, IOTF)) with
+ * pwf_forward (x = exp(psi); v = P2{t P1{x}}; f = Re F^-1{IOTF F{|v|^2}}) with
  * the same kernels, but keeps its scratch field and 1-D tables in fixed
  * file-scope device arrays of the library (about 16.2 MiB on every GPU where
  * the library's code is loaded, held until the process exits). It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *   desc: as for pwf_plan_create (eta, gamma, alpha and flags are not used);
- *         the work is enqueued on desc->stream.
+ *         the work is enqueued on desc->stream. Only the paper's forms are
+ *         served: n_modes 0 or 1 (IOTF, or coherent when x_coh = y_coh = 0).
+ *         A source-mode descriptor (n_modes 9 or 25) returns
+ *         PWF_ERR_UNSUPPORTED, any other n_modes PWF_ERR_INVALID_ARG, both
+ *         before any work.
  *   psi, t, f: as for pwf_forward (caller-owned device memory).
  * Limit: batch * ny * nx <= 2097152 (2^21) complex elements; larger problems
  * return PWF_ERR_UNSUPPORTED before any work. Other errors as pwf_forward.

@@ -1,6 +1,6 @@
 """torch.autograd.Function over the PWF forward model (Eq. (1)).
 
-forward:  f = PhysicalModel(psi, t)                      -> pwf_forward
+forward:  f = f(psi, t) of Eq. (1)                      -> pwf_forward
 backward: (dL/dpsi, dL/dt) for a real cotangent dL/df    -> pwf_forward_vjp
 
 Only psi and t are saved for the backward pass; the propagated fields (P1{x},
@@ -45,5 +45,5 @@ class PWFForward(torch.autograd.Function):
 
 
 def physical_model(psi: torch.Tensor, t: torch.Tensor, plan: "_pwf.Plan") -> torch.Tensor:
-    """Differentiable f = PhysicalModel(psi, t) on the CUDA path."""
+    """Differentiable forward model f(psi, t) of Eq. (1) on the CUDA path."""
     return PWFForward.apply(psi, t, plan)

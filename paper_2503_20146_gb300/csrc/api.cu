@@ -47,7 +47,7 @@ const LengthKernels* kernels_for_length(int n) {
 // ---------------------------------------------------------------------------
 // small kernels
 // ---------------------------------------------------------------------------
-// max over the diffuser of |t|^2 (Algorithm S2, WirtingerDerivative). Values
+// max over the diffuser of |t|^2 (the normalisation of g, Algorithm S2). Values
 // are non-negative floats, whose bit patterns order like integers.
 __global__ void k_max_abs2(const float2* __restrict__ t, size_t n, float* out) {
   float m = 0.f;
@@ -260,7 +260,7 @@ __global__ void k_mean(const float* __restrict__ I, size_t n, double* out) {
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s / (double)n);
 }
 
-// g = (Re g + i Re Filter(Im g, P^-1)) + (Re a Re rho + i Im a Im rho); Nesterov.
+// g = (Re g + i Re F^-1{P^-1 F{Im g}}) + (Re a Re rho + i Im a Im rho); Nesterov.
 __global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __restrict__ S,
                                  const float2* __restrict__ H, float2* psi, float2* phi, size_t n, float eta,
                                  float are, float aim, const float* beta_p, double* acc) {
@@ -829,7 +829,7 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     LAUNCH(p, row(p, ROW_INTENSITY, a, nproj_of(p)));   // v stored; F_row{|v|^2}
     a.yhat = p->YH;
     LAUNCH(p, col(p, COL_RESID_IOTF2, a, nproj_of(p))); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
-    LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v Filter(-e, IOTF)
+    LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v F^-1{IOTF F{-e}}
   }
   if ((r = fused_backprop(p, a, t, joint, nproj_of(p), p->GT))) return r;
   a.psi = psi;
@@ -948,7 +948,7 @@ pwf_status plain_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   cudaStream_t s = p->stream;
   float2 *X = p->X, *V = p->V, *S = p->S, *H = p->YH;
   pwf_status r;
-  // PhysicalModel
+  // forward model, Eq. (1)
   k_exp<<<G, 256, 0, s>>>(psi + o, X + o, n);
   if ((r = plain_filter(p, X, proj, PF_Q, 1, 0))) return r;
   k_mul_t<<<G, 256, 0, s>>>(X + o, t, n, 0);
@@ -957,7 +957,7 @@ pwf_status plain_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   if ((r = plain_filter(p, X, proj, PF_IOTF, 0, 0))) return r;
   // e = y - f
   k_resid<<<G, 256, 0, s>>>(X + o, y + o, n, p->acc + (size_t)proj * NACC + ACC_LOSS);
-  // WirtingerDerivative
+  // Wirtinger derivative (back-propagation)
   if ((r = plain_filter(p, X, proj, PF_IOTF, 0, 0))) return r;
   k_mul_v_real<<<G, 256, 0, s>>>(X + o, V + o, n);
   if ((r = plain_filter(p, X, proj, PF_Q, 2, 1))) return r;
@@ -967,7 +967,7 @@ pwf_status plain_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   // Preconditioner
   k_split<<<G, 256, 0, s>>>(X + o, p->REG + o, S + o, n);
   if ((r = plain_filter(p, S, proj, PF_PINV, 0, 0))) return r;
-  // Regularizer
+  // regularizer, Eqs. (14)-(15)
   k_copy<<<G, 256, 0, s>>>(psi + o, H + o, n);
   if ((r = plain_filter(p, H, proj, PF_GAMMA2, 0, 0))) return r;
   // Nesterov
@@ -1244,9 +1244,9 @@ pwf_status pwf_gradient(pwf_plan* p, const void* psi, const void* t, const float
   } else {
     a.v = p->V;
     LAUNCH(p, row(p, ROW_INTENSITY, a, a.B));   // |v|^2, v kept
-    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // f = Filter(|v|^2, IOTF)
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // f = F^-1{IOTF F{|v|^2}}
     LAUNCH(p, row(p, ROW_RESID, a, a.B));       // e = y - f; loss; -e
-    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // Filter(-e, IOTF)
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // F^-1{IOTF F{-e}}
     LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v g
   }
   if ((r = fused_backprop(p, a, (const float2*)t, false, a.B))) return r;
@@ -1339,7 +1339,7 @@ pwf_status pwf_forward_vjp(pwf_plan* p, const void* psi, const void* t, const fl
     a.out = p->X;
     a.y = grad_f;
     LAUNCH(p, row(p, ROW_REAL_FFT, a, a.B));    // F_row{grad_f}
-    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // Filter(grad_f, IOTF)
+    LAUNCH(p, col(p, COL_IOTF, a, a.B));        // F^-1{IOTF F{grad_f}}
     a.v = p->V;
     LAUNCH(p, row(p, ROW_MUL_V, a, a.B));       // v G
   }

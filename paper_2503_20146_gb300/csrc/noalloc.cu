@@ -153,6 +153,11 @@ extern "C" pwf_status pwf_forward_noalloc(const pwf_plan_desc* desc, const void*
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0)
     return PWF_ERR_INVALID_ARG;
+  // the n_modes values pwf_plan_create accepts; only the paper's forms (0, 1)
+  // are computed here, the source-mode variant needs a plan
+  if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
+    return PWF_ERR_INVALID_ARG;
+  if (d.n_modes > 1) return PWF_ERR_UNSUPPORTED;
   const LengthKernels* krow = kernels_for_length(d.nx);
   const LengthKernels* kcol = kernels_for_length(d.ny);
   if (!krow || !kcol) return PWF_ERR_UNSUPPORTED;

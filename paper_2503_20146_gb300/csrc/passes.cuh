@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
       const float2 p = a.psi[rb + x];
       const float2 fp = a.phi[rb + x];
       const float gr = a.reg[rb + x];
-      // g = Preconditioner(g) + Regularizer(psi) = Re g + z
+      // total direction: preconditioned g plus the regularizer term = Re g + z
       const float2 g = make_float2(gr + v[j].x, v[j].y);
       const float2 f = make_float2(fmaf(-a.eta, g.x, p.x), fmaf(-a.eta, g.y, p.y));
       const float2 pn = make_float2(fmaf(beta, f.x - fp.x, f.x), fmaf(beta, f.y - fp.y, f.y));

@@ -33,7 +33,7 @@ def blob_batch(w: S.Workload, batch: int, ny=None, nx=None, seed_proj0=0):
 
 def measurement(psi_true_b, t, geom, photons, config):
     """y = Poisson(photons * f(psi_true)) / photons, f from the oracle."""
-    f = O.physical_model_batch(psi_true_b, t, geom)
+    f = O.intensity_batch(psi_true_b, t, geom)
     return np.stack([S.poisson_measurement(f[b], photons, S.rng_for(config, 50 + b)) for b in range(len(f))])
 
 

@@ -36,8 +36,8 @@ def plan_for(P, g):
 def reference_speckle(g, seed):
     """Partially coherent reference speckle without the sample (Eq. (1), psi = 0)."""
     t = S.diffuser(g.ny, g.nx, S.rng_for(7, seed))
-    I_coh = np.abs(O.FreePropagation(t, g, g.L2)) ** 2
-    return O.Filter(I_coh, O.iotf(g)).real
+    I_coh = np.abs(O.propagate(t, g, g.L2)) ** 2
+    return O.fourier_filter(I_coh, O.iotf(g)).real
 
 
 @pytest.mark.parametrize("ny,nx,max_lag", [(256, 256, 3), (128, 512, 3), (1024, 1024, 4)])

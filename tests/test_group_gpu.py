@@ -37,7 +37,7 @@ def _class_inputs(ny, nx, batch, seed):
     psi_true, t = blob_batch(W2, batch, ny, nx, seed_proj0=seed)
     rng = np.random.default_rng(seed)
     photons = np.exp(rng.uniform(np.log(1e3), np.log(1e5), batch))       # per projection
-    f = np.stack([O.PhysicalModel(p, t, geom)[0] for p in psi_true])
+    f = np.stack([O.intensity(p, t, geom) for p in psi_true])
     y = np.stack([S.poisson_measurement(f[b], photons[b], S.rng_for(5, seed + b)) for b in range(batch)])
     return geom, to_c64(t), to_f32(y)
 
@@ -69,10 +69,10 @@ def test_group_matches_individual_solves_and_oracle(pwf):
             # and the oracle on the last projection of the class
             b = d.batch - 1
             if K > 1:
-                ref = O.modal_pwf(y[b].astype(np.float64), t.astype(np.complex128), geom,
+                ref = O.modal_solve(y[b].astype(np.float64), t.astype(np.complex128), geom,
                                   O.source_modes(geom, K, 2.0), iters)
             else:
-                ref = O.pwf(y[b].astype(np.float64), t.astype(np.complex128), geom, iters)
+                ref = O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, iters)
             assert phase_rms(psis[k].cpu().numpy()[b], ref.psi) <= 1e-3
     finally:
         pwf.pwf_group_destroy(g)

@@ -68,7 +68,7 @@ def test_host_solve_matches_device_solve(pwf, w, batch, ny, nx, chunk):
 def test_host_solve_matches_oracle(pwf):
     g, t, y = case(W2, 3, 128, 128)
     n = 20
-    refs = [O.pwf(y[b].astype(np.float64), t.astype(np.complex128), g, n) for b in range(3)]
+    refs = [O.solve(y[b].astype(np.float64), t.astype(np.complex128), g, n) for b in range(3)]
     psi_h = np.zeros((3, 128, 128), np.complex64)             # pageable numpy buffers work too
     with plan_for(pwf, g, 3) as plan:
         it, loss = plan.solve_host(y, t, psi_h, n, psi_is_input=False, chunk=1)

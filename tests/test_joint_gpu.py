@@ -46,7 +46,7 @@ def perturbed_case(wname, batch, ny, nx):
 def test_joint_refinement_matches_oracle(pwf, wname, batch, ny, nx, iters):
     g, y, t0 = perturbed_case(wname, batch, ny, nx)
     eta_t = 3e-3
-    ref = O.joint_pwf(y, t0, g, iters, eta_t)
+    ref = O.joint_solve(y, t0, g, iters, eta_t)
     with plan_for(pwf, g, batch) as plan:
         t = dev(to_c64(t0))
         psi = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
@@ -74,7 +74,7 @@ def test_joint_with_zero_step_equals_solve(pwf):
 def test_joint_full_size_sample_matches_oracle(pwf):
     w = S.WORKLOADS["tomo180x1024_iotf"]
     g, y, t0 = perturbed_case("tomo180x1024_iotf", 4, w.ny, w.nx)
-    ref = O.joint_pwf(y, t0, g, 2, 1e-3)
+    ref = O.joint_solve(y, t0, g, 2, 1e-3)
     with plan_for(pwf, g, 4) as plan:
         t = dev(to_c64(t0))
         psi = torch.zeros((4, w.ny, w.nx), dtype=torch.complex64, device="cuda")

@@ -61,7 +61,7 @@ def test_modal_forward_gradient_vjp(pwf, name, K, batch, ny, nx):
     gt_ref = np.zeros_like(T64)
     for b in range(batch):
         P64 = psi[b].astype(np.complex128)
-        assert rel_l2(f[b], O.ModalPhysicalModel(P64, T64, geom, modes)[0]) <= FWD_TOL
+        assert rel_l2(f[b], O.modal_intensity(P64, T64, geom, modes)) <= FWD_TOL
         ge, le = O.modal_gradient(P64, T64, y[b].astype(np.float64), geom, modes)
         assert rel_l2(g[b], ge) <= GRAD_TOL
         assert abs(L[b] - le) <= 1e-5 * le
@@ -77,9 +77,9 @@ def test_modal_solve_matches_oracle(pwf, K, n, iters):
     modes = O.source_modes(geom, K, SIGMA)
     psi_true, t = blob_batch(W2, 1, n, n)
     t = to_c64(t)
-    f_true = O.ModalPhysicalModel(psi_true[0], t.astype(np.complex128), geom, modes)[0]
+    f_true = O.modal_intensity(psi_true[0], t.astype(np.complex128), geom, modes)
     y = to_f32(S.poisson_measurement(f_true, W2.photons, S.rng_for(W2.config, 77))[None])
-    ref = O.modal_pwf(y[0].astype(np.float64), t.astype(np.complex128), geom, modes, iters)
+    ref = O.modal_solve(y[0].astype(np.float64), t.astype(np.complex128), geom, modes, iters)
     with modal_plan(pwf, geom, 1, K) as plan:
         p = torch.zeros((1, n, n), dtype=torch.complex64, device="cuda")
         it, loss = plan.solve(dev(y), dev(t), p, iters)

@@ -35,7 +35,7 @@ def dft_matrix(n, sign):
 
 
 # ----------------------------------------------------------------------------
-# Filter (Algorithm S2) against the DFT definition and direct convolution
+# Fourier-domain filtering against the DFT definition and direct convolution
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("ny,nx", [(16, 16), (12, 12), (12, 16), (9, 8)])
 def test_filter_matches_bruteforce_dft(ny, nx):
@@ -45,7 +45,7 @@ def test_filter_matches_bruteforce_dft(ny, nx):
     Fy, Fx = dft_matrix(ny, -1), dft_matrix(nx, -1)
     X = Fy @ x @ Fx.T                                  # sum_{r} x_r e^{-2 pi i k.r / N}
     back = dft_matrix(ny, +1) @ (X * W) @ dft_matrix(nx, +1).T / (ny * nx)
-    got = O.Filter(x, W)
+    got = O.fourier_filter(x, W)
     assert np.max(np.abs(got - back)) <= 1e-12 * np.max(np.abs(back))
 
 
@@ -60,27 +60,27 @@ def test_filter_is_circular_convolution():
             for a in range(ny):
                 for b in range(nx):
                     conv[r, c] += x[a, b] * h[(r - a) % ny, (c - b) % nx]
-    got = O.Filter(x, np.fft.fft2(h))
+    got = O.fourier_filter(x, np.fft.fft2(h))
     assert np.max(np.abs(got - conv)) <= 1e-12 * np.max(np.abs(conv))
 
 
 # ----------------------------------------------------------------------------
-# FreePropagation
+# Free-space propagation (angular spectrum)
 # ----------------------------------------------------------------------------
 def test_propagation_identity_unitarity_semigroup_adjoint():
     rng = np.random.default_rng(2)
     g = geom(32, 24)
     x, y = crandn(rng, (32, 24)), crandn(rng, (32, 24))
-    assert np.max(np.abs(O.FreePropagation(x, g, 0.0) - x)) <= 1e-14 * np.max(np.abs(x))
-    px = O.FreePropagation(x, g, 0.3)
+    assert np.max(np.abs(O.propagate(x, g, 0.0) - x)) <= 1e-14 * np.max(np.abs(x))
+    px = O.propagate(x, g, 0.3)
     assert abs(np.linalg.norm(px) - np.linalg.norm(x)) <= 1e-13 * np.linalg.norm(x)
-    back = O.FreePropagation(px, g, -0.3)
+    back = O.propagate(px, g, -0.3)
     assert np.max(np.abs(back - x)) <= 1e-13 * np.max(np.abs(x))
-    two = O.FreePropagation(O.FreePropagation(x, g, 0.1), g, 0.25)
-    one = O.FreePropagation(x, g, 0.35)
+    two = O.propagate(O.propagate(x, g, 0.1), g, 0.25)
+    one = O.propagate(x, g, 0.35)
     assert np.max(np.abs(two - one)) <= 1e-12 * np.max(np.abs(one))
-    lhs = np.vdot(y, O.FreePropagation(x, g, 0.4))
-    rhs = np.vdot(O.FreePropagation(y, g, -0.4), x)
+    lhs = np.vdot(y, O.propagate(x, g, 0.4))
+    rhs = np.vdot(O.propagate(y, g, -0.4), x)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
@@ -96,7 +96,7 @@ def test_propagation_matches_paraxial_gaussian_beam():
     zr = math.pi * w0 ** 2 / lam
     q = w0 ** 2 * (1 + 1j * z / zr)
     expect = np.exp(-r2 / q) / (1 + 1j * z / zr)
-    got = O.FreePropagation(np.exp(-r2 / w0 ** 2), g, z)
+    got = O.propagate(np.exp(-r2 / w0 ** 2), g, z)
     assert np.max(np.abs(got - expect)) <= 1e-9
     # and the beam really changed (z/zR ~ 0.3)
     assert np.max(np.abs(expect - np.exp(-r2 / w0 ** 2))) > 0.1
@@ -107,10 +107,10 @@ def test_piston_reading_matches_literal_transfer_function():
     w = S.WORKLOADS["blob128_coherent"]
     psi, t = S.blob_case(w)
     g = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m)
-    v1 = O.Filter(O.Filter(np.exp(psi), O.transfer_function_literal(g, g.L1)) * t,
+    v1 = O.fourier_filter(O.fourier_filter(np.exp(psi), O.transfer_function_literal(g, g.L1)) * t,
                   O.transfer_function_literal(g, g.L2))
     f_lit = np.abs(v1) ** 2
-    f = O.PhysicalModel(psi, t, g)[0]
+    f = O.intensity(psi, t, g)
     # The literal phase 2 pi w L is ~4e10 rad; fp64 keeps it to ~1e-5 rad.
     assert np.linalg.norm(f - f_lit) <= 2e-5 * np.linalg.norm(f)
 
@@ -135,7 +135,7 @@ def test_iotf_is_fourier_pair_of_ipsf():
     g = geom(ny, nx, xcoh=xc, ycoh=yc, pixel=p)
     delta = np.zeros((ny, nx))
     delta[0, 0] = 1.0
-    blur = O.Filter(delta, O.iotf(g)).real
+    blur = O.fourier_filter(delta, O.iotf(g)).real
     yy = np.fft.fftfreq(ny, 1.0 / ny)[:, None] * p        # signed periodic offsets
     xx = np.fft.fftfreq(nx, 1.0 / nx)[None, :] * p
     ipsf = 2.0 / (xc * yc) * np.exp(-2 * np.pi * (xx ** 2 / xc ** 2 + yy ** 2 / yc ** 2))
@@ -154,7 +154,7 @@ def test_stf_is_iotf_power_and_window_vanishes_at_dc():
 
 
 # ----------------------------------------------------------------------------
-# Preconditioner (Eq. (11)) and Regularizer (Algorithm S2)
+# Preconditioner (Eq. (11)) and regularization window (Eqs. (14)-(15))
 # ----------------------------------------------------------------------------
 def test_preconditioner_closed_form_on_a_cosine():
     ny, nx, ky, kx = 32, 48, 3, 5
@@ -162,7 +162,7 @@ def test_preconditioner_closed_form_on_a_cosine():
     yy, xx = np.mgrid[0:ny, 0:nx]
     c = np.cos(2 * np.pi * (ky * yy / ny + kx * xx / nx))
     gin = 0.7 * c + 1j * (c + 2.5)            # Re part untouched, DC of Im dropped
-    out = O.Preconditioner(gin, O.precond_filter(g))
+    out = O.precondition(gin, O.precond_filter(g))
     scale = 1.0 / ((ky / ny) ** 2 + (kx / nx) ** 2)    # cycles per pixel (R3)
     assert np.max(np.abs(out.real - 0.7 * c)) < 1e-12
     assert np.max(np.abs(out.imag - scale * c)) < 1e-9 * scale
@@ -172,12 +172,12 @@ def test_regularizer_special_cases():
     rng = np.random.default_rng(3)
     psi = crandn(rng, (16, 20))
     ones = np.ones((16, 20))
-    assert np.max(np.abs(O.Regularizer(psi, ones, 1 + 1j) - psi)) < 1e-13
-    r = O.Regularizer(psi, ones, 0.1 + 0.01j)
+    assert np.max(np.abs(O.regularization(psi, ones, 1 + 1j) - psi)) < 1e-13
+    r = O.regularization(psi, ones, 0.1 + 0.01j)
     assert np.max(np.abs(r - (0.1 * psi.real + 0.01j * psi.imag))) < 1e-13
     g = geom(16, 20, xcoh=7e-6, ycoh=7e-6)
     const = np.full((16, 20), 2.0 - 3.0j)      # DC only: Gamma^2(0) = 0
-    assert np.max(np.abs(O.Regularizer(const, O.reg_window(g), 0.1 + 0.01j))) < 1e-13
+    assert np.max(np.abs(O.regularization(const, O.reg_window(g), 0.1 + 0.01j))) < 1e-13
 
 
 # ----------------------------------------------------------------------------
@@ -187,15 +187,15 @@ def test_forward_flat_and_energy_conservation():
     rng = np.random.default_rng(4)
     g = geom(32, 32, xcoh=6e-6, ycoh=6e-6)
     t = np.exp(1j * rng.standard_normal((32, 32)))
-    f0 = O.PhysicalModel(np.zeros((32, 32), complex), t, O.Geometry(32, 32, 1e-6, 6.2e-11, 0.0, 0.0, 6e-6, 6e-6))[0]
+    f0 = O.intensity(np.zeros((32, 32), complex), t, O.Geometry(32, 32, 1e-6, 6.2e-11, 0.0, 0.0, 6e-6, 6e-6))
     assert np.max(np.abs(f0 - 1.0)) < 1e-13                  # P_0 = I, |t| = 1, IOTF(0) = 1
     psi = 0.2 * crandn(rng, (32, 32))
-    f = O.PhysicalModel(psi, t, g)[0]
+    f = O.intensity(psi, t, g)
     assert abs(np.sum(f) - np.sum(np.exp(2 * psi.real))) < 1e-11 * np.sum(f)
 
 
 # ----------------------------------------------------------------------------
-# Loss and gradient (Eq. (2), Algorithm S2 WirtingerDerivative)
+# Loss and gradient (Eq. (2); the Wirtinger derivative of Results)
 # ----------------------------------------------------------------------------
 def _fd_case(seed=5, n=32, coherent=False):
     rng = np.random.default_rng(seed)
@@ -215,8 +215,8 @@ def test_gradient_matches_central_differences(coherent):
         d = crandn(rng, psi.shape)
         an = np.sum(G.real * d.real + G.imag * d.imag)
         for eps, tol in ((1e-3, 1e-4), (1e-6, 1e-7)):
-            Lp = O.loss(y, O.PhysicalModel(psi + eps * d, t, g)[0])
-            Lm = O.loss(y, O.PhysicalModel(psi - eps * d, t, g)[0])
+            Lp = O.loss(y, O.intensity(psi + eps * d, t, g))
+            Lm = O.loss(y, O.intensity(psi - eps * d, t, g))
             assert abs((Lp - Lm) / (2 * eps) - an) <= tol * abs(an)
 
 
@@ -228,11 +228,11 @@ def test_vjp_matches_central_differences_for_psi_and_diffuser():
     for grad, which in ((gp, "psi"), (gt, "t")):
         d = crandn(rng, psi.shape)
         if which == "psi":
-            Fp = np.sum(gf * O.PhysicalModel(psi + eps * d, t, g)[0])
-            Fm = np.sum(gf * O.PhysicalModel(psi - eps * d, t, g)[0])
+            Fp = np.sum(gf * O.intensity(psi + eps * d, t, g))
+            Fm = np.sum(gf * O.intensity(psi - eps * d, t, g))
         else:
-            Fp = np.sum(gf * O.PhysicalModel(psi, t + eps * d, g)[0])
-            Fm = np.sum(gf * O.PhysicalModel(psi, t - eps * d, g)[0])
+            Fp = np.sum(gf * O.intensity(psi, t + eps * d, g))
+            Fm = np.sum(gf * O.intensity(psi, t - eps * d, g))
         an = np.sum(grad.real * d.real + grad.imag * d.imag)
         assert abs((Fp - Fm) / (2 * eps) - an) <= 1e-7 * abs(an)
 
@@ -241,13 +241,13 @@ def test_truth_is_stationary():
     w = S.WORKLOADS["blob128_coherent"]
     psi, t = S.blob_case(w)
     g = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, 5e-6, 5e-6)
-    y = O.PhysicalModel(psi, t, g)[0]
-    gr, L = O.gradient(psi, t, y, g)
+    y = O.intensity(psi, t, g)
+    gr, L = O.wirtinger_gradient(psi, t, y, g)
     assert L < 1e-20 and np.max(np.abs(gr)) < 1e-12
 
 
 # ----------------------------------------------------------------------------
-# Algorithm S1 loop
+# The PWF loop (Algorithm S1): Nesterov's step, recovery, stopping rule
 # ----------------------------------------------------------------------------
 def test_nesterov_sequence_and_first_step():
     mu1 = O.nesterov_mu(1.0)
@@ -255,12 +255,16 @@ def test_nesterov_sequence_and_first_step():
     rng, g, psi, t, y = _fd_case(seed=7, n=16)
     g = O.Geometry(**{**g.__dict__, "eta": 0.01})
     zero = np.zeros_like(psi)
-    psi1, phi1, m1, _ = O.pwf_iteration(zero, zero, 1.0, y, t, g)
+    solver = O.PWFSolver(O.SpeckleModel(g, t), g)
+    mom = O.Momentum(np.zeros_like(psi))
+    psi1, _ = solver.step(zero, y, mom)
+    phi1, m1 = mom.phi, mom.mu
     assert np.array_equal(psi1, phi1)                              # (mu_prev - 1) = 0
-    gr, _ = O.gradient(zero, t, y, g)
-    step = O.Preconditioner(gr, O.precond_filter(g))               # Regularizer(0) = 0
+    gr, _ = O.wirtinger_gradient(zero, t, y, g)
+    step = O.precondition(gr, O.precond_filter(g))               # the regularizer of psi = 0 is 0
     assert np.max(np.abs(psi1 + 0.01 * step)) < 1e-15 + 1e-12 * np.max(np.abs(psi1))
-    psi2, phi2, m2, _ = O.pwf_iteration(psi1, phi1, m1, y, t, g)
+    psi2, _ = solver.step(psi1, y, mom)
+    phi2, m2 = mom.phi, mom.mu
     beta = (m1 - 1) / m2
     assert abs(beta - ((1 + math.sqrt(5)) / 2 - 1) / O.nesterov_mu(mu1)) < 1e-15
     assert np.max(np.abs(psi2 - (phi2 + beta * (phi2 - phi1)))) < 1e-14
@@ -274,12 +278,12 @@ def test_noise_free_recovery_blob128():
     w = S.WORKLOADS["blob128_coherent"]
     psi_true, t = S.blob_case(w)
     g = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, eta=2.0 ** -10)
-    y = O.PhysicalModel(psi_true, t, g)[0]
-    r = O.pwf(y, t, g, 200)
+    y = O.intensity(psi_true, t, g)
+    r = O.solve(y, t, g, 200)
     assert r.losses[0] / r.losses[-1] > 1e3
-    f = O.PhysicalModel(r.psi, t, g)[0]
+    f = O.intensity(r.psi, t, g)
     assert np.linalg.norm(f - y) < 1e-3 * np.linalg.norm(y)
-    assert np.linalg.norm(O.PhysicalModel(np.zeros_like(psi_true), t, g)[0] - y) > 0.03 * np.linalg.norm(y)
+    assert np.linalg.norm(O.intensity(np.zeros_like(psi_true), t, g) - y) > 0.03 * np.linalg.norm(y)
 
 
 def test_stop_rule_reading():
@@ -287,6 +291,22 @@ def test_stop_rule_reading():
     x = np.exp(1j * np.linspace(0, 1, 50))
     assert abs(O.correlation(x, x) - 1.0) < 1e-15
     assert abs(O.correlation(3.0 * x, x) - 1.0) < 1e-15             # scale-free
+
+
+def test_correlation_is_phase_blind_and_matches_a_hand_computed_pair():
+    # a global phase rotation leaves the field unchanged up to its phase: the
+    # modulus of the inner product (not its real part) makes the correlation 1
+    rng = np.random.default_rng(40)
+    x = crandn(rng, (8, 6))
+    for theta in (0.3, 1.5, math.pi):
+        assert abs(O.correlation(x * np.exp(1j * theta), x) - 1.0) < 1e-14
+    # x_old = (1, i), x_new = (1, 1): <x_old, x_new> = 1 - i, |.| = sqrt 2, norms sqrt 2 each
+    c = O.correlation(np.array([1.0, 1.0]), np.array([1.0, 1j]))
+    assert abs(c - math.sqrt(2.0) / 2.0) < 1e-15
+    # orthogonal fields correlate to 0; the measure is symmetric
+    assert O.correlation(np.array([1.0, 0.0]), np.array([0.0, 1.0])) == 0.0
+    y = crandn(rng, (8, 6))
+    assert abs(O.correlation(x, y) - O.correlation(y, x)) < 1e-15
 
 
 # ----------------------------------------------------------------------------
@@ -319,8 +339,8 @@ def test_single_mode_is_the_coherent_model():
     g = geom(32, 48)
     psi = 0.3 * crandn(rng, (32, 48))
     t = np.exp(1j * rng.standard_normal((32, 48)))
-    f1 = O.ModalPhysicalModel(psi, t, g, [(0, 0, 1.0)])[0]
-    assert np.max(np.abs(f1 - O.PhysicalModel(psi, t, g)[0])) < 1e-13
+    f1 = O.modal_intensity(psi, t, g, [(0, 0, 1.0)])
+    assert np.max(np.abs(f1 - O.intensity(psi, t, g))) < 1e-13
 
 
 @pytest.mark.parametrize("mx,my", [(3, -2), (-5, 7), (0, 31), (47, 0)])
@@ -346,12 +366,12 @@ def test_tilted_modes_shift_the_field_by_lambda_L2_q():
     rng = S.rng_for(1, 5)
     psi = 0.4j * np.angle(S.diffuser(n, n, rng, corr_px=6.0, std_rad=1.0)) - 0.02
     t = S.diffuser(n, n, rng, corr_px=6.0, std_rad=0.5)
-    v0 = O.ModalPhysicalModel(psi, t, g, [(0, 0, 1.0)])[2][0]
+    v0 = O.ModalSpeckleModel(g, t, [(0, 0, 1.0)]).evaluate(psi).v[0]
     V0 = np.fft.fft2(v0)
     kx = np.fft.fftfreq(n)[None, :]
     ky = np.fft.fftfreq(n)[:, None]
     for mx, my in ((3, 0), (-2, 5)):
-        vm = O.ModalPhysicalModel(psi, t, g, [(mx, my, 1.0)])[2][0]
+        vm = O.ModalSpeckleModel(g, t, [(mx, my, 1.0)]).evaluate(psi).v[0]
         qx, qy = mx / (n * g.pixel), my / (n * g.pixel)
         dx, dy = g.wavelength * g.L2 * qx / g.pixel, g.wavelength * g.L2 * qy / g.pixel   # pixels
         shifted = np.fft.ifft2(V0 * np.exp(-2j * np.pi * (kx * dx + ky * dy)))
@@ -374,8 +394,8 @@ def test_modal_gradient_matches_central_differences():
         d = crandn(rng, psi.shape)
         an = np.sum(G.real * d.real + G.imag * d.imag)
         eps = 1e-6
-        Lp = O.loss(y, O.ModalPhysicalModel(psi + eps * d, t, g, modes)[0])
-        Lm = O.loss(y, O.ModalPhysicalModel(psi - eps * d, t, g, modes)[0])
+        Lp = O.loss(y, O.modal_intensity(psi + eps * d, t, g, modes))
+        Lm = O.loss(y, O.modal_intensity(psi - eps * d, t, g, modes))
         assert abs((Lp - Lm) / (2 * eps) - an) <= 1e-7 * abs(an)
 
 
@@ -392,8 +412,8 @@ def test_modal_vjp_matches_central_differences():
         d = crandn(rng, psi.shape)
         a = (psi + eps * d, t) if which == "psi" else (psi, t + eps * d)
         b = (psi - eps * d, t) if which == "psi" else (psi, t - eps * d)
-        Fp = np.sum(gf * O.ModalPhysicalModel(a[0], a[1], g, modes)[0])
-        Fm = np.sum(gf * O.ModalPhysicalModel(b[0], b[1], g, modes)[0])
+        Fp = np.sum(gf * O.modal_intensity(a[0], a[1], g, modes))
+        Fm = np.sum(gf * O.modal_intensity(b[0], b[1], g, modes))
         an = np.sum(grad.real * d.real + grad.imag * d.imag)
         assert abs((Fp - Fm) / (2 * eps) - an) <= 1e-7 * abs(an)
 
@@ -405,15 +425,10 @@ def test_without_preconditioner_the_phase_is_underestimated():
     psi_true, t = S.blob_case(w)
     g = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, S.xcoh_from_blur_sigma(2.0),
                    S.xcoh_from_blur_sigma(2.0), eta=2.0 ** -9)
-    y = O.PhysicalModel(psi_true, t, g)[0]
-    with_p = O.pwf(y, t, g, 60).psi
+    y = O.intensity(psi_true, t, g)
+    with_p = O.solve(y, t, g, 60).psi
 
-    ones = np.ones((w.ny, w.nx))
-    psi = np.zeros_like(psi_true)
-    phi = np.zeros_like(psi)
-    mu = 1.0
-    for _ in range(60):
-        psi, phi, mu, _ = O.pwf_iteration(psi, phi, mu, y, t, g, Pinv=ones)
+    psi = O.solve(y, t, g, 60, Pinv=np.ones((w.ny, w.nx))).psi
     rms = lambda a: float(np.sqrt(np.mean((a.imag - a.imag.mean()) ** 2)))  # noqa: E731
     assert rms(psi) < 0.1 * rms(with_p)
     assert rms(with_p) > 0.2 * rms(psi_true)
@@ -453,26 +468,26 @@ def test_wiener_inverts_a_noise_free_blur_and_the_diffuser_reproduces_the_refere
     n = 64
     g = O.Geometry(n, n, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4, 3e-6, 3.5e-6)
     t_true = S.diffuser(n, n, S.rng_for(1, 6))
-    I_coh = np.abs(O.FreePropagation(t_true, g, g.L2)) ** 2     # coherent reference speckle
-    I_ref = O.Filter(I_coh, O.iotf(g)).real                     # partial coherence (Eq. (1), no sample)
+    I_coh = np.abs(O.propagate(t_true, g, g.L2)) ** 2     # coherent reference speckle
+    I_ref = O.fourier_filter(I_coh, O.iotf(g)).real                     # partial coherence (Eq. (1), no sample)
     assert np.max(np.abs(O.wiener_deconvolve(I_ref, g, 1e-14) - I_coh)) < 1e-8
     t = O.diffuser_from_reference(I_ref, g, 1e-14)
-    v = O.FreePropagation(t, g, g.L2)
+    v = O.propagate(t, g, g.L2)
     assert np.max(np.abs(np.abs(v) ** 2 - I_coh)) < 1e-7         # reproduces the reference
     assert np.max(np.abs(v.imag)) < 1e-7                         # zero phase at the detector
 
 
 @pytest.mark.parametrize("coherent", [False, True])
 def test_diffuser_gradient_matches_central_differences(coherent):
-    # dL/dRe t + i dL/dIm t = 4 max|t|^2 g_t (the normalisation of Algorithm S2)
+    # dL/dRe t + i dL/dIm t = 4 max|t|^2 g_t (g's normalisation: factor 2 dropped, / max|t|^2)
     rng, g, psi, t, y = _fd_case(seed=21, coherent=coherent)
     gt = 4.0 * np.max(np.abs(t) ** 2) * O.diffuser_gradient(psi, t, y, g)
     for _ in range(3):
         d = crandn(rng, t.shape)
         an = np.sum(gt.real * d.real + gt.imag * d.imag)
         eps = 1e-6
-        Lp = O.loss(y, O.PhysicalModel(psi, t + eps * d, g)[0])
-        Lm = O.loss(y, O.PhysicalModel(psi, t - eps * d, g)[0])
+        Lp = O.loss(y, O.intensity(psi, t + eps * d, g))
+        Lm = O.loss(y, O.intensity(psi, t - eps * d, g))
         assert abs((Lp - Lm) / (2 * eps) - an) <= 1e-7 * abs(an)
 
 
@@ -481,15 +496,15 @@ def _joint_case(n=32, B=3):
     g = O.Geometry(n, n, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m, w.gamma, w.alpha, w.eta)
     t = S.diffuser(n, n, S.rng_for(w.config, 99))
     psi_true = np.stack([S.complex_phase_from(S.blob_phase(n, n, S.rng_for(w.config, b))) for b in range(B)])
-    f = O.physical_model_batch(psi_true, t, g)
+    f = O.intensity_batch(psi_true, t, g)
     y = np.stack([S.poisson_measurement(f[b], 1e4, S.rng_for(w.config, 50 + b)) for b in range(B)])
     return g, t, y
 
 
 def test_joint_refinement_with_zero_step_is_algorithm_s1_per_projection():
     g, t, y = _joint_case()
-    r = O.joint_pwf(y, t, g, 6, 0.0)
-    plain = O.pwf_batch(y, t, g, 6)
+    r = O.joint_solve(y, t, g, 6, 0.0)
+    plain = O.solve_batch(y, t, g, 6)
     for b in range(len(y)):
         assert np.max(np.abs(r.psi[b] - plain[b].psi)) < 1e-12
     assert np.array_equal(r.t, t)
@@ -499,14 +514,14 @@ def test_joint_refinement_with_zero_step_is_algorithm_s1_per_projection():
 def test_joint_refinement_lowers_the_loss_from_a_perturbed_diffuser():
     g, t, y = _joint_case(n=48, B=3)
     t0 = t * np.exp(0.3j * np.angle(S.diffuser(48, 48, np.random.default_rng(5))))
-    fixed = O.joint_pwf(y, t0, g, 25, 0.0)
-    joint = O.joint_pwf(y, t0, g, 25, 3e-3)
+    fixed = O.joint_solve(y, t0, g, 25, 0.0)
+    joint = O.joint_solve(y, t0, g, 25, 3e-3)
     assert joint.losses[-1] < 0.97 * fixed.losses[-1]
     assert not np.array_equal(joint.t, t0)
 
 
 def test_linear_pieces_are_adjoint_to_1e_12():
-    # <A x, y> = <x, A^H y> for every linear piece of Algorithm S2: the Filters
+    # <A x, y> = <x, A^H y> for every linear piece of the forward chain: the Fourier windows
     # with the real, even windows (IOTF, P^-1, Gamma^2; self-adjoint), the
     # propagations (adjoint P(-L)), the multiplication by t (adjoint conj(t))
     rng = np.random.default_rng(31)
@@ -519,11 +534,110 @@ def test_linear_pieces_are_adjoint_to_1e_12():
         assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0), (lhs, rhs)
 
     for W in (O.iotf(g), O.precond_filter(g), O.reg_window(g)):
-        check(lambda v, W=W: O.Filter(v, W), lambda v, W=W: O.Filter(v, W))
+        check(lambda v, W=W: O.fourier_filter(v, W), lambda v, W=W: O.fourier_filter(v, W))
     for L in (g.L1, g.L2):
-        check(lambda v, L=L: O.FreePropagation(v, g, L), lambda v, L=L: O.FreePropagation(v, g, -L))
+        check(lambda v, L=L: O.propagate(v, g, L), lambda v, L=L: O.propagate(v, g, -L))
     check(lambda v: t * v, lambda v: np.conj(t) * v)
-    # the chain of Algorithm S2's back-propagation is the adjoint of the forward chain
-    fwd = lambda v: O.FreePropagation(t * O.FreePropagation(v, g, g.L1), g, g.L2)
-    bwd = lambda v: O.FreePropagation(np.conj(t) * O.FreePropagation(v, g, -g.L2), g, -g.L1)
+    # the back-propagation (propagation over -L, conj(t)) is the adjoint of the forward chain
+    fwd = lambda v: O.propagate(t * O.propagate(v, g, g.L1), g, g.L2)
+    bwd = lambda v: O.propagate(np.conj(t) * O.propagate(v, g, -g.L2), g, -g.L1)
     check(fwd, bwd)
+    # the operator objects the forward model is built from carry the same adjoints
+    Wc = crandn(rng, (24, 20))
+    check(O.FourierMultiplier(Wc), O.FourierMultiplier(Wc).H)
+    check(O.Pointwise(t), O.Pointwise(t).H)
+    P1 = O.propagator(g, g.L1)
+    assert np.max(np.abs(P1.H(x) - O.propagate(x, g, -g.L1))) < 1e-13 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("modal", [False, True])
+def test_pullback_is_the_adjoint_of_the_linearised_forward_model(modal):
+    # For real df: sum df . (J dpsi) = 2 Re <pullback(df), dpsi>, with J the
+    # derivative of f at psi, formed here by forward-mode perturbation of the
+    # chain (dx = x dpsi, du1 = P1 dx, dv = P2(t du1) [+ P2(dt u1)],
+    # dI = 2 Re(conj(v) dv), df = K dI), independently of the reverse sweep.
+    rng = np.random.default_rng(41)
+    g = geom(20, 24, xcoh=5e-6, ycoh=4e-6)
+    psi = 0.3 * crandn(rng, (20, 24))
+    t = np.exp(1j * rng.standard_normal((20, 24))) * (1 + 0.2 * rng.standard_normal((20, 24)))
+    df = rng.standard_normal((20, 24))
+    dpsi_in, dt_in = crandn(rng, (20, 24)), crandn(rng, (20, 24))
+    if modal:
+        modes = [(0, 0, 0.5), (2, -1, 0.3), (-3, 4, 0.2)]
+        m = O.ModalSpeckleModel(g, t, modes)
+    else:
+        modes = [(0, 0, 1.0)]
+        m = O.SpeckleModel(g, t)
+    tr = m.evaluate(psi)
+    gp, gt = m.pullback(tr, df)
+    x = np.exp(psi)
+    Q1, Q2, K = O.transfer_function(g, g.L1), O.transfer_function(g, g.L2), O.iotf(g)
+    jp = np.zeros((20, 24))
+    jt = np.zeros((20, 24))
+    for mx, my, w in modes:
+        s = O.mode_wave(g, mx, my)
+        u1 = np.fft.ifft2(np.fft.fft2(x * s) * Q1)
+        v = np.fft.ifft2(np.fft.fft2(t * u1) * Q2)
+        dv_p = np.fft.ifft2(np.fft.fft2(t * np.fft.ifft2(np.fft.fft2(x * s * dpsi_in) * Q1)) * Q2)
+        dv_t = np.fft.ifft2(np.fft.fft2(dt_in * u1) * Q2)
+        jp += w * 2.0 * np.real(np.conj(v) * dv_p)
+        jt += w * 2.0 * np.real(np.conj(v) * dv_t)
+    if not modal:
+        jp = np.fft.ifft2(np.fft.fft2(jp) * K).real
+        jt = np.fft.ifft2(np.fft.fft2(jt) * K).real
+    for grad, d, j in ((gp, dpsi_in, jp), (gt, dt_in, jt)):
+        lhs = np.sum(df * j)
+        rhs = 2.0 * np.real(np.vdot(grad, d))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ----------------------------------------------------------------------------
+# Source-mode bins and weights (reading R13): the walk-off distribution
+# ----------------------------------------------------------------------------
+def _walk_off(g, n_modes, sigma_px):
+    """(s_x, s_y, w): detector walk-off of every mode in pixels, s = lambda (L1 +
+    L2) q / p with q = m / (N p) the tilt of bin m, and the mode weights."""
+    modes = O.source_modes(g, n_modes, sigma_px)
+    z = g.wavelength * (g.L1 + g.L2)
+    sx = np.array([mx / (g.nx * g.pixel) for mx, _, _ in modes]) * z / g.pixel
+    sy = np.array([my / (g.ny * g.pixel) for _, my, _ in modes]) * z / g.pixel
+    return sx, sy, np.array([w for _, _, w in modes]), modes
+
+
+@pytest.mark.parametrize("n,n_modes", [(1024, 9), (1024, 25), (512, 9), (2048, 25), (768, 25)])
+def test_source_mode_walk_off_has_the_gaussian_moments(n, n_modes):
+    """The K tilts and weights discretise a Gaussian source whose walk-off at
+    the detector has standard deviation sigma pixels per axis, the axes
+    independent: mean 0, second moment sigma^2, fourth moment 3 sigma^4
+    (exact for the 3- and 5-point rules), cross moment 0 and
+    E[s_x^2 s_y^2] = sigma^4, each within the bound that rounding the tilt to
+    whole bins (at most half a bin, Delta / 2 pixels) allows."""
+    sigma = 2.0
+    g = O.Geometry(n, n, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4)
+    sx, sy, w, modes = _walk_off(g, n_modes, sigma)
+    assert len({(mx, my) for mx, my, _ in modes}) == n_modes
+    assert all(isinstance(mx, int) and isinstance(my, int) for mx, my, _ in modes)
+    delta = g.wavelength * (g.L1 + g.L2) / (n * g.pixel ** 2)        # one bin in pixels
+    assert delta < 0.1                                                # fine enough for 4th moments
+    h = delta / 2
+    smax = np.max(np.abs(sx)) + h
+    assert abs(np.sum(w) - 1.0) < 1e-14
+    for s in (sx, sy):
+        assert abs(np.sum(w * s)) <= h + 1e-12                        # symmetric rule
+        assert abs(np.sum(w * s ** 2) - sigma ** 2) <= 2 * smax * h + h * h
+        assert abs(np.sum(w * s ** 4) - 3 * sigma ** 4) <= 4 * smax ** 3 * h + 1e-9
+    assert abs(np.sum(w * sx * sy)) <= 2 * smax * h
+    assert abs(np.sum(w * sx ** 2 * sy ** 2) - sigma ** 4) <= 4 * smax ** 3 * h
+    # the marginal of each axis is the 1-D rule: weights of equal s_x sum to the 1-D weights
+    nodes, weights = O.gauss_hermite(int(round(math.sqrt(n_modes))))
+    for node, wt in zip(nodes, weights):
+        sel = np.abs(sx - sigma * node) <= h + 1e-12
+        assert abs(np.sum(w[sel]) - wt) < 1e-14
+
+
+def test_source_modes_degenerate_cases():
+    g = O.Geometry(256, 256, 1e-6, S.WAVELENGTH_20KEV_M, 0.1, 0.4)
+    assert O.source_modes(g, 1, 2.0) == [(0, 0, 1.0)]                 # one mode: the coherent model
+    assert all(mx == 0 and my == 0 for mx, my, _ in O.source_modes(g, 9, 0.0))
+    with pytest.raises(ValueError):
+        O.source_modes(g, 8, 2.0)

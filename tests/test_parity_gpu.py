@@ -66,7 +66,7 @@ def case_inputs(w, batch, ny, nx, coherent):
 @pytest.mark.parametrize("name,w,batch,ny,nx,coh", CASES, ids=[c[0] for c in CASES])
 def test_forward_parity(pwf, name, w, batch, ny, nx, coh):
     geom, psi, t = case_inputs(w, batch, ny, nx, coh)
-    expect = O.physical_model_batch(psi.astype(np.complex128), t.astype(np.complex128), geom)
+    expect = O.intensity_batch(psi.astype(np.complex128), t.astype(np.complex128), geom)
     with plan_for(pwf, geom, batch) as plan:
         f = plan.forward(dev(psi), dev(t)).cpu().numpy()
     assert rel_l2(f, expect) <= FWD_TOL
@@ -111,7 +111,7 @@ def _solve_case(w, batch, ny=None, nx=None):
 @pytest.mark.parametrize("w,batch", [(W1, 1), (W2, 1)], ids=["blob128_coherent_50it", "blob512_iotf_100it"])
 def test_solve_parity(pwf, w, batch):
     geom, t, y = _solve_case(w, batch)
-    ref = [O.pwf(y[b].astype(np.float64), t.astype(np.complex128), geom, w.n_iter) for b in range(batch)]
+    ref = [O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, w.n_iter) for b in range(batch)]
     psi = torch.zeros((batch, w.ny, w.nx), dtype=torch.complex64, device="cuda")
     with plan_for(pwf, geom, batch) as plan:
         iters, loss = plan.solve(dev(y), dev(t), psi, w.n_iter)
@@ -126,7 +126,7 @@ def test_step_matches_solve_and_oracle_losses(pwf):
     w = W2
     geom, t, y = _solve_case(w, 2, 128, 128)
     n = 12
-    ref = [O.pwf(y[b].astype(np.float64), t.astype(np.complex128), geom, n) for b in range(2)]
+    ref = [O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, n) for b in range(2)]
     with plan_for(pwf, geom, 2) as plan:
         a = torch.zeros((2, 128, 128), dtype=torch.complex64, device="cuda")
         plan.solve(dev(y), dev(t), a, n)
@@ -169,12 +169,8 @@ def test_ablation_flags_match_oracle(pwf, flags):
         Gamma2 = O.reg_window(geom)
         alpha = 0j
     g2 = O.Geometry(**{**geom.__dict__, "alpha": alpha})
-    psi = np.zeros((128, 128), complex)
-    phi = np.zeros_like(psi)
-    mu = 1.0
-    for _ in range(n):
-        psi, phi, mu, _ = O.pwf_iteration(psi, phi, mu, y[0].astype(np.float64), t.astype(np.complex128), g2,
-                                          Pinv, Gamma2)
+    solver = O.PWFSolver(O.SpeckleModel(g2, t.astype(np.complex128)), g2, Pinv, Gamma2)
+    psi = solver.solve(y[0].astype(np.float64), n).psi
     with plan_for(pwf, geom, 1, flags) as plan:
         p = torch.zeros((1, 128, 128), dtype=torch.complex64, device="cuda")
         plan.solve(dev(y), dev(t), p, n)
@@ -182,17 +178,31 @@ def test_ablation_flags_match_oracle(pwf, flags):
 
 
 def test_stopping_rule_matches_oracle(pwf):
+    # The stopping iteration is an integer that floating point decides: the
+    # threshold is put halfway across the widest step of the oracle's
+    # correlation sequence (iterations 10..80, a step of 2e-6), so that the
+    # FP32 path, whose correlations follow the oracle's far closer than the
+    # 1e-6 half-step, must stop at exactly the same iteration; the retrieved
+    # phase is then compared as usual.
     w = W1
     geom, t, y = _solve_case(w, 1)
-    tol = 0.99999          # first crossed after ~40-60 iterations (the early steps are small)
-    ref = O.pwf(y[0].astype(np.float64), t.astype(np.complex128), geom, 200, corr_tol=tol)
-    assert ref.iterations < 200
+    y64, t128 = y[0].astype(np.float64), t.astype(np.complex128)
+    free = O.solve(y64, t128, geom, 80)
+    c = np.array(free.correlations)
+    best_k, margin = None, 0.0
+    for k in range(10, len(c)):
+        m = c[k] - np.max(c[:k])
+        if m > margin:
+            best_k, margin = k, m
+    assert best_k is not None and margin >= 1e-6, margin
+    tol = float(np.max(c[:best_k]) + margin / 2)
+    ref = O.solve(y64, t128, geom, 200, corr_tol=tol)
+    assert ref.iterations == best_k + 1
     with plan_for(pwf, geom, 1) as plan:
         psi = torch.zeros((1, w.ny, w.nx), dtype=torch.complex64, device="cuda")
         iters, _ = plan.solve(dev(y), dev(t), psi, 200, corr_tol=tol)
-    assert abs(int(iters[0]) - ref.iterations) <= 1
-    if int(iters[0]) == ref.iterations:
-        assert phase_rms(psi.cpu().numpy()[0], ref.psi) <= PHASE_TOL
+    assert int(iters[0]) == ref.iterations
+    assert phase_rms(psi.cpu().numpy()[0], ref.psi) <= PHASE_TOL
 
 
 def test_checkpoint_resume_is_bitwise(pwf):
@@ -263,11 +273,11 @@ def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
         p = p.cpu().numpy()
     for b in (0, batch // 2, batch - 1):
         P64, T64 = psi[b].astype(np.complex128), t.astype(np.complex128)
-        assert rel_l2(f[b], O.PhysicalModel(P64, T64, geom)[0]) <= FWD_TOL
-        ge, le = O.gradient(P64, T64, y[b].astype(np.float64), geom)
+        assert rel_l2(f[b], O.intensity(P64, T64, geom)) <= FWD_TOL
+        ge, le = O.wirtinger_gradient(P64, T64, y[b].astype(np.float64), geom)
         assert rel_l2(g[b], ge) <= GRAD_TOL
         assert abs(L[b] - le) <= 1e-5 * le
-        ref = O.pwf(y[b].astype(np.float64), T64, geom, 3)
+        ref = O.solve(y[b].astype(np.float64), T64, geom, 3)
         assert phase_rms(p[b], ref.psi) <= PHASE_TOL
 
 
@@ -306,9 +316,9 @@ def test_every_column_shape_matches_oracle(pwf, ny, nx, batch):
     y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(6).standard_normal((batch, ny, nx)), 0, None))
     P64, T64 = psi.astype(np.complex128), t.astype(np.complex128)
     b = batch - 1
-    f_ref = O.PhysicalModel(P64[b], T64, geom)[0]
-    g_ref, _ = O.gradient(P64[b], T64, y[b].astype(np.float64), geom)
-    ref3 = O.pwf(y[b].astype(np.float64), T64, geom, 2)
+    f_ref = O.intensity(P64[b], T64, geom)
+    g_ref, _ = O.wirtinger_gradient(P64[b], T64, y[b].astype(np.float64), geom)
+    ref3 = O.solve(y[b].astype(np.float64), T64, geom, 2)
     with plan_for(pwf, geom, batch) as plan:
         nshape = max(pwf.pwf_plan_column_shapes(plan.handle, op) for op in range(6))
         assert nshape >= 3
@@ -354,7 +364,7 @@ def test_full_size_tomo_forward_sampled(pwf, tomo):
     with plan_for(pwf, geom, psi.shape[0]) as plan:
         f = plan.forward(psi32, dev(t32))
     for b in (0, 97, 179):
-        expect = O.PhysicalModel(psi32[b].cpu().numpy().astype(np.complex128), t32.astype(np.complex128), geom)[0]
+        expect = O.intensity(psi32[b].cpu().numpy().astype(np.complex128), t32.astype(np.complex128), geom)
         assert rel_l2(f[b].cpu().numpy(), expect) <= FWD_TOL
 
 
@@ -372,7 +382,7 @@ def test_full_size_tomo_iterations_sampled(pwf, tomo):
         iters, loss = plan.solve(y, dev(t32), psi, 3)
     assert list(iters) == [3] * psi.shape[0]
     for b in (5, 150):
-        ref = O.pwf(y[b].cpu().numpy().astype(np.float64), t32.astype(np.complex128), geom, 3)
+        ref = O.solve(y[b].cpu().numpy().astype(np.float64), t32.astype(np.complex128), geom, 3)
         got = psi[b].cpu().numpy()
         assert phase_rms(got, ref.psi) <= PHASE_TOL
         # attenuation (Re psi) to the same absolute bound
