@@ -78,8 +78,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
     ap.add_argument("--legs", default="all",
-                    help="comma list of extra legs to run (plain,e2e,modal,mixed,autograd,fbp,ablation,cpu) or all")
-    ap.add_argument("--overlap", action="store_true", help="two half-batch chains (PWF_FLAG_OVERLAP)")
+                    help="comma list of extra legs to run (plain,e2e,modal,small,mixed,autograd,fbp,ablation,cpu) "
+                         "or all")
     return ap.parse_args()
 
 
@@ -177,17 +177,21 @@ class ClockSampler:
 # workload synthesis (seeded; on the GPU for speed)
 # ----------------------------------------------------------------------------
 def make_workload(P, S, w, batch, device, rank=0, world=1):
-    """Rank r of `world` takes every world-th angle of a world*batch-angle series
-    (weak scaling: each rank solves its own batch of distinct projections)."""
+    """Rank r of `world` takes its cost-balanced share of a world*batch-angle
+    series (shard.shard_projections; weak scaling: each rank solves its own
+    batch of distinct projections, no exchange during the iterations)."""
     import numpy as np
     import torch
+    from paper_2503_20146_gb300 import shard
     n = w.ny
     if w.name.startswith("tomo"):
         ph = S.ellipsoid_phantom(S.rng_for(w.config, 0), size=n)
         xd, yd = S.detector_grid(n, n, xp=torch)
         xd, yd = xd.to(device), yd.to(device)
-        psi_true = torch.empty((batch, n, n), dtype=torch.complex64, device=device)
-        for i, ang in enumerate(S.tomo_angles(batch * world)[rank::world]):
+        angles = S.tomo_angles(batch * world)
+        mine = shard.shard_projections([(n, n, w.n_modes)] * (batch * world), world, rank)
+        psi_true = torch.empty((len(mine), n, n), dtype=torch.complex64, device=device)
+        for i, ang in enumerate(angles[mine]):
             re, im = S.ellipsoid_projection(ph, float(ang), xd, yd, w.wavelength_m)
             psi_true[i] = torch.complex(re, im).to(torch.complex64)
     else:
@@ -294,50 +298,81 @@ def peaks():
 # ----------------------------------------------------------------------------
 # oracle timing on the host (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
-CPU_SAMPLE_ITERS = 24  # ~0.5 s per 1024^2 iteration on one host core
+CPU_SAMPLE_ITERS = 12  # ~0.5-1 s per 1024^2 iteration on one host core
 
 
-def oracle_sample(w, n_proj, seed_iters):
-    """Times the FP64 oracle on n_proj projections of the workload's size
-    (blob objects stand in for the phantom: the oracle's cost does not depend
-    on the values) for `seed_iters` iterations; returns (seconds, Mpx*it)."""
+def oracle_job(wname, b, iters):
+    """The unchanged FP64 oracle on projection b of the workload's size (blob
+    measurements stand in for the phantom: the oracle's cost does not depend
+    on the values) for `iters` iterations, in a worker process; returns the
+    seconds the solve took."""
     import numpy as np
     from oracle import pwf_oracle as O
     from paper_2503_20146_gb300 import synth as S
+    w = S.WORKLOADS[wname]
     geom = O.Geometry(w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m, w.gamma,
                       w.alpha, w.eta)
     t = S.diffuser(w.ny, w.nx, S.rng_for(w.config, 99))
-    ys = [np.clip(1.0 + 0.1 * S.rng_for(w.config, 200 + b).standard_normal((w.ny, w.nx)), 0, None)
-          for b in range(n_proj)]
+    y = np.clip(1.0 + 0.1 * S.rng_for(w.config, 200 + b).standard_normal((w.ny, w.nx)), 0, None)
     t0 = time.perf_counter()
-    for y in ys:
-        O.solve(y, t, geom, seed_iters)
-    dt = time.perf_counter() - t0
-    return dt, n_proj * w.ny * w.nx * seed_iters / 1e6
+    O.solve(y, t, geom, iters)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """One worker process per host core (spawn: the parent already holds a
+    CUDA context), each running the oracle single-threaded on its own
+    projection; a sample is `cores` projections solved at once."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.cores = cores or host_cores()
+        self.ex = ProcessPoolExecutor(max_workers=self.cores, mp_context=mp.get_context("spawn"))
+
+    def sample(self, w, iters):
+        """Wall-clock seconds for `cores` projections x `iters` iterations, and the Mpx*it done."""
+        t0 = time.perf_counter()
+        list(self.ex.map(oracle_job, [w.name] * self.cores, range(self.cores), [iters] * self.cores))
+        return time.perf_counter() - t0, self.cores * w.ny * w.nx * iters / 1e6
+
+    def close(self):
+        self.ex.shutdown()
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    # one step = one oracle iteration over one projection of the workload
+    # one step = one oracle iteration on each of `cores` projections, one
+    # worker process per host core
+    pool = OraclePool()
     for _ in range(args.warmup):
-        oracle_sample(w, 1, 1)
-    times = []
+        pool.sample(w, 1)
+    times, work = [], 0.0
     for _ in range(args.steps):
-        dt, _ = oracle_sample(w, 1, 1)
+        dt, mpx = pool.sample(w, 1)
         times.append(dt)
+        work += mpx
+    pool.close()
     total = sum(times)
-    value = args.steps * w.ny * w.nx / 1e6 / total
+    value = work / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: oracle on 1 of {w.batch} projections per step",
+        "config": {"workload": f"{w.name}: oracle on {pool.cores} of {w.batch} projections per step",
                    "ny": w.ny, "nx": w.nx, "batch": w.batch},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"1 projection of {w.ny}x{w.nx}, 1 iteration per step, numpy FP64 (single thread)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                         "sample": f"{pool.cores} projections of {w.ny}x{w.nx} (one per core, worker "
+                                   f"processes), 1 iteration per step, numpy FP64"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -407,6 +442,50 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
             "launch": "one CUDA graph launch per iteration over all four size classes",
             "model_bytes_per_px": bpp, "model_gbs": gbs, "model_frac_of_measured_hbm": gbs / hbm,
             "per_class_alone": per_class}
+
+
+def run_small(P, S, torch, dev, stream, reps=5):
+    """The single-projection workloads: 128^2 coherent (50 iterations) and
+    512^2 with partial coherence (100 iterations; IOTF form and K = 9 source
+    modes). One solve call of the workload's iterations is timed, graph replay
+    (the default) and the persistent launch. At these sizes an iteration is a
+    chain of ~13 kernels on a field that sits in L2: launch latency, not HBM,
+    sets the time, so no HBM fraction is reported."""
+    import numpy as np
+    out = {}
+    cases = (("blob128_coherent", 0), ("blob512_iotf", 0), ("blob512_iotf", 9))
+    for name, K in cases:
+        w = S.WORKLOADS[name]
+        psi_true = torch.from_numpy(S.complex_phase_from(S.blob_phase(w.ny, w.nx, S.rng_for(w.config, 0)))
+                                    .astype(np.complex64))[None].to(dev)
+        t = torch.from_numpy(S.diffuser(w.ny, w.nx, S.rng_for(w.config, 99)).astype(np.complex64)).to(dev)
+        paths = (("graph", P.FLAG_GRAPH), ("persistent", P.FLAG_PERSISTENT)) if K == 0 else (("graph", 0),)
+        for path, flags in paths:
+            plan = P.Plan(P.PlanDesc(1, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
+                                     w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags, K, 2.0 if K else 0.0))
+            f = plan.forward(psi_true, t)
+            g = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config)
+            y = (torch.poisson(f.clamp_min(0) * w.photons, generator=g) / w.photons).contiguous()
+            psi = torch.zeros_like(psi_true)
+            for _ in range(3):
+                psi.zero_()
+                plan.solve(y, t, psi, w.n_iter, read_back=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                psi.zero_()
+                plan.solve(y, t, psi, w.n_iter, read_back=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            key = f"{name}{'_k%d' % K if K else ''}_{path}"
+            out[key] = {"value": w.ny * w.nx * w.n_iter / 1e6 / (ms / 1e3), "unit": UNIT,
+                        "iterations_per_s": w.n_iter / (ms / 1e3), "us_per_iteration": 1e3 * ms / w.n_iter,
+                        "ms_per_solve": ms, "iterations": w.n_iter, "ny": w.ny, "nx": w.nx, "n_modes": K,
+                        "hbm_fraction": "not applicable (launch-latency bound, field resident in L2)"}
+            plan.close()
+    return out
 
 
 def run_autograd(P, S, torch, dev, stream, reps=3):
@@ -501,7 +580,7 @@ def main():
     mpx_iter = batch * w.ny * w.nx / 1e6
 
     psi_true, t = make_workload(P, S, w, batch, dev, rank, world)
-    plan = P.Plan(plan_desc(P, w, batch, P.FLAG_OVERLAP if args.overlap else 0))
+    plan = P.Plan(plan_desc(P, w, batch))
     f = plan.forward(psi_true, t)
     gen = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config + rank)
     y = (torch.poisson(f.clamp_min(0) * w.photons, generator=gen) / w.photons).contiguous()
@@ -607,7 +686,7 @@ def main():
     if not args.no_extras and rank == 0:
         if leg("plain"):
             # plain per-projection baseline (unfused, Algorithm S2 step by step) on a sample
-            nplain, iplain = 4, 2
+            nplain, iplain = 16, 5
             plain = P.Plan(plan_desc(P, w, nplain, P.FLAG_PLAIN))
             yp = y[:nplain].contiguous()
             pp = torch.zeros((nplain, w.ny, w.nx), dtype=torch.complex64, device=dev)
@@ -642,11 +721,31 @@ def main():
             mms = m0.elapsed_time(m1)
             mbpp = modal_bytes_per_px(wk.n_modes)
             mgbs = batch * w.ny * w.nx * mbpp / (mms / msteps / 1e3) / 1e9
-            extras["modal_k9"] = {"value": mpx_iter * msteps / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / msteps,
-                                  "workload": wk.name, "steps": msteps, "model_bytes_per_px": mbpp,
-                                  "model_gbs": mgbs, "model_frac_of_measured_hbm": mgbs / hbm}
+            pm.zero_()
+            mpasses = P.pwf_profile_iteration(mplan.handle, y, t, pm, 1)
+            mtot = {}
+            for name, pms in mpasses:
+                mtot[name] = mtot.get(name, 0.0) + pms
+            mdom = max(mtot, key=mtot.get)
+            mdom_ms = [pms for name, pms in mpasses if name == mdom]
+            mdom_avg = sum(mdom_ms) / len(mdom_ms)
+            mach = PASS_BYTES_PER_PX.get(mdom, 0) * batch * w.ny * w.nx / (mdom_avg / 1e3) / 1e9
+            extras["modal_k9"] = {"metric": METRIC, "value": mpx_iter * msteps / (mms / 1e3), "unit": UNIT,
+                                  "ms_per_step": mms / msteps, "workload": wk.name, "steps": msteps,
+                                  "config": {"workload": wk.name, "projections_per_gpu": batch, "ny": w.ny,
+                                             "nx": w.nx, "coherence": "9 source modes, sigma = 2 px"},
+                                  "model_bytes_per_px": mbpp, "model_gbs": mgbs, "model_frac_of_measured_hbm": mgbs / hbm,
+                                  "roofline": {"bound": "hbm", "kernel": mdom, "achieved": mach, "peak": hbm,
+                                               "unit": "GB/s", "frac": mach / hbm, "traffic": None,
+                                               "peak_kind": peak_kind, "launch_ms": mdom_avg,
+                                               "share_of_iteration": sum(mdom_ms) / sum(p for _, p in mpasses)},
+                                  "passes": [[n, round(x, 4)] for n, x in mpasses]}
             mplan.close()
             del pm
+
+        # the single-projection workloads (128^2 coherent, 512^2 partially coherent)
+        if leg("small") and w.name == "tomo180x1024_iotf":
+            extras["small"] = run_small(P, S, torch, dev, stream)
 
         # uneven batch: 16 each of 256^2, 768^2, 1536^2, 2048^2, 25 modes, one group
         if leg("mixed") and w.name == "tomo180x1024_iotf":
@@ -668,12 +767,16 @@ def main():
             del series
 
         if leg("cpu"):
-            # FP64 oracle on the host cores, bounded sample (~10 s of CPU work)
-            dt, work = oracle_sample(w, 1, CPU_SAMPLE_ITERS)
-            extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                      "sample": f"1 projection of {w.ny}x{w.nx}, {CPU_SAMPLE_ITERS} iterations, "
-                                                "numpy FP64 (single thread)",
+            # FP64 oracle on every host core (one worker process per core, each
+            # on its own projection), bounded sample (~10 s of CPU work per core)
+            pool = OraclePool()
+            pool.sample(w, 1)  # workers start and import numpy
+            dt, work = pool.sample(w, CPU_SAMPLE_ITERS)
+            extras["cpu_baseline"] = {"value": work / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                                      "sample": f"{pool.cores} projections of {w.ny}x{w.nx} (one per core), "
+                                                f"{CPU_SAMPLE_ITERS} iterations, numpy FP64",
                                       "seconds": dt}
+            pool.close()
 
     if rank == 0:
         line = {
@@ -684,8 +787,7 @@ def main():
                        "coherence": "IOTF, Gaussian sigma = 2 px" if w.xcoh_m > 0 else "coherent",
                        "eta": w.eta, "l2_flush": "inputs larger than L2 (state ~1.5 GB per field)",
                        "step": "one PWF iteration over all projections",
-                       "column_shapes": tuned,
-                       "overlap": "two half-batch chains offset by one pass" if args.overlap else "one chain"},
+                       "column_shapes": tuned},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "iteration": iteration,

@@ -48,7 +48,10 @@ typedef enum {
   PWF_ERR_NOMEM = 3,        /* device allocation failed */
   PWF_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
   PWF_ERR_NONFINITE = 5,    /* a non-finite loss was produced */
-  PWF_ERR_STATE = 6         /* state / plan mismatch or bad checkpoint buffer */
+  PWF_ERR_STATE = 6,        /* state / plan mismatch or bad checkpoint buffer */
+  PWF_ERR_TIMEOUT = 7       /* a device-side wait of the persistent solver ran
+                               out (pwf_plan_set_wait_limit); the GPU context
+                               stays usable, psi and the state are not defined */
 } pwf_status;
 
 typedef struct pwf_plan pwf_plan;
@@ -60,11 +63,12 @@ typedef struct pwf_state pwf_state;
 #define PWF_FLAG_PLAIN 0x4u      /* unfused per-operation kernels, one projection at
                                     a time: Algorithm S2 executed step by step     */
 #define PWF_FLAG_NO_TUNE 0x8u    /* skip the plan-time column-pass autotuning      */
-#define PWF_FLAG_OVERLAP 0x10u   /* pwf_solve iterates the two halves of the batch as
-                                    two graph branches offset by one pass, so column
-                                    passes (arithmetic-bound) of one half run beside
-                                    row passes (bandwidth-bound) of the other; column
-                                    shapes are then tuned among one-tile-per-CTA ones */
+#define PWF_FLAG_PERSISTENT 0x20u /* pwf_solve as ONE cooperative launch for all
+                                    iterations (grid barriers between the passes,
+                                    every wait bounded); square grids of 64, 128, 256
+                                    or 512 only, else PWF_ERR_UNSUPPORTED           */
+#define PWF_FLAG_GRAPH 0x40u     /* pwf_solve by CUDA-graph replay of one iteration
+                                    (the default; excludes PWF_FLAG_PERSISTENT)     */
 
 /* Inputs of Algorithm S1 other than y and t. All lengths in metres. */
 typedef struct {
@@ -164,7 +168,16 @@ pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_h
 
 /* Algorithm S1 from the caller's psi (Algorithm S1 starts from psi = 0; the
  * caller zeroes psi for that): up to max_iter iterations, with the stopping
- * rule when corr_tol > 0. Fused, batched kernels replayed from a CUDA graph.
+ * rule when corr_tol > 0. Fused, batched passes, run one of two ways:
+ *  - CUDA-graph replay: one iteration (its passes and the end-of-iteration
+ *    kernel) captured once and launched max_iter times;
+ *  - one persistent cooperative launch for all iterations (PWF_FLAG_PERSISTENT;
+ *    square IOTF/coherent plans of 64^2..512^2): the passes are split into
+ *    warp-sized items over every SM, with grid barriers between passes. Each
+ *    barrier waits at most the plan's wait limit; when a wait runs out the
+ *    launch ends early, and the call (or the next pwf_state_read) returns
+ *    PWF_ERR_TIMEOUT. Graph replay is the default: it measured faster at every
+ *    size the persistent launch serves.
  * iters_host / loss_host: HOST arrays of length B (may be NULL); when either is
  * given the call synchronises. psi is updated in place. */
 pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
@@ -197,8 +210,9 @@ pwf_status pwf_solve_host(pwf_plan* plan, const float* y_host, const void* t_hos
  * sample gradient (a plain gradient step; max|t|^2 is recomputed from the new
  * t). t (complex64 [ny][nx], device) is updated in place, as is psi.
  * eta_t = 0 reproduces pwf_solve with corr_tol = 0. Keeps B extra fields of
- * workspace (allocated on the first call). PWF_ERR_UNSUPPORTED for source-mode,
- * plain or overlapped plans; PWF_ERR_INVALID_ARG if eta_t < 0. */
+ * workspace (allocated on the first call). PWF_ERR_UNSUPPORTED for source-mode
+ * or plain plans; PWF_ERR_INVALID_ARG if eta_t < 0. It runs on the graph replay
+ * (also for PWF_FLAG_PERSISTENT plans). */
 pwf_status pwf_solve_joint(pwf_plan* plan, const float* y, void* t, void* psi, int32_t max_iter, double eta_t,
                            int32_t* iters_host, double* loss_host);
 
@@ -298,6 +312,14 @@ int32_t pwf_plan_column_shapes(const pwf_plan* plan, int32_t pass);
 pwf_status pwf_plan_set_column_shape(pwf_plan* plan, int32_t pass, int32_t shape);
 pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t iters,
                                  float* pass_ms, const char** pass_names, int32_t* n_passes);
+/* Longest wait of one grid barrier of the persistent solver, in SM clock
+ * cycles (clock64); default 2^31 (about one second). A limit of 0 makes the
+ * first barrier any CTA reaches before the others run out at once, which is
+ * how the timeout path is tested. PWF_ERR_INVALID_ARG for a negative limit.
+ * pwf_plan_uses_persistent: 1 if pwf_solve takes the persistent launch on
+ * this plan, 0 if it replays the graph, -1 for NULL. */
+pwf_status pwf_plan_set_wait_limit(pwf_plan* plan, int64_t cycles);
+int32_t pwf_plan_uses_persistent(const pwf_plan* plan);
 
 /* Forward model for callers that cannot allocate device memory. The paper has
  * no counterpart: this is an interface choice, not part of the method.

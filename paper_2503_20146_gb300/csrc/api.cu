@@ -1,18 +1,21 @@
 // C ABI of the PWF library: plans, filter tables, the pass schedules of
 // Algorithms S1/S2, the solver state, CUDA-graph replay of the fused iteration,
 // and the unfused per-operation baseline.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "../../include/pwf.h"
 #include "host_tables.h"
-#include "passes.cuh"
+#include "persist.cuh"
 
 namespace pwf {
 const LengthKernels* length_kernels_16();
@@ -26,6 +29,32 @@ const LengthKernels* length_kernels_768();
 const LengthKernels* length_kernels_1024();
 const LengthKernels* length_kernels_1536();
 const LengthKernels* length_kernels_2048();
+
+// TMA map of a batch of complex64 fields [B][ny][nx] as float32 [B][ny][2 nx]
+// with boxes of C columns x min(ny, 256) rows (the TMA-staged column shapes).
+// The encoder is the driver's, reached through the runtime's entry-point
+// query, so the library links only the runtime.
+bool encode_field_tmap(CUtensorMap* m, const void* base, int B, int ny, int nx, int C) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  if (!fn || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (nx & 1)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * nx, (cuuint64_t)ny, (cuuint64_t)B};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float2), (cuuint64_t)nx * ny * sizeof(float2)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * C), (cuuint32_t)tma_box_rows(ny), 1u};
+  const cuuint32_t estride[3] = {1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 const LengthKernels* kernels_for_length(int n) {
   switch (n) {
@@ -57,14 +86,6 @@ __global__ void k_max_abs2(const float2* __restrict__ t, size_t n, float* out) {
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
 }
 
-struct DevIter {
-  double mu;       // mu of Algorithm S1 after the last completed iteration
-  float beta;      // (mu_prev - 1)/mu for the next iteration
-  int iter;        // completed iterations
-  int n_active;    // projections still iterating
-  int nonfinite;   // a non-finite loss was seen
-};
-
 // End of one iteration: per-projection loss / correlation / stopping rule,
 // accumulator reset, and the Nesterov coefficients of the next iteration.
 __global__ void k_finalize(double* acc, int B, int* active, int* iters, double* loss, double* corr,
@@ -75,30 +96,13 @@ __global__ void k_finalize(double* acc, int B, int* active, int* iters, double* 
   int na = 0, nf = 0;
   for (int p = threadIdx.x; p < B; p += blockDim.x) {
     double* a = acc + (size_t)p * NACC;
-    if (active[p]) {
-      const double L = a[ACC_LOSS];
-      const double c = sqrt(a[ACC_XR] * a[ACC_XR] + a[ACC_XI] * a[ACC_XI]) / sqrt(a[ACC_XNEW] * a[ACC_XOLD]);
-      loss[p] = L;
-      corr[p] = c;
-      iters[p] += 1;
-      if (!isfinite(L)) nf = 1;
-      if (corr_tol > 0.0 && c > corr_tol) active[p] = 0;
-      else na += 1;
-    }
+    na += finalize_projection(p, a, active, iters, loss, corr, corr_tol, nf);
     for (int k = 0; k < NACC; k++) a[k] = 0.0;
   }
   atomicAdd(&s_active, na);
   if (nf) it->nonfinite = 1;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double mu_prev = it->mu;
-    const double mu = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu_prev * mu_prev));
-    const double mu_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu * mu));
-    it->mu = mu;
-    it->beta = (float)((mu - 1.0) / mu_next);
-    it->iter += 1;
-    it->n_active = s_active;
-  }
+  if (threadIdx.x == 0) finalize_momentum(it, s_active);
 }
 
 __global__ void k_state_reset(DevIter* it, int* active, int* iters, double* loss, double* corr, int B) {
@@ -114,6 +118,7 @@ __global__ void k_state_reset(DevIter* it, int* active, int* iters, double* loss
     it->iter = 0;
     it->n_active = B;
     it->nonfinite = 0;
+    it->status = PWF_OK;
   }
 }
 
@@ -149,7 +154,7 @@ enum PlainFilter : int { PF_Q = 0, PF_IOTF = 1, PF_PINV = 2, PF_GAMMA2 = 3, PF_W
 
 __global__ void k_exp(const float2* __restrict__ psi, float2* __restrict__ x, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    x[i] = cexpf2(psi[i]);
+    x[i] = cexpf_acc(psi[i]);
 }
 __global__ void k_filter(float2* X, int ny, int nx, int which, const float2* qx, const float2* qy, int conj,
                          const float* ix, const float* iy, const float* u2x, const float* u2y, const float* ex,
@@ -171,7 +176,7 @@ __global__ void k_filter(float2* X, int ny, int nx, int which, const float2* qx,
       const float r2 = u2x[kx] + u2y[ky];
       v = cscale(v, no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f));
     } else {
-      v = cscale(v, -expm1f(-(ex[kx] + ey[ky])));
+      v = cscale(v, -fmaf(ex[kx], ey[ky], ex[kx] + ey[ky]));  // Gamma^2 = 1 - STF_x STF_y
     }
     X[i] = v;
   }
@@ -209,7 +214,7 @@ __global__ void k_mul_v_real(float2* X, const float2* __restrict__ V, size_t n) 
 __global__ void k_grad(float2* X, const float2* __restrict__ psi, size_t n, const float* maxt2) {
   const float s = 1.0f / *maxt2;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    X[i] = cscale(cmulc(X[i], cexpf2(psi[i])), s);
+    X[i] = cscale(cmulc(X[i], cexpf_acc(psi[i])), s);
 }
 // REG = Re X; S = Im X (as a complex field with zero imaginary part)
 __global__ void k_split(const float2* __restrict__ X, float* reg, float2* S, size_t n) {
@@ -274,7 +279,7 @@ __global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __
     const float2 pn = make_float2(f.x + beta * (f.x - fp.x), f.y + beta * (f.y - fp.y));
     phi[i] = f;
     psi[i] = pn;
-    const float2 xo = cexpf2(p), xn = cexpf2(pn);
+    const float2 xo = cexpf2(p), xn = cexpf_acc(pn);
     const float2 c = cmulc(xn, xo);
     p0 += c.x;
     p1 += c.y;
@@ -323,7 +328,7 @@ struct AxisTables {
   float2* q2 = nullptr;
   float* iotf = nullptr;
   float* u2 = nullptr;   // squared frequency, cycles per pixel
-  float* stf = nullptr;  // pi gamma u^2 coh^2
+  float* stf = nullptr;  // STF - 1 of this axis, exp(-pi gamma u^2 coh^2) - 1
 };
 
 struct Mode {
@@ -368,6 +373,7 @@ struct pwf_plan {
   float2* YH = nullptr;
   double* acc = nullptr;
   float* maxt2 = nullptr;
+  int* kstatus = nullptr;    // set by a kernel whose bounded wait ran out (PWF_ERR_TIMEOUT)
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
   // solver
@@ -379,13 +385,6 @@ struct pwf_plan {
   float2* GT = nullptr;       // per-projection diffuser-gradient terms (joint refinement)
   pwf_status sticky = PWF_OK;
   char err[256] = "";
-  // overlap of two half-batches (PWF_FLAG_OVERLAP): the projection range of
-  // the passes being enqueued, and the per-pass events of the two chains
-  int rng_proj0 = 0, rng_nproj = 0;
-  int ovl_mode = 0;  // 0 off, 1 record after each pass, 2 wait before each pass
-  int ovl_k = 0;
-  std::vector<cudaEvent_t> ovl_ev;
-  cudaStream_t ovl_stream[2] = {nullptr, nullptr};
   // instrumentation: kernels enqueued, and per-pass event timing
   long long launches = 0;
   long long graph_kernels = 0;  // kernels in the captured iteration graph
@@ -394,6 +393,13 @@ struct pwf_plan {
   std::vector<const char*> prof_names;
   size_t prof_n = 0;
   HostPipe* pipe = nullptr;  // created by the first pwf_solve_host
+  // persistent solver (square grids of persist_size; see persist.cuh)
+  bool persist = false;          // pwf_solve takes the persistent launch
+  int persist_grid = 0;          // CTAs of the cooperative launch
+  long long wait_cap = 1ll << 31;  // clock64 cycles one grid barrier may wait
+  double* gpart = nullptr;       // [persist_grid][B][NACC]
+  unsigned* bar = nullptr;       // grid barrier words
+  PersistPhase* phases = nullptr;  // device copy of the iteration's passes
 };
 
 namespace {
@@ -463,7 +469,7 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
     q2[k] = make_float2((float)std::cos(a2), (float)std::sin(a2));
     io[k] = (float)std::exp(-0.5 * M_PI * u * u * coh * coh);
     u2[k] = (float)(f * f);
-    st[k] = (float)(M_PI * d.gamma * u * u * coh * coh);
+    st[k] = (float)std::expm1(-M_PI * d.gamma * u * u * coh * coh);  // STF of this axis minus 1, Eq. (14)
   }
   pwf_status r;
   if ((r = dalloc(p, &A.tw_fwd, tlf)) || (r = dalloc(p, &A.tw_inv, tli)) || (r = dalloc(p, &A.q1, n)) ||
@@ -492,6 +498,7 @@ PassArgs base_args(pwf_plan* p) {
   a.nx = p->d.nx;
   a.maxt2 = p->maxt2;
   a.acc = p->acc;
+  a.kstatus = p->kstatus;
   a.scale = (float)(1.0 / ((double)p->d.nx * p->d.ny));
   a.eta = (float)p->d.eta;
   const bool no_reg = (p->d.flags & PWF_FLAG_NO_REG) != 0;
@@ -500,12 +507,12 @@ PassArgs base_args(pwf_plan* p) {
   a.no_precond = (p->d.flags & PWF_FLAG_NO_PRECOND) ? 1 : 0;
   a.gscale = 1.0f;
   a.mode_w = 1.0f;
-  a.proj0 = p->rng_proj0;
+  a.proj0 = 0;
   return a;
 }
 
-// projections covered by the passes being enqueued (all, or one half when overlapping)
-int nproj_of(const pwf_plan* p) { return p->rng_nproj > 0 ? p->rng_nproj : p->d.batch; }
+// projections covered by the passes being enqueued
+int nproj_of(const pwf_plan* p) { return p->d.batch; }
 
 const char* const kRowNames[NUM_ROW_OPS] = {
     "row_exp_fft", "row_real_fft", "row_fft", "row_ifft", "row_mul_t", "row_intensity", "row_intensity_out",
@@ -517,18 +524,6 @@ const char* const kColNames[NUM_COL_OPS] = {"col_q", "col_iotf", "col_resid_iotf
 // Enqueues one kernel; under pwf_profile_iteration it is bracketed by events.
 template <class F>
 cudaError_t enqueue(pwf_plan* p, const char* name, F&& launch) {
-  if (p->ovl_mode) {  // chain B waits for chain A's pass k; chain A marks it
-    if (p->ovl_k >= (int)p->ovl_ev.size()) return cudaErrorInvalidValue;
-    if (p->ovl_mode == 2) {
-      cudaError_t e = cudaStreamWaitEvent(p->stream, p->ovl_ev[p->ovl_k], 0);
-      if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = launch();
-    p->launches++;
-    if (e == cudaSuccess && p->ovl_mode == 1) e = cudaEventRecord(p->ovl_ev[p->ovl_k], p->stream);
-    p->ovl_k++;
-    return e;
-  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (p->prof) {
     if (p->prof_n + 2 > p->ev_pool.size()) {
@@ -552,13 +547,14 @@ cudaError_t enqueue(pwf_plan* p, const char* name, F&& launch) {
   return e;
 }
 
-// row pass on axis x, column pass on axis y
-cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
+// the tables a row pass on axis x, a column pass on axis y and a propagator
+// column pass (Q1 or Q2, conjugated for the back-propagation) read
+PassArgs row_args(const pwf_plan* p, PassArgs a) {
   a.tw_fwd = p->ax.tw_fwd;
   a.tw_inv = p->ax.tw_inv;
-  return enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
+  return a;
 }
-cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
+PassArgs col_args(const pwf_plan* p, PassArgs a) {
   a.tw_fwd = p->ay.tw_fwd;
   a.tw_inv = p->ay.tw_inv;
   a.qx = nullptr;
@@ -568,14 +564,28 @@ cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a.u2y = p->ay.u2;
   a.ex = p->ax.stf;
   a.ey = p->ay.stf;
-  return enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
+  return a;
 }
-cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
+PassArgs colq_args(const pwf_plan* p, PassArgs a, int which, int conj) {
   a.tw_fwd = p->ay.tw_fwd;
   a.tw_inv = p->ay.tw_inv;
   a.qx = which == 1 ? p->ax.q1 : p->ax.q2;
   a.qy = which == 1 ? p->ay.q1 : p->ay.q2;
   a.conj_q = conj;
+  return a;
+}
+
+// row pass on axis x, column pass on axis y
+cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
+  a = row_args(p, a);
+  return enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
+}
+cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
+  a = col_args(p, a);
+  return enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
+}
+cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
+  a = colq_args(p, a, which, conj);
   return enqueue(p, kColNames[COL_Q],
                  [&] { return p->kcol->colv[COL_Q][p->colsel[COL_Q]].launch(a, nproj, p->stream); });
 }
@@ -775,7 +785,7 @@ pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
   const size_t per = (size_t)p->d.ny * p->d.nx;
   dim3 grid((unsigned)((per + 255) / 256 > 64 ? 64 : (per + 255) / 256), (unsigned)nproj_of(p));
   return enqueue(p, "modal_resid", [&] {
-           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc, p->rng_proj0);
+           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc, 0);
            return cudaGetLastError();
          }) == cudaSuccess
              ? PWF_OK
@@ -808,8 +818,7 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     a.psi_out = psi;
     a.phi = st->phi;
     LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
-    if (p->ovl_mode == 0)
-      LAUNCH(p, enqueue(p, "finalize", [&] {
+    LAUNCH(p, enqueue(p, "finalize", [&] {
         k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it,
                                              corr_tol);
         return cudaGetLastError();
@@ -841,8 +850,7 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   a.psi_out = psi;
   a.phi = st->phi;
   LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
-  if (p->ovl_mode == 0)
-    LAUNCH(p, enqueue(p, "finalize", [&] {
+  LAUNCH(p, enqueue(p, "finalize", [&] {
       k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
       return cudaGetLastError();
     }));
@@ -860,43 +868,77 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   return PWF_OK;
 }
 
-// One iteration as two chains over the halves of the batch, captured from
-// p->capture_stream; finalize runs once after both.
-pwf_status overlapped_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
-                                double corr_tol) {
-  cudaStream_t main = p->capture_stream;
-  const int B = p->d.batch, B1 = B / 2;
-  cudaEvent_t fork = p->ovl_ev[p->ovl_ev.size() - 1], joinA = p->ovl_ev[p->ovl_ev.size() - 2],
-              joinB = p->ovl_ev[p->ovl_ev.size() - 3];
-  PWF_CUDA(p, cudaEventRecord(fork, main));
-  pwf_status r = PWF_OK;
-  for (int h = 0; h < 2 && r == PWF_OK; h++) {
-    cudaStream_t s = p->ovl_stream[h];
-    PWF_CUDA(p, cudaStreamWaitEvent(s, fork, 0));
-    p->stream = s;
-    p->rng_proj0 = h == 0 ? 0 : B1;
-    p->rng_nproj = h == 0 ? B1 : B - B1;
-    p->ovl_mode = h == 0 ? 1 : 2;
-    p->ovl_k = 0;
-    r = fused_iteration(p, st, y, t, psi, true, corr_tol);
-    if (r == PWF_OK && p->ovl_k > (int)p->ovl_ev.size() - 3) r = fail(p, PWF_ERR_STATE, "too many passes to overlap");
-    if (r == PWF_OK) {
-      cudaError_t e = cudaEventRecord(h == 0 ? joinA : joinB, s);
-      if (e != cudaSuccess) r = cuda_fail(p, e, "join");
-    }
+// The passes of one fused iteration (IOTF or coherent form, the same order
+// and arguments as fused_iteration) for the persistent solver, ending with the
+// end-of-iteration step.
+void persist_schedule(const pwf_plan* p, const pwf_state* st, const float* y, const float2* t, float2* psi,
+                      std::vector<PersistPhase>& ph) {
+  PassArgs a = base_args(const_cast<pwf_plan*>(p));
+  a.active = st->active;
+  a.beta = &st->it->beta;
+  a.in = p->X;
+  a.out = p->X;
+  auto row_ph = [&](int op, const PassArgs& b) { ph.push_back({PK_ROW, op, 0, row_args(p, b)}); };
+  auto col_ph = [&](int op, const PassArgs& b) { ph.push_back({PK_COL, op, 0, col_args(p, b)}); };
+  auto colq_ph = [&](const PassArgs& b, int which, int conj) {
+    ph.push_back({PK_COL, COL_Q, 0, colq_args(p, b, which, conj)});
+  };
+  colq_ph(a, 1, 0);                       // P1
+  a.t = t;
+  a.conj_t = 0;
+  row_ph(ROW_MUL_T, a);                   // t P1{x}
+  colq_ph(a, 2, 0);                       // P2
+  a.y = y;
+  if (p->coherent) {
+    row_ph(ROW_COH_RESID, a);             // e = y - |v|^2; loss; v (-e)
+  } else {
+    a.v = p->V;
+    row_ph(ROW_INTENSITY, a);             // v stored; F_row{|v|^2}
+    a.yhat = p->YH;
+    col_ph(COL_RESID_IOTF2, a);           // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
+    row_ph(ROW_MUL_V, a);                 // v F^-1{IOTF F{-e}}
   }
-  p->ovl_mode = 0;
-  p->ovl_k = 0;
-  p->rng_proj0 = 0;
-  p->rng_nproj = 0;
-  p->stream = main;
-  if (r) return r;
-  PWF_CUDA(p, cudaStreamWaitEvent(main, joinA, 0));
-  PWF_CUDA(p, cudaStreamWaitEvent(main, joinB, 0));
-  LAUNCH(p, enqueue(p, "finalize", [&] {
-    k_finalize<<<1, 256, 0, main>>>(p->acc, B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
-    return cudaGetLastError();
-  }));
+  colq_ph(a, 2, 1);                       // P2^H
+  a.conj_t = 1;
+  row_ph(ROW_MUL_T, a);                   // conj(t)
+  colq_ph(a, 1, 1);                       // P1^H
+  a.psi = psi;
+  a.reg = p->REG;
+  a.aux = p->S;
+  row_ph(ROW_GRAD_PACK, a);               // Re g; F_row{alpha o psi}; F_row{Im g}
+  a.aux_in = p->S;
+  col_ph(COL_PRECOND_REG, a);             // Gamma^2 H + i P^-1 S
+  a.psi_out = psi;
+  a.phi = st->phi;
+  row_ph(ROW_NESTEROV_FFT, a);            // Nesterov; correlation sums; F_row{exp psi}
+  ph.back().flush = 1;
+  ph.push_back({PK_FINALIZE, 0, 0, a});
+}
+
+// All max_iter iterations as one cooperative launch (X holds F_row{exp psi}).
+pwf_status persist_solve(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi, int max_iter,
+                         double corr_tol) {
+  std::vector<PersistPhase> ph;
+  persist_schedule(p, st, y, t, psi, ph);
+  if ((int)ph.size() > PERSIST_MAX_PHASES) return fail(p, PWF_ERR_STATE, "too many passes for the persistent solver");
+  PWF_CUDA(p, cudaMemcpyAsync(p->phases, ph.data(), ph.size() * sizeof(PersistPhase), cudaMemcpyHostToDevice,
+                              p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
+  PersistArgs pa{};
+  pa.phases = p->phases;
+  pa.nphases = (int)ph.size();
+  pa.B = p->d.batch;
+  pa.max_iter = max_iter;
+  pa.corr_tol = corr_tol;
+  pa.gpart = p->gpart;
+  pa.bar = p->bar;
+  pa.cap = p->wait_cap;
+  pa.active = st->active;
+  pa.iters = st->iters;
+  pa.loss = st->loss;
+  pa.corr = st->corr;
+  pa.it = st->it;
+  LAUNCH(p, enqueue(p, "persist", [&] { return p->kcol->persist(pa, p->persist_grid, p->stream); }));
   return PWF_OK;
 }
 
@@ -1009,14 +1051,16 @@ pwf_status tune_columns(pwf_plan* p) {
   a.ex = p->ax.stf;
   a.ey = p->ay.stf;
   cudaError_t err = cudaSuccess;
-  // when two half-batches overlap, persistent column kernels would fill the
-  // SMs and serialise the two chains: only one-tile-per-CTA shapes compete
-  const bool overlap = !p->ovl_ev.empty();
   for (int op = 0; op < NUM_COL_OPS && err == cudaSuccess; op++) {
     float best = 1e30f;
     for (int v = 0; v < p->kcol->ncolv[op] && err == cudaSuccess; v++) {
-      if (overlap && p->kcol->colv[op][v].pipe) continue;
       const PassFn fn = p->kcol->colv[op][v].launch;
+      if (p->kcol->colv[op][v].pipe == 5 && fn(a, a.B, p->stream) != cudaSuccess) {
+        // a TMA shape whose tensor map the driver would not encode: not offered
+        cudaGetLastError();
+        p->coltime[op][v] = 1e30f;
+        continue;
+      }
       if ((err = fn(a, a.B, p->stream)) != cudaSuccess) break;
       cudaEventRecord(e0, p->stream);
       for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) err = fn(a, a.B, p->stream);
@@ -1062,6 +1106,7 @@ const char* pwf_status_string(pwf_status s) {
     case PWF_ERR_CUDA: return "PWF_ERR_CUDA";
     case PWF_ERR_NONFINITE: return "PWF_ERR_NONFINITE";
     case PWF_ERR_STATE: return "PWF_ERR_STATE";
+    case PWF_ERR_TIMEOUT: return "PWF_ERR_TIMEOUT";
   }
   return "PWF_ERR_UNKNOWN";
 }
@@ -1074,8 +1119,10 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   const pwf_plan_desc& d = *desc;
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
-      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE | PWF_FLAG_OVERLAP)))
+      (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE |
+                   PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH)))
     return PWF_ERR_INVALID_ARG;
+  if ((d.flags & PWF_FLAG_PERSISTENT) && (d.flags & PWF_FLAG_GRAPH)) return PWF_ERR_INVALID_ARG;
   if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
     return PWF_ERR_INVALID_ARG;
   if (d.n_modes > 1 && (d.flags & PWF_FLAG_PLAIN)) return PWF_ERR_UNSUPPORTED;  // baseline is the paper's form
@@ -1103,6 +1150,7 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       (r = dalloc(p, &p->X, n)) || (r = dalloc(p, &p->S, n)) || (r = dalloc(p, &p->REG, n)) ||
       (r = dalloc(p, &p->V, n)) || (r = dalloc(p, &p->YH, n)) ||
       (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1)) ||
+      (r = dalloc(p, &p->kstatus, 1)) ||
       (!p->modes.empty() && ((r = dalloc(p, &p->M, n)) || (r = dalloc(p, &p->ACC, n)) ||
                              (r = dalloc(p, &p->IBUF, n))))) {
     pwf_plan_destroy(p);
@@ -1128,24 +1176,42 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
         return PWF_ERR_CUDA;
       }
   if (cudaMemset(p->acc, 0, (size_t)d.batch * NACC * sizeof(double)) != cudaSuccess ||
+      cudaMemset(p->kstatus, 0, sizeof(int)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     pwf_plan_destroy(p);
     return PWF_ERR_CUDA;
   }
-  if ((d.flags & PWF_FLAG_OVERLAP) && d.batch >= 2) {
-    bool ok = cudaStreamCreateWithFlags(&p->ovl_stream[0], cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&p->ovl_stream[1], cudaStreamNonBlocking) == cudaSuccess;
-    const size_t nev = 8 + 8 * (p->modes.size() + 4);  // passes per iteration, generously
-    for (size_t i = 0; i < nev && ok; i++) {
-      cudaEvent_t e;
-      ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-      if (ok) p->ovl_ev.push_back(e);
-    }
-    if (!ok) {
-      cudaGetLastError();
+  // persistent solver (PWF_FLAG_PERSISTENT): square IOTF/coherent plans of
+  // the built sizes. Not the default: on a GB300 its grid barriers cost more
+  // than the graph replay's launch gaps at every size it serves (128^2: 132
+  // against 56 us per iteration; 512^2: 180 against 80)
+  {
+    const bool eligible = p->kcol->persist != nullptr && d.nx == d.ny && p->modes.empty() &&
+                          !(d.flags & PWF_FLAG_PLAIN);
+    const bool want = (d.flags & PWF_FLAG_PERSISTENT) != 0;
+    if ((d.flags & PWF_FLAG_PERSISTENT) && !eligible) {
       pwf_plan_destroy(p);
-      return PWF_ERR_CUDA;
+      return PWF_ERR_UNSUPPORTED;
+    }
+    if (eligible && want) {
+      int per_sm = 0;
+      if (p->kcol->persist_prep(d.batch) != cudaSuccess || p->kcol->persist_occupancy(d.batch, &per_sm) != cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        if (d.flags & PWF_FLAG_PERSISTENT) {
+          pwf_plan_destroy(p);
+          return PWF_ERR_UNSUPPORTED;
+        }
+      } else {
+        p->persist_grid = device_sms();
+        if ((r = dalloc(p, &p->gpart, (size_t)p->persist_grid * d.batch * NACC)) || (r = dalloc(p, &p->bar, 2)) ||
+            (r = dalloc(p, &p->phases, PERSIST_MAX_PHASES))) {
+          pwf_plan_destroy(p);
+          return r;
+        }
+        p->persist = true;
+      }
     }
   }
   if (!(d.flags & PWF_FLAG_NO_TUNE) && (r = tune_columns(p)) != PWF_OK) {
@@ -1164,9 +1230,6 @@ pwf_status pwf_plan_destroy(pwf_plan* p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
   if (p->solve_state) pwf_state_destroy(p->solve_state);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-  for (cudaEvent_t e : p->ovl_ev) cudaEventDestroy(e);
-  for (cudaStream_t s : p->ovl_stream)
-    if (s) cudaStreamDestroy(s);
   for (void* q : p->allocs) cudaFree(q);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   delete p;
@@ -1456,6 +1519,13 @@ pwf_status pwf_state_read(pwf_plan* p, const pwf_state* s, double* loss_host, do
   PWF_CUDA(p, cudaStreamSynchronize(p->stream));
   DevIter it;
   PWF_CUDA(p, cudaMemcpy(&it, s->it, sizeof(DevIter), cudaMemcpyDeviceToHost));
+  int ks = 0;
+  PWF_CUDA(p, cudaMemcpy(&ks, p->kstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  if (ks != 0) {
+    cudaMemset(p->kstatus, 0, sizeof(int));
+    return fail(p, PWF_ERR_TIMEOUT, "a bounded wait for a tile copy ran out");
+  }
+  if (it.status == PWF_ERR_TIMEOUT) return fail(p, PWF_ERR_TIMEOUT, "a grid barrier of the persistent solver ran out");
   if (it.nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss");
   return PWF_OK;
 }
@@ -1473,7 +1543,7 @@ pwf_status pwf_solve_joint(pwf_plan* p, const float* y, void* t, void* psi, int3
   pwf_status r = check_plan(p);
   if (r) return r;
   if (!(eta_t >= 0.0)) return PWF_ERR_INVALID_ARG;
-  if (!p->modes.empty() || (p->d.flags & (PWF_FLAG_PLAIN | PWF_FLAG_OVERLAP)))
+  if (!p->modes.empty() || (p->d.flags & PWF_FLAG_PLAIN))
     return fail(p, PWF_ERR_UNSUPPORTED, "joint refinement runs the fused single-chain IOTF/coherent path");
   return solve_impl(p, y, t, psi, max_iter, 0.0, iters_host, loss_host, eta_t);
 }
@@ -1502,6 +1572,11 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
     a.psi = P;
     a.out = p->X;
     LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
+    if (p->persist && !joint) {
+      if ((r = persist_solve(p, st, y, (const float2*)t, P, max_iter, corr_tol))) return r;
+      if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
+      return PWF_OK;
+    }
     // capture one fused iteration into a graph (re-captured when the operands change)
     const void* key[4] = {y, t, psi, p->stream};
     if (!p->graph || std::memcmp(key, p->graph_key, sizeof(key)) != 0 || p->graph_tol != corr_tol ||
@@ -1517,10 +1592,6 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
       const long long before = p->launches;
       if (joint) {
         r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol, (float2*)t, eta_t);
-      } else if (!p->ovl_ev.empty()) {
-        // two half-batches in two branches; pass k of the second waits for pass
-        // k of the first, so their column and row passes run side by side
-        r = overlapped_iteration(p, st, y, (const float2*)t, P, corr_tol);
       } else {
         r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
       }
@@ -1713,6 +1784,14 @@ pwf_status pwf_solve_host(pwf_plan* p, const float* y_host, const void* t_host, 
 
 long long pwf_plan_launch_count(const pwf_plan* p) { return p ? p->launches : -1; }
 
+pwf_status pwf_plan_set_wait_limit(pwf_plan* p, int64_t cycles) {
+  if (!p || cycles < 0) return PWF_ERR_INVALID_ARG;
+  p->wait_cap = (long long)cycles;
+  return PWF_OK;
+}
+
+int32_t pwf_plan_uses_persistent(const pwf_plan* p) { return p ? (p->persist ? 1 : 0) : -1; }
+
 int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
   if (!p || pass < 0 || pass >= NUM_COL_OPS) return -1;
   return p->kcol->ncolv[pass];
@@ -1733,9 +1812,10 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   char tmp[2048];
   size_t o = 0;
   auto shape = [&](const ColVariant& v) {
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   };
-  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d", p->d.ny, p->d.nx, p->d.batch);
+  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d solver=%s", p->d.ny, p->d.nx, p->d.batch,
+                     p->persist ? "persistent" : "graph");
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {
     o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);
@@ -2082,7 +2162,7 @@ pwf_status pwf_state_save(pwf_plan* p, const pwf_state* s, void* host_buf, size_
   h.B = s->B;
   h.ny = s->ny;
   h.nx = s->nx;
-  h.version = 1;
+  h.version = 2;
   std::memcpy(b, &h, sizeof(h));
   b += 64;
   const size_t nf = (size_t)s->B * s->ny * s->nx * sizeof(float2);
@@ -2109,7 +2189,7 @@ pwf_status pwf_state_load(pwf_plan* p, pwf_state* s, const void* host_buf, size_
   const char* b = static_cast<const char*>(host_buf);
   CkptHeader h;
   std::memcpy(&h, b, sizeof(h));
-  if (std::memcmp(h.magic, "PWFSTAT1", 8) != 0 || h.version != 1 || h.B != s->B || h.ny != s->ny || h.nx != s->nx)
+  if (std::memcmp(h.magic, "PWFSTAT1", 8) != 0 || h.version != 2 || h.B != s->B || h.ny != s->ny || h.nx != s->nx)
     return PWF_ERR_STATE;
   b += 64;
   const size_t nf = (size_t)s->B * s->ny * s->nx * sizeof(float2);

@@ -337,6 +337,28 @@ struct ColLayout {
 // ---------------------------------------------------------------------------
 // Stockham stages
 // ---------------------------------------------------------------------------
+// Twiddle W^(r k) of a radix-R stage (table entry (r - 1) NS + k of the stage
+// at offset OFF). Every entry is read from the table, which holds all R - 1
+// powers rounded once from double precision. Forming the odd powers as
+// products of two power-of-two entries instead saves table reads but doubles
+// their rounding error, and that error is the same in every row and column of
+// a field: on smooth objects it adds up coherently in the lowest spatial
+// frequencies of the modelled intensity. PWF_TWIDDLE_PRODUCTS restores the
+// products (for measurement).
+template <int R>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int off, int ns, int k, int r,
+                                          const float2 (&w)[R]) {
+#ifdef PWF_TWIDDLE_PRODUCTS
+  if ((r & (r - 1)) != 0 && R != 3) {
+    const int hi = r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : 2;
+    return cmul(w[hi], w[r - hi]);
+  }
+#else
+  (void)w;
+#endif
+  return __ldg(&tw[off + (r - 1) * ns + k]);
+}
+
 // Runs stages [K, S) of the length-N transform with direction DIR on the slot
 // registers v. Before the call, v holds the inputs of stage K in slot order of
 // its radix (for K = 0, the transform's input). After it, v holds the outputs
@@ -369,18 +391,11 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
     for (int i = 0; i < NB; i++) {
       const int b = t + i * TPF;
       const int k = b % NS;
-      // W^(r k) for r = 1..R-1: the powers r = 1, 2, 4, 8 come from the table,
-      // the others are products of two of them (one rounding each)
+      // W^(r k) for r = 1..R-1, each read from the table (computed in double
+      // precision, rounded once)
       float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; r++) {
-        if ((r & (r - 1)) == 0 || R == 3) {
-          w[r] = __ldg(&tw[OFF + (r - 1) * NS + k]);
-        } else {
-          const int hi = r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : 2;
-          w[r] = cmul(w[hi], w[r - hi]);
-        }
-      }
+      for (int r = 1; r < R; r++) w[r] = twiddle<R>(tw, OFF, NS, k, r, w);
 #pragma unroll
       for (int r = 1; r < R; r++) v[i * R + r] = cmul(v[i * R + r], w[r]);
       dft<R, DIR>(&v[i * R]);
@@ -422,10 +437,21 @@ struct ColPairLayout {
   }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
+// The same without the padding rows: the dense [N][C] tile a TMA box copy
+// writes (the first stage's stride-R writes then meet twice the bank
+// conflicts of the padded layout; the other accesses stay conflict-free).
+template <int C>
+struct ColPairLayoutDense {
+  float2* base;  // offset by the even column c
+  __device__ __forceinline__ float4& operator[](int p) const { return *reinterpret_cast<float4*>(base + p * C); }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
 
-template <int N, int DIR, int K, int C>
+// L: a layout whose operator[] gives the float4 of element p of the pair
+// (ColPairLayout, or the unpadded ColPairLayoutDense of TMA-filled tiles).
+template <int N, int DIR, int K, class L>
 __device__ __forceinline__ void fft_stages2(float2 (&v)[ept_for(N)], float2 (&u)[ept_for(N)],
-                                            const ColPairLayout<C>& sm, int t, const float2* __restrict__ tw) {
+                                            const L& sm, int t, const float2* __restrict__ tw) {
   constexpr Sched S = sched_for(N);
   constexpr int EPT = ept_for(N);
   constexpr int TPF = tpf_for(N);
@@ -453,14 +479,7 @@ __device__ __forceinline__ void fft_stages2(float2 (&v)[ept_for(N)], float2 (&u)
       const int k = b % NS;
       float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; r++) {
-        if ((r & (r - 1)) == 0 || R == 3) {
-          w[r] = __ldg(&tw[OFF + (r - 1) * NS + k]);
-        } else {
-          const int hi = r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : 2;
-          w[r] = cmul(w[hi], w[r - hi]);
-        }
-      }
+      for (int r = 1; r < R; r++) w[r] = twiddle<R>(tw, OFF, NS, k, r, w);
 #pragma unroll
       for (int r = 1; r < R; r++) {
         v[i * R + r] = cmul(v[i * R + r], w[r]);
@@ -491,14 +510,14 @@ __device__ __forceinline__ void fft_stages2(float2 (&v)[ept_for(N)], float2 (&u)
       }
     }
     sm.sync();
-    fft_stages2<N, DIR, K + 1, C>(v, u, sm, t, tw);
+    fft_stages2<N, DIR, K + 1, L>(v, u, sm, t, tw);
   }
 }
 
-template <int N, int DIR, int C>
+template <int N, int DIR, class L>
 __device__ __forceinline__ void fft_run2(float2 (&v)[ept_for(N)], float2 (&u)[ept_for(N)],
-                                         const ColPairLayout<C>& sm, int t, const float2* __restrict__ tw) {
-  fft_stages2<N, DIR, 0, C>(v, u, sm, t, tw);
+                                         const L& sm, int t, const float2* __restrict__ tw) {
+  fft_stages2<N, DIR, 0, L>(v, u, sm, t, tw);
 }
 
 // radix of the slot layout at the start / end of a transform

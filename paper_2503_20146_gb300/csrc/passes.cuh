@@ -12,6 +12,8 @@
 // Every pass is in place on its primary buffer: a CTA owns whole rows (row
 // pass) or whole columns (column pass) of the field it transforms.
 #pragma once
+#include <cuda.h>
+
 #include "fft.cuh"
 
 namespace pwf {
@@ -65,7 +67,7 @@ struct PassArgs {
   const float* iy;
   const float* u2x;        // squared frequency, cycles/pixel
   const float* u2y;
-  const float* ex;         // STF exponents pi gamma u^2 xcoh^2
+  const float* ex;         // STF - 1 along x (and y): exp(-pi gamma u^2 xcoh^2) - 1, Eq. (14)
   const float* ey;
   const float2* yhat;      // 2-D spectrum of y
   float scale;             // 1/(nx ny), the inverse-transform normalisation
@@ -81,6 +83,8 @@ struct PassArgs {
   int mode_mx, mode_my;
   float mode_w;
   int accumulate;
+  int* kstatus;            // device word set to PWF_ERR_TIMEOUT (7) when a bounded wait runs out
+  CUtensorMap tmap;        // TMA map of `in` (filled by the launcher of a TMA-staged shape)
 };
 
 enum RowOp : int {
@@ -148,6 +152,27 @@ __device__ __forceinline__ float2 cexpf2(float2 z) {
   return make_float2(m * c, m * s);
 }
 
+// exp(z) to about one ulp, for the object field x = exp(psi) that enters the
+// forward model and the gradient. The phase is reduced to [-pi, pi] by the same
+// two-constant Cody-Waite step as cexpf2 (so that the library sincosf stays on
+// its short-argument path), and the library sincosf and expf give the rest.
+// The hardware approximations of cexpf2 are 2^-21.4 absolute on the phase and
+// a few ulp on the modulus; both errors are smooth functions of psi, so over a
+// smooth object they add up coherently in the lowest spatial frequencies of
+// the modelled intensity, where the preconditioner of Eq. (11) amplifies them
+// by up to N^2. cexpf2 stays where its errors cancel: the correlation sums.
+__device__ __forceinline__ float2 cexpf_acc(float2 z) {
+  constexpr float kInv2Pi = 0.159154943091895336f;
+  constexpr float kC1 = 6.28318548202514648f;
+  constexpr float kC2 = -1.74845553146951715e-07f;
+  const float k = rintf(z.y * kInv2Pi);
+  const float r = fmaf(-k, kC2, fmaf(-k, kC1, z.y));
+  float s, c;
+  sincosf(r, &s, &c);
+  const float m = expf(z.x);
+  return make_float2(m * c, m * s);
+}
+
 // Block-wide sum of NR thread partials into acc[proj*NACC + first + k] (float64).
 template <int NR>
 __device__ __forceinline__ void block_reduce_add(const float (&part)[5], double* acc, int first,
@@ -175,24 +200,21 @@ __device__ __forceinline__ void block_reduce_add(const float (&part)[5], double*
 // ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
-template <int N, int OP>
-__global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_kernel(const PassArgs a) {
-  constexpr int EPT = ept_for(N), TPF = tpf_for(N), ROWS = rows_for(N);
+// One row of a row pass: thread t of the TPF threads that own row `row`
+// (global row index over the batch) with the row's shared-memory layout sm.
+// The thread's partial sums of the pass's reductions are added to part; the
+// caller reduces them. Every thread of the row must call this.
+template <int N, int OP, class L>
+__device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t, const L& sm, float (&part)[5]) {
+  constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();  // slot radix of real-space data
   constexpr int RK = last_radix<N, FWD>();   // slot radix of spectra
   using T = RowT<OP>;
-  extern __shared__ float2 smem[];
-
-  const int tid = threadIdx.x;
-  const int rr = tid / TPF, t = tid - rr * TPF;
-  const long long row = (long long)blockIdx.x * ROWS + rr + (long long)a.proj0 * a.ny;
   const int proj = (int)(row / a.ny);
   const int yrow = (int)(row - (long long)proj * a.ny);
-  if (a.active != nullptr && a.active[proj] == 0) return;  // uniform per CTA (ny % ROWS == 0)
+  (void)proj;
   const size_t rb = (size_t)row * N;
-  const RowLayout<TPF, ROWS * TPF> sm{smem + rr * row_smem_len(N), 1 + rr};
   float2 v[EPT];
-  float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
   // Pull this row's side inputs into L2 while the first transform runs.
   if (t == 0) {
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
     fft_run<N, INV>(v, sm, t, a.tw_inv);
   } else if constexpr (OP == ROW_EXP_FFT) {
 #pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = cexpf2(a.psi[rb + slot_index<N, RS>(t, j)]);
+    for (int j = 0; j < EPT; j++) v[j] = cexpf_acc(a.psi[rb + slot_index<N, RS>(t, j)]);
   } else if constexpr (OP == ROW_REAL_FFT) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = make_float2(a.y[rb + slot_index<N, RS>(t, j)], 0.f);
@@ -285,7 +307,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int x = slot_index<N, RS>(t, j);
-      const float2 xx = cexpf2(a.psi[rb + x]);
+      const float2 xx = cexpf_acc(a.psi[rb + x]);
       a.g_out[rb + x] = cscale(cmulc(v[j], xx), s);
     }
   } else if constexpr (OP == ROW_GRAD_PACK) {
@@ -295,7 +317,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int x = slot_index<N, RS>(t, j);
-      const float2 g = cscale(cmulc(v[j], cexpf2(a.psi[rb + x])), s);
+      const float2 g = cscale(cmulc(v[j], cexpf_acc(a.psi[rb + x])), s);
       a.reg[rb + x] = g.x;
       v[j] = make_float2(g.y, 0.f);
     }
@@ -313,7 +335,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
       const float2 pn = make_float2(fmaf(beta, f.x - fp.x, f.x), fmaf(beta, f.y - fp.y, f.y));
       a.phi[rb + x] = f;
       a.psi_out[rb + x] = pn;
-      const float2 xo = cexpf2(p), xn = cexpf2(pn);
+      const float2 xo = cexpf2(p), xn = cexpf_acc(pn);
       const float2 c = cmulc(xn, xo);
       part[0] += c.x;
       part[1] += c.y;
@@ -355,7 +377,8 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
     float2* b2;
     asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
     asm volatile("mov.b64 %0, %1;" : "=l"(b2) : "l"(sm.base));
-    const RowLayout<TPF, ROWS * TPF> sm2{b2, sm.bar};
+    L sm2 = sm;
+    sm2.base = b2;
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const float2 p = a.psi[rb + slot_index<N, RS>(t2, j)];
@@ -369,6 +392,22 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t, j)] = v[j];
   }
+}
+
+template <int N, int OP>
+__global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_kernel(const PassArgs a) {
+  constexpr int TPF = tpf_for(N), ROWS = rows_for(N);
+  using T = RowT<OP>;
+  extern __shared__ float2 smem[];
+
+  const int tid = threadIdx.x;
+  const int rr = tid / TPF, t = tid - rr * TPF;
+  const long long row = (long long)blockIdx.x * ROWS + rr + (long long)a.proj0 * a.ny;
+  const int proj = (int)(row / a.ny);
+  if (a.active != nullptr && a.active[proj] == 0) return;  // uniform per CTA (ny % ROWS == 0)
+  const RowLayout<TPF, ROWS * TPF> sm{smem + rr * row_smem_len(N), 1 + rr};
+  float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  row_body<N, OP>(a, row, t, sm, part);
 
   // ---- reductions ----
   if constexpr (T::nred == 1) {
@@ -437,12 +476,15 @@ __device__ __forceinline__ void col_tile_filter(const PassArgs& a, const L& sm, 
     part[0] *= a.scale;
   } else if constexpr (OP == COL_PRECOND_REG) {
     fft_run<N, FWD>(s2, sm, t, a.tw_fwd);
-    const float exv = __ldg(&a.ex[col]);
+    const float gx = __ldg(&a.ex[col]);
     const float u2 = __ldg(&a.u2x[col]);
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int ky = slot_index<N, RK>(t, j);
-      const float g2 = -expm1f(-(exv + __ldg(&a.ey[ky])));  // Gamma^2 = 1 - STF
+      // Gamma^2 = 1 - STF = 1 - (1 + gx)(1 + gy), gx, gy = STF - 1 of each axis
+      // (Eqs. (14)-(15)): both are <= 0, so the three terms do not cancel
+      const float gy = __ldg(&a.ey[ky]);
+      const float g2 = -fmaf(gx, gy, gx + gy);
       const float r2 = u2 + __ldg(&a.u2y[ky]);
       const float pinv = a.no_precond ? 1.0f : (r2 > 0.f ? 1.0f / r2 : 0.0f);
       // Z = Gamma^2 H + i P^-1 S
@@ -451,25 +493,20 @@ __device__ __forceinline__ void col_tile_filter(const PassArgs& a, const L& sm, 
   }
 }
 
-template <int N, int OP, int C>
-__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
-    col_kernel(const PassArgs a) {
+// One column of a column pass: thread t of the TPF threads that own column
+// `col` of projection `proj`, reading the first stage's inputs straight from
+// global memory, with the column's shared-memory layout sm (interleaved with
+// other columns or one column alone). Partial sums go to part.
+template <int N, int OP, class L>
+__device__ __forceinline__ void col_body(const PassArgs& a, int proj, int col, int t, const L& sm,
+                                         float (&part)[5]) {
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
-  extern __shared__ float2 smem[];
-
-  const int tid = threadIdx.x;
-  const int c = tid % C, t = tid / C;
-  const int proj = blockIdx.y + a.proj0;
-  const int col = blockIdx.x * C + c;
-  if (a.active != nullptr && a.active[proj] == 0) return;
   const size_t base = (size_t)proj * a.ny * a.nx + col;
   const size_t ld = (size_t)a.nx;
-  const ColLayout<C> sm{smem + c};
   float2 v[EPT];
   float2 s2[(OP == COL_PRECOND_REG) ? EPT : 1];
-  float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
   if constexpr (OP == COL_IFFT) {
 #pragma unroll
@@ -492,6 +529,20 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_t
   fft_run<N, INV>(v, sm, t, a.tw_inv);
 #pragma unroll
   for (int j = 0; j < EPT; j++) a.out[base + (size_t)slot_index<N, RS>(t, j) * ld] = v[j];
+}
+
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
+    col_kernel(const PassArgs a) {
+  extern __shared__ float2 smem[];
+  const int tid = threadIdx.x;
+  const int c = tid % C, t = tid / C;
+  const int proj = blockIdx.y + a.proj0;
+  const int col = blockIdx.x * C + c;
+  if (a.active != nullptr && a.active[proj] == 0) return;
+  const ColLayout<C> sm{smem + c};
+  float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  col_body<N, OP>(a, proj, col, t, sm, part);
   if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, smem);
 }
 
@@ -739,7 +790,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
         v[j] = make_float2(q.x, q.y);
         u[j] = make_float2(q.z, q.w);
       }
-      fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
+      fft_run2<N, FWD>(v, u, sm, t, a.tw_fwd);
       if constexpr (OP != COL_FFT) col_pair_filter<N, OP, ColPairLayout<C>>(a, t, col, base, v, u, part);
     }
     if constexpr (OP == COL_FFT) {
@@ -748,7 +799,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
         *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RK>(t, j) * ld) =
             make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
     } else {
-      fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
+      fft_run2<N, INV>(v, u, sm, t, a.tw_inv);
 #pragma unroll
       for (int j = 0; j < EPT; j++)
         *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RS>(t, j) * ld) =
@@ -759,6 +810,155 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
   }
   cp_async_wait<0>();
 }
+
+// ---------------------------------------------------------------------------
+// TMA-staged pair kernel
+// ---------------------------------------------------------------------------
+// As col_kernel_pipe2 with one buffer, but the tile arrives by tensor-memory
+// access: one thread issues cp.async.bulk.tensor copies of boxes of C columns
+// x min(N, 256) rows into a dense [N][C] tile and arms an mbarrier with the
+// tile's byte count; the copy engine completes the barrier. No thread spends
+// instructions on address generation or copy chunks, and the other CTA on the
+// SM overlaps the copy. The wait is bounded: if the barrier has not completed
+// after kTmaWaitCycles, the kernel records PWF_ERR_TIMEOUT in *a.kstatus,
+// waits once more (bounded) for the copy in flight and returns.
+constexpr long long kTmaWaitCycles = 1ll << 31;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// shared writes of the generic proxy before a TMA write of the same bytes
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_addr(dst)), "l"(tm), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z) : "memory");
+}
+// thread 0 polls with a cycle bound; returns false (for every thread) if it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* kstatus, int* s_flag) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+      if (clock64() - t0 > kTmaWaitCycles) {
+        ok = 0;
+        break;
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  if (*s_flag) {
+    while (!mbar_try_wait(bar, parity)) {
+    }  // completed: returns at once, and makes the tile visible to this thread
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    if (kstatus) atomicExch(kstatus, 7 /* PWF_ERR_TIMEOUT */);
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity) && clock64() - t0 < kTmaWaitCycles) {
+    }
+  }
+  __syncthreads();
+  return false;
+}
+__host__ __device__ constexpr int tma_box_rows(int n) { return n < 256 ? n : 256; }
+__host__ __device__ constexpr size_t tma_smem_bytes(int n, int c) { return (size_t)n * c * sizeof(float2) + 1024; }
+
+template <int N, int OP, int C>
+__global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_tma2(const __grid_constant__ PassArgs a, int nproj) {
+  constexpr int EPT = ept_for(N);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  constexpr int BOX = tma_box_rows(N);
+  constexpr unsigned TILE_BYTES = (unsigned)(N * C * sizeof(float2));
+  static_assert(N % BOX == 0, "tile rows must be whole boxes");
+  static_assert(OP != COL_PRECOND_REG, "single-input passes only");
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  __shared__ int s_flag;
+  // TMA destinations on a 1024-byte boundary
+  float2* tile = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+  const int tid = threadIdx.x;
+  const int c2 = tid % (C / 2), t = tid / (C / 2);
+  const int tiles_per_proj = a.nx / C;
+  const int ntiles = nproj * tiles_per_proj;
+  const size_t ld = (size_t)a.nx;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned parity = 0;
+  for (int tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
+    const int proj = a.proj0 + tile_i / tiles_per_proj;
+    const int col0 = (tile_i % tiles_per_proj) * C;
+    if (a.active != nullptr && a.active[proj] == 0) continue;  // uniform per CTA
+    if (tid == 0) {
+      fence_proxy_async_shared();  // the previous tile's exchanges precede the copy
+      mbar_arrive_expect_tx(&bar, TILE_BYTES);
+#pragma unroll
+      for (int k = 0; k < N / BOX; k++) tma_load_3d(tile + k * BOX * C, &a.tmap, &bar, 2 * col0, k * BOX, proj);
+    }
+    if (!mbar_wait_bounded(&bar, parity, a.kstatus, &s_flag)) return;
+    parity ^= 1u;
+
+    const size_t base = (size_t)proj * a.ny * a.nx + col0 + 2 * c2;
+    const int col = col0 + 2 * c2;
+    const ColPairLayoutDense<C> sm{tile + 2 * c2};
+    float2 v[EPT], u[EPT];
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if constexpr (OP == COL_IFFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) {
+        const float4 q = sm[slot_index<N, RK>(t, j)];
+        v[j] = make_float2(q.x * a.scale, q.y * a.scale);
+        u[j] = make_float2(q.z * a.scale, q.w * a.scale);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) {
+        const float4 q = sm[slot_index<N, RS>(t, j)];
+        v[j] = make_float2(q.x, q.y);
+        u[j] = make_float2(q.z, q.w);
+      }
+      fft_run2<N, FWD>(v, u, sm, t, a.tw_fwd);
+      if constexpr (OP != COL_FFT) col_pair_filter<N, OP, ColPairLayoutDense<C>>(a, t, col, base, v, u, part);
+    }
+    if constexpr (OP == COL_FFT) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++)
+        *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RK>(t, j) * ld) =
+            make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
+    } else {
+      fft_run2<N, INV>(v, u, sm, t, a.tw_inv);
+#pragma unroll
+      for (int j = 0; j < EPT; j++)
+        *reinterpret_cast<float4*>(a.out + base + (size_t)slot_index<N, RS>(t, j) * ld) =
+            make_float4(v[j].x, v[j].y, u[j].x, u[j].y);
+    }
+    if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, tile);
+    __syncthreads();  // every thread is done with the tile before the next copy
+  }
+}
+
+// The TMA map of a batch of complex64 fields [B][ny][nx] seen as float32
+// [B][ny][2 nx]: box = 2C floats (C columns) x min(ny, 256) rows x 1 field.
+// Encoded on the host through the driver entry point (no libcuda link).
+bool encode_field_tmap(CUtensorMap* m, const void* base, int B, int ny, int nx, int C);
 
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
@@ -955,7 +1155,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
       v[j] = cmul(a.in[o + sh0], cmul(qa, qy));
       u[j] = cmul(a.in[o + sh1], cmul(qb, qy));
     }
-    fft_run2<N, INV, C>(v, u, sm, t, a.tw_inv);
+    fft_run2<N, INV>(v, u, sm, t, a.tw_inv);
 #pragma unroll
     for (int j = 0; j < EPT; j++)
       *reinterpret_cast<float4*>(a.out + pb + col + (size_t)slot_index<N, RS>(t, j) * ld) =
@@ -967,7 +1167,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
       v[j] = a.in[o + sh0];
       u[j] = a.in[o + sh1];
     }
-    fft_run2<N, FWD, C>(v, u, sm, t, a.tw_fwd);
+    fft_run2<N, FWD>(v, u, sm, t, a.tw_fwd);
     // Q1 at the input columns (the mode's own frame), weight folded in
     const float ws = a.scale * a.mode_w;
     const float2 qa = cscale(__ldg(&a.qx[sh0]), ws), qb = cscale(__ldg(&a.qx[sh1]), ws);
@@ -1025,7 +1225,15 @@ template <int N, int OP, int C, int PIPE>
 struct ColShape {
   static int resident;  // CTAs per SM of the persistent kernels (set by prep)
   static cudaError_t prep() {
-    if constexpr (PIPE == 3 || PIPE == 4) {
+    if constexpr (PIPE == 5) {
+      constexpr size_t SM = tma_smem_bytes(N, C);
+      cudaError_t e = cudaFuncSetAttribute(col_kernel_tma2<N, OP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+      if (e != cudaSuccess) return e;
+      int r = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_tma2<N, OP, C>, col2_threads(N, C), SM);
+      resident = r > 0 ? r : 1;
+      return e;
+    } else if constexpr (PIPE == 3 || PIPE == 4) {
       constexpr int NB = PIPE == 3 ? 2 : 1;
       constexpr size_t SM = NB * col_smem_bytes(N, C);
       cudaError_t e = cudaFuncSetAttribute(col_kernel_pipe2<N, OP, C, NB>,
@@ -1063,7 +1271,11 @@ struct ColShape {
       const long long ntiles = (long long)nproj * (a.nx / C);
       const long long slots = (long long)device_sms() * resident;
       const int grid = (int)(ntiles < slots ? ntiles : slots);
-      if constexpr (PIPE == 3)
+      if constexpr (PIPE == 5) {
+        PassArgs b = a;
+        if (!encode_field_tmap(&b.tmap, a.in, a.proj0 + nproj, a.ny, a.nx, C)) return cudaErrorInvalidValue;
+        col_kernel_tma2<N, OP, C><<<grid, col2_threads(N, C), tma_smem_bytes(N, C), s>>>(b, nproj);
+      } else if constexpr (PIPE == 3)
         col_kernel_pipe2<N, OP, C, 2><<<grid, col2_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
       else if constexpr (PIPE == 4)
         col_kernel_pipe2<N, OP, C, 1><<<grid, col2_threads(N, C), col_smem_bytes(N, C), s>>>(a, nproj);
@@ -1081,13 +1293,18 @@ struct ColShape {
 template <int N, int OP, int C, int PIPE>
 int ColShape<N, OP, C, PIPE>::resident = 1;
 
+struct PersistArgs;  // persist.cuh
+using PersistFn = cudaError_t (*)(const PersistArgs&, int grid, cudaStream_t);
+using PersistPrepFn = cudaError_t (*)(int batch);
+using PersistOccFn = cudaError_t (*)(int batch, int* per_sm);
+
 struct ColVariant {
   PassFn launch;
   PrepFn prep;
   int C;
   int pipe;
 };
-constexpr int MAX_COL_VARIANTS = 12;
+constexpr int MAX_COL_VARIANTS = 14;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
@@ -1098,6 +1315,10 @@ struct LengthKernels {
   int ncolv[NUM_COL_OPS];
   PassFn colmode[2];
   PrepFn colmode_prep[2];
+  // persistent solver (square grids of the sizes persist_size accepts; null otherwise)
+  PersistFn persist;
+  PersistPrepFn persist_prep;
+  PersistOccFn persist_occupancy;
 };
 
 // the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
@@ -1129,10 +1350,12 @@ cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
 // a shape is offered when its CTA has 16..512 threads and its buffers fit
 template <int N, int OP, int C, int PIPE>
 constexpr bool col_shape_ok() {
-  constexpr bool pair = PIPE == 3 || PIPE == 4;
+  constexpr bool pair = PIPE == 3 || PIPE == 4 || PIPE == 5;
   constexpr int th = pair ? col2_threads(N, C) : col_threads(N, C);
-  constexpr size_t sm =
-      PIPE == 2 ? colt_smem_bytes(N, C) : (PIPE == 1 || PIPE == 3) ? colp_smem_bytes(N, C) : col_smem_bytes(N, C);
+  constexpr size_t sm = PIPE == 5   ? tma_smem_bytes(N, C)
+                       : PIPE == 2 ? colt_smem_bytes(N, C)
+                       : (PIPE == 1 || PIPE == 3) ? colp_smem_bytes(N, C)
+                                                  : col_smem_bytes(N, C);
   return th >= 16 && th <= 512 && sm <= 200 * 1024 && ((PIPE == 0 || PIPE == 2) || (N * C / 2) % th == 0) &&
          (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8)) &&
          (!pair || (OP != COL_PRECOND_REG && C >= 4 && th >= 32 && th <= 256));
@@ -1161,6 +1384,8 @@ void add_col_op(LengthKernels& k) {
   add_col_variant<N, OP, 8, 4>(k);
   add_col_variant<N, OP, 16, 4>(k);
   add_col_variant<N, OP, 4, 4>(k);
+  add_col_variant<N, OP, 8, 5>(k);
+  add_col_variant<N, OP, 4, 5>(k);
 }
 
 template <int N>

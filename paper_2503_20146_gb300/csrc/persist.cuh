@@ -1,0 +1,318 @@
+// End-of-iteration bookkeeping of Algorithm S1 and the persistent solver.
+//
+// Algorithm S1 ends every iteration with the loss of Eq. (2), the correlation
+// of successive fields (the stopping rule of Methods, "Reconstruction
+// procedure") and Nesterov's sequence mu. The graph-replayed solver does that
+// in k_finalize (api.cu); the persistent solver below does it inside its own
+// launch. Both use the helpers of this header.
+//
+// Persistent solver: for square grids of at most 512^2 the whole solve is one
+// cooperative launch of one CTA per SM. Each iteration runs the same passes as
+// the graph (the row and column bodies of passes.cuh), separated by grid
+// barriers. A pass is split into warp-sized items (32 / TPF rows or columns,
+// TPF the threads of one transform), dealt round-robin over the warps of the
+// grid with consecutive items on different SMs, so that even a 128^2 field
+// spreads over the whole GPU; at these sizes every field stays in L2 and the
+// time of a pass is the latency of one item. Reductions go to per-CTA partial
+// sums in shared memory, written out once per iteration and summed by CTA 0
+// in a fixed order (no global atomics). Every barrier waits at most `cap`
+// clock64 cycles; a wait that runs out writes PWF_ERR_TIMEOUT to the status
+// word, and every CTA leaves at its next barrier.
+#pragma once
+#include "../../include/pwf.h"
+#include "passes.cuh"
+
+namespace pwf {
+
+struct DevIter {
+  double mu;       // mu of Algorithm S1 after the last completed iteration
+  float beta;      // (mu_prev - 1)/mu for the next iteration
+  int iter;        // completed iterations
+  int n_active;    // projections still iterating
+  int nonfinite;   // a non-finite loss was seen
+  int status;      // PWF_OK, or PWF_ERR_TIMEOUT once a device-side wait ran out
+};
+
+// Per-projection end of an iteration from its five sums (loss and the three
+// correlation sums): loss, correlation, iteration count and the stopping rule.
+// Returns 1 while the projection keeps iterating.
+__device__ __forceinline__ int finalize_projection(int p, const double* a, int* active, int* iters, double* loss,
+                                                   double* corr, double corr_tol, int& nonfinite) {
+  if (!active[p]) return 0;
+  const double L = a[ACC_LOSS];
+  const double c = sqrt(a[ACC_XR] * a[ACC_XR] + a[ACC_XI] * a[ACC_XI]) / sqrt(a[ACC_XNEW] * a[ACC_XOLD]);
+  loss[p] = L;
+  corr[p] = c;
+  iters[p] += 1;
+  if (!isfinite(L)) nonfinite = 1;
+  if (corr_tol > 0.0 && c > corr_tol) {
+    active[p] = 0;
+    return 0;
+  }
+  return 1;
+}
+
+// Nesterov's sequence mu <- (1 + sqrt(1 + 4 mu^2)) / 2 and the momentum
+// coefficient (mu_prev - 1)/mu of the next iteration, kept in FP64.
+__device__ __forceinline__ void finalize_momentum(DevIter* it, int n_active) {
+  const double mu_prev = it->mu;
+  const double mu = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu_prev * mu_prev));
+  const double mu_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * mu * mu));
+  it->mu = mu;
+  it->beta = (float)((mu - 1.0) / mu_next);
+  it->iter += 1;
+  it->n_active = n_active;
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier with a bounded wait
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// bar[0] counts arrivals, bar[1] is the generation. Returns false once the
+// status word holds an error (this wait ran out, or another CTA's did).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, long long cap) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = ld_volatile_i32(status) == PWF_OK;
+    if (ok) {
+      const unsigned gen = ld_acquire_u32(&bar[1]);
+      __threadfence();
+      if (atomicAdd(&bar[0], 1u) + 1u == gridDim.x) {
+        bar[0] = 0u;
+        st_release_u32(&bar[1], gen + 1u);
+      } else {
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&bar[1]) == gen) {
+          if (clock64() - t0 > cap) {
+            atomicCAS(status, PWF_OK, PWF_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+      ok = ld_volatile_i32(status) == PWF_OK;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// persistent solver
+// ---------------------------------------------------------------------------
+enum PersistKind : int { PK_ROW = 0, PK_COL = 1, PK_FINALIZE = 2 };
+constexpr int PERSIST_THREADS = 512;
+constexpr int PERSIST_MAX_PHASES = 16;
+__host__ __device__ constexpr bool persist_size(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+
+struct PersistPhase {
+  int kind;
+  int op;
+  int flush;   // after this pass, write the CTA's sums of the iteration out
+  PassArgs a;
+};
+
+struct PersistArgs {
+  const PersistPhase* phases;  // device array of nphases
+  int nphases;
+  int B;
+  int max_iter;
+  double corr_tol;
+  double* gpart;               // [gridDim.x][B][NACC] per-CTA partial sums
+  unsigned* bar;               // grid barrier (2 words, zeroed before the launch)
+  long long cap;               // clock64 cycles a barrier may wait
+  int* active;
+  int* iters;
+  double* loss;
+  double* corr;
+  DevIter* it;
+};
+
+__host__ __device__ constexpr size_t persist_smem_bytes(int n, int batch) {
+  return (size_t)(PERSIST_THREADS / 32) * (32 / tpf_for(n)) * row_smem_len(n) * sizeof(float2) +
+         (size_t)batch * NACC * sizeof(double);
+}
+
+// sum of a thread's float partial over the warp, in FP64
+__device__ __forceinline__ double warp_sum(float x) {
+  double s = (double)x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// rows of a row pass: item = 32/TPF consecutive rows (one projection)
+template <int N, int OP>
+__device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc) {
+  constexpr int TPF = tpf_for(N), RPW = 32 / TPF;
+  const int sub = lane / TPF, t = lane - sub * TPF;
+  const RowLayout<TPF, 32> sm{wsm + sub * row_smem_len(N), 0};
+  const long long items = (long long)a.B * a.ny / RPW;
+  for (long long it = gw; it < items; it += GW) {
+    const long long row = it * RPW + sub;
+    const int proj = (int)((it * RPW) / a.ny);
+    if (a.active != nullptr && a.active[proj] == 0) continue;  // uniform per warp
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    row_body<N, OP>(a, row, t, sm, part);
+    if constexpr (RowT<OP>::nred == 1) {
+      const double s = warp_sum(part[0]);
+      if (lane == 0) atomicAdd(&s_acc[proj * NACC + ACC_LOSS], s);
+    } else if constexpr (RowT<OP>::nred == 5) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const double s = warp_sum(part[k]);
+        if (lane == 0) atomicAdd(&s_acc[proj * NACC + ACC_XR + k], s);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// columns of a column pass: item = 32/TPF adjacent columns of one projection;
+// lane = t * CPW + c, so that a warp's loads cover CPW adjacent columns
+template <int N, int OP>
+__device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc) {
+  constexpr int TPF = tpf_for(N), CPW = 32 / TPF;
+  const int c = lane % CPW, t = lane / CPW;
+  const RowLayout<TPF, 32> sm{wsm + c * row_smem_len(N), 0};
+  const long long items = (long long)a.B * a.nx / CPW;
+  for (long long it = gw; it < items; it += GW) {
+    const long long cg = it * CPW;
+    const int proj = (int)(cg / a.nx);
+    const int col = (int)(cg - (long long)proj * a.nx) + c;
+    if (a.active != nullptr && a.active[proj] == 0) continue;
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    col_body<N, OP>(a, proj, col, t, sm, part);
+    if constexpr (OP == COL_RESID_IOTF2) {
+      const double s = warp_sum(part[0]);
+      if (lane == 0) atomicAdd(&s_acc[proj * NACC + ACC_LOSS], s);
+    }
+    __syncwarp();
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void persist_row_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
+                                               double* s_acc) {
+  switch (op) {
+    case ROW_MUL_T: persist_rows<N, ROW_MUL_T>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_INTENSITY: persist_rows<N, ROW_INTENSITY>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_MUL_V: persist_rows<N, ROW_MUL_V>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_COH_RESID: persist_rows<N, ROW_COH_RESID>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_GRAD_PACK: persist_rows<N, ROW_GRAD_PACK>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_NESTEROV_FFT: persist_rows<N, ROW_NESTEROV_FFT>(a, gw, GW, lane, wsm, s_acc); break;
+    default: break;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void persist_col_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
+                                               double* s_acc) {
+  switch (op) {
+    case COL_Q: persist_cols<N, COL_Q>(a, gw, GW, lane, wsm, s_acc); break;
+    case COL_RESID_IOTF2: persist_cols<N, COL_RESID_IOTF2>(a, gw, GW, lane, wsm, s_acc); break;
+    case COL_PRECOND_REG: persist_cols<N, COL_PRECOND_REG>(a, gw, GW, lane, wsm, s_acc); break;
+    default: break;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(PERSIST_THREADS, 1) persist_kernel(const PersistArgs pa) {
+  constexpr int W = PERSIST_THREADS / 32, RPW = 32 / tpf_for(N);
+  extern __shared__ float2 smem[];
+  double* s_acc = reinterpret_cast<double*>(smem + W * RPW * row_smem_len(N));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = warp * gridDim.x + blockIdx.x;  // consecutive items on different SMs
+  const int GW = gridDim.x * W;
+  float2* wsm = smem + warp * RPW * row_smem_len(N);
+  int* status = &pa.it->status;
+  for (int i = threadIdx.x; i < pa.B * NACC; i += blockDim.x) s_acc[i] = 0.0;
+
+  for (int iter = 0; iter < pa.max_iter; iter++) {
+    for (int ph = 0; ph < pa.nphases; ph++) {
+      const PersistPhase& P = pa.phases[ph];
+      const int kind = P.kind, op = P.op;
+      if (kind == PK_ROW) {
+        persist_row_op<N>(op, P.a, gw, GW, lane, wsm, s_acc);
+      } else if (kind == PK_COL) {
+        persist_col_op<N>(op, P.a, gw, GW, lane, wsm, s_acc);
+      } else if (kind == PK_FINALIZE && blockIdx.x == 0) {
+        __shared__ int s_na, s_nf;
+        if (threadIdx.x == 0) s_na = 0, s_nf = 0;
+        __syncthreads();
+        int na = 0, nf = 0;
+        for (int p = threadIdx.x; p < pa.B; p += blockDim.x) {
+          double sums[NACC] = {};
+          for (int g = 0; g < (int)gridDim.x; g++) {  // fixed order: deterministic
+            const double* q = pa.gpart + ((size_t)g * pa.B + p) * NACC;
+#pragma unroll
+            for (int k = 0; k < 5; k++) sums[k] += q[k];
+          }
+          na += finalize_projection(p, sums, pa.active, pa.iters, pa.loss, pa.corr, pa.corr_tol, nf);
+        }
+        atomicAdd(&s_na, na);
+        if (nf) atomicOr(&s_nf, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          if (s_nf) pa.it->nonfinite = 1;
+          finalize_momentum(pa.it, s_na);
+        }
+      }
+      if (P.flush) {
+        // this CTA's sums of the iteration to its slot (read by CTA 0 after
+        // the barrier); zeroed for the next iteration
+        __syncthreads();
+        double* g = pa.gpart + (size_t)blockIdx.x * pa.B * NACC;
+        for (int i = threadIdx.x; i < pa.B * NACC; i += blockDim.x) {
+          g[i] = s_acc[i];
+          s_acc[i] = 0.0;
+        }
+      }
+      if (!grid_sync(pa.bar, status, pa.cap)) return;
+    }
+    if (pa.corr_tol > 0.0 && ld_volatile_i32(&pa.it->n_active) == 0) break;
+  }
+}
+
+template <int N>
+cudaError_t prep_persist(int batch) {
+  return cudaFuncSetAttribute(persist_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)persist_smem_bytes(N, batch));
+}
+
+template <int N>
+cudaError_t launch_persist(const PersistArgs& pa, int grid, cudaStream_t s) {
+  void* args[] = {const_cast<PersistArgs*>(&pa)};
+  return cudaLaunchCooperativeKernel((const void*)persist_kernel<N>, dim3(grid), dim3(PERSIST_THREADS), args,
+                                     persist_smem_bytes(N, pa.B), s);
+}
+
+template <int N>
+cudaError_t occupancy_persist(int batch, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, persist_kernel<N>, PERSIST_THREADS,
+                                                       persist_smem_bytes(N, batch));
+}
+
+template <int N>
+LengthKernels with_persist(LengthKernels k) {
+  if constexpr (persist_size(N)) {
+    k.persist = launch_persist<N>;
+    k.persist_prep = prep_persist<N>;
+    k.persist_occupancy = occupancy_persist<N>;
+  }
+  return k;
+}
+
+}  // namespace pwf

@@ -21,10 +21,11 @@ FLAG_NO_PRECOND = 0x1
 FLAG_NO_REG = 0x2
 FLAG_PLAIN = 0x4
 FLAG_NO_TUNE = 0x8
-FLAG_OVERLAP = 0x10
+FLAG_PERSISTENT = 0x20
+FLAG_GRAPH = 0x40
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
-          4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE"}
+          4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE", 7: "PWF_ERR_TIMEOUT"}
 
 SIZES = (16, 32, 64, 96, 128, 256, 512, 768, 1024, 1536, 2048)
 
@@ -108,6 +109,8 @@ def load(path: str | None = None):
         "pwf_fbp": ([_P, i32, i32, i32, ctypes.POINTER(f64), f64, f64, _P, _P, ctypes.c_size_t, _P], i32),
         "pwf_calibrate_coherence": ([_P, _P, i32, ctypes.POINTER(f64), ctypes.POINTER(f64)], i32),
         "pwf_diffuser_from_reference": ([_P, _P, f64, _P], i32),
+        "pwf_plan_set_wait_limit": ([_P, ctypes.c_int64], i32),
+        "pwf_plan_uses_persistent": ([_P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +225,15 @@ def pwf_forward_noalloc(desc: "PlanDesc", psi, t, f):
     torch stream."""
     d = _desc_struct(desc)
     _check(load().pwf_forward_noalloc(ctypes.byref(d), _ptr(psi), _ptr(t), _ptr(f)), "pwf_forward_noalloc")
+
+
+def pwf_plan_set_wait_limit(plan, cycles: int):
+    """Longest wait of one grid barrier of the persistent solver (SM cycles)."""
+    _check(load().pwf_plan_set_wait_limit(plan, int(cycles)), "pwf_plan_set_wait_limit", plan)
+
+
+def pwf_plan_uses_persistent(plan) -> int:
+    return int(load().pwf_plan_uses_persistent(plan))
 
 
 def pwf_gradient(plan, psi, t, y, g, loss=None):

@@ -1,5 +1,7 @@
 """Mixed-size batches: plans of different sizes (and coherence models) solved
 together from one graph match each plan solved alone and the oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -62,7 +64,7 @@ def test_group_matches_individual_solves_and_oracle(pwf):
             loss, it = pwf.pwf_group_read(g, k, d.batch)
             assert list(it) == [iters] * d.batch
             # the same class solved on its own, through its own graph
-            with pwf.Plan(d) as alone:
+            with pwf.Plan(dataclasses.replace(d, flags=d.flags | pwf.FLAG_GRAPH)) as alone:
                 p = torch.zeros_like(psis[k])
                 alone.solve(ys[k], ts[k], p, iters)
             assert torch.equal(p, psis[k])
@@ -101,7 +103,7 @@ def test_group_chains_large_classes_and_matches_individual_solves(pwf):
         pwf.pwf_group_solve(g, ys, ts, psis, iters)
         torch.cuda.synchronize()
         for k, d in enumerate(descs):
-            with pwf.Plan(d) as alone:
+            with pwf.Plan(dataclasses.replace(d, flags=d.flags | pwf.FLAG_GRAPH)) as alone:
                 p = torch.zeros_like(psis[k])
                 alone.solve(ys[k], ts[k], p, iters)
             assert torch.equal(p, psis[k]), k

@@ -60,8 +60,9 @@ def test_joint_refinement_matches_oracle(pwf, wname, batch, ny, nx, iters):
 
 
 def test_joint_with_zero_step_equals_solve(pwf):
+    # the joint refinement runs on the graph replay, so pwf_solve is held to it
     g, y, t0 = perturbed_case("blob512_iotf", 3, 64, 64)
-    with plan_for(pwf, g, 3) as plan:
+    with plan_for(pwf, g, 3, pwf.FLAG_GRAPH) as plan:
         yd, t = dev(to_f32(y)), dev(to_c64(t0))
         p1 = torch.zeros((3, 64, 64), dtype=torch.complex64, device="cuda")
         p2 = torch.zeros_like(p1)

@@ -281,28 +281,6 @@ def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
         assert phase_rms(p[b], ref.psi) <= PHASE_TOL
 
 
-@pytest.mark.parametrize("K", [0, 9], ids=["iotf", "k9"])
-def test_overlapped_halves_match_single_chain(pwf, K):
-    """PWF_FLAG_OVERLAP (two half-batch graph branches) gives the same iterates."""
-    w = W2
-    n, batch = 256, 5
-    geom = geometry(w, n, n)
-    psi_true, t = blob_batch(w, batch, n, n)
-    t = to_c64(t)
-    y = to_f32(measurement(psi_true, t.astype(np.complex128), geom, w.photons, w.config))
-    out = []
-    for flags in (0, pwf.FLAG_OVERLAP):
-        d = pwf.PlanDesc(batch, n, n, geom.pixel, geom.wavelength, geom.L1, geom.L2, geom.xcoh, geom.ycoh,
-                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta, flags, K, 2.0)
-        with pwf.Plan(d) as plan:
-            p = torch.zeros((batch, n, n), dtype=torch.complex64, device="cuda")
-            it, loss = plan.solve(dev(y), dev(t), p, 6)
-            assert list(it) == [6] * batch
-            out.append((p.cpu().numpy(), loss))
-    assert rel_l2(out[1][0], out[0][0]) <= 1e-6
-    assert np.max(np.abs(out[1][1] - out[0][1]) / out[0][1]) <= 1e-6
-
-
 # ----------------------------------------------------------------------------
 # every column-pass shape the tuner may choose, forced one at a time
 # ----------------------------------------------------------------------------
