@@ -122,6 +122,19 @@ __global__ void k_state_reset(DevIter* it, int* active, int* iters, double* loss
   }
 }
 
+// The device-side loop of pwf_solve: the last node of every iteration sets the
+// while-condition of the graph that holds the iteration. ctl[0] is the
+// iteration limit and ctl[1] the bodies run so far (both written by the host
+// before the launch); the loop ends after ctl[0] bodies whatever the solver
+// state holds, or earlier once the stopping rule has retired every projection.
+__global__ void k_loop_control(cudaGraphConditionalHandle h, const DevIter* it, int* ctl, double corr_tol) {
+  if (threadIdx.x == 0) {
+    const int done = ++ctl[1];
+    const bool more = done < ctl[0] && (corr_tol <= 0.0 || it->n_active > 0);
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
 __global__ void k_gather_loss(const double* acc, double* loss, int B) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < B) loss[p] = acc[(size_t)p * NACC + ACC_LOSS];
@@ -374,6 +387,7 @@ struct pwf_plan {
   double* acc = nullptr;
   float* maxt2 = nullptr;
   int* kstatus = nullptr;    // set by a kernel whose bounded wait ran out (PWF_ERR_TIMEOUT)
+  int* loop_ctl = nullptr;   // device-side loop: {iteration limit, bodies run} (written per solve)
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
   // solver
@@ -382,6 +396,7 @@ struct pwf_plan {
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   double graph_tol = 0.0;
   double graph_eta_t = -1.0;  // joint diffuser step of the captured graph (< 0: t fixed)
+  bool graph_loop = false;    // the graph holds the whole loop (conditional WHILE node)
   float2* GT = nullptr;       // per-projection diffuser-gradient terms (joint refinement)
   pwf_status sticky = PWF_OK;
   char err[256] = "";
@@ -1082,6 +1097,94 @@ pwf_status tune_columns(pwf_plan* p) {
   return PWF_OK;
 }
 
+// One iteration (enqueued by `body` on the capture stream) as a graph replayed
+// once per iteration from the host.
+template <class F>
+pwf_status capture_step_graph(pwf_plan* p, F&& body) {
+  cudaStream_t user = p->stream;
+  p->stream = p->capture_stream;
+  cudaGraph_t g = nullptr;
+  PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = p->launches;
+  pwf_status r = body();
+  p->graph_kernels = p->launches - before;
+  p->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(p->capture_stream, &g);
+  p->stream = user;
+  if (r) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&p->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaGraphInstantiate");
+  p->graph_loop = false;
+  return PWF_OK;
+}
+
+// The iteration captured into the body of a conditional WHILE node, closed by
+// k_loop_control: one launch runs the loop. PWF_ERR_UNSUPPORTED (with no
+// error left pending) when the driver does not take conditional nodes.
+template <class F>
+pwf_status capture_loop_graph(pwf_plan* p, pwf_state* st, double corr_tol, F&& body) {
+  cudaGraph_t g = nullptr;
+  PWF_CUDA(p, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return PWF_ERR_UNSUPPORTED;
+  }
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return PWF_ERR_UNSUPPORTED;
+  }
+  cudaGraph_t loop_body = np.conditional.phGraph_out[0];
+  cudaStream_t user = p->stream;
+  p->stream = p->capture_stream;
+  cudaError_t ce = cudaStreamBeginCaptureToGraph(p->stream, loop_body, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    p->stream = user;
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return PWF_ERR_UNSUPPORTED;
+  }
+  const long long before = p->launches;
+  pwf_status r = body();
+  if (r == PWF_OK) {
+    k_loop_control<<<1, 32, 0, p->stream>>>(h, st->it, p->loop_ctl, corr_tol);
+    if ((ce = cudaGetLastError()) != cudaSuccess) r = cuda_fail(p, ce, "k_loop_control");
+    p->launches++;
+  }
+  p->graph_kernels = p->launches - before;
+  p->launches = before;
+  cudaGraph_t captured = nullptr;
+  ce = cudaStreamEndCapture(p->capture_stream, &captured);
+  p->stream = user;
+  if (r || ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return r ? r : cuda_fail(p, ce, "cudaStreamEndCapture (loop body)");
+  }
+  ce = cudaGraphInstantiate(&p->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    p->graph = nullptr;
+    return PWF_ERR_UNSUPPORTED;
+  }
+  p->graph_loop = true;
+  return PWF_OK;
+}
+
 bool size_ok(int n) { return kernels_for_length(n) != nullptr; }
 
 pwf_status check_plan(pwf_plan* p) {
@@ -1150,7 +1253,7 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       (r = dalloc(p, &p->X, n)) || (r = dalloc(p, &p->S, n)) || (r = dalloc(p, &p->REG, n)) ||
       (r = dalloc(p, &p->V, n)) || (r = dalloc(p, &p->YH, n)) ||
       (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1)) ||
-      (r = dalloc(p, &p->kstatus, 1)) ||
+      (r = dalloc(p, &p->kstatus, 1)) || (r = dalloc(p, &p->loop_ctl, 2)) ||
       (!p->modes.empty() && ((r = dalloc(p, &p->M, n)) || (r = dalloc(p, &p->ACC, n)) ||
                              (r = dalloc(p, &p->IBUF, n))))) {
     pwf_plan_destroy(p);
@@ -1577,7 +1680,11 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
       if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
       return PWF_OK;
     }
-    // capture one fused iteration into a graph (re-captured when the operands change)
+    // The whole loop as one graph: one fused iteration captured into the body
+    // of a conditional WHILE node whose condition the iteration's last kernel
+    // sets, so that a solve is a single graph launch and the loop runs on the
+    // device (re-captured when the operands change). If the driver refuses
+    // conditional nodes, the single-iteration graph is replayed from the host.
     const void* key[4] = {y, t, psi, p->stream};
     if (!p->graph || std::memcmp(key, p->graph_key, sizeof(key)) != 0 || p->graph_tol != corr_tol ||
         p->graph_eta_t != (joint ? eta_t : -1.0)) {
@@ -1585,41 +1692,32 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
       }
-      cudaStream_t user = p->stream;
-      p->stream = p->capture_stream;
-      cudaGraph_t g = nullptr;
-      PWF_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-      const long long before = p->launches;
-      if (joint) {
-        r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol, (float2*)t, eta_t);
-      } else {
-        r = fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
-      }
-      p->graph_kernels = p->launches - before;
-      p->launches = before;
-      cudaError_t ce = cudaStreamEndCapture(p->capture_stream, &g);
-      p->stream = user;
-      if (r) {
-        if (g) cudaGraphDestroy(g);
-        return r;
-      }
-      if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaStreamEndCapture");
-      ce = cudaGraphInstantiate(&p->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaGraphInstantiate");
+      auto body = [&]() {
+        return joint ? fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol, (float2*)t, eta_t)
+                     : fused_iteration(p, st, y, (const float2*)t, P, true, corr_tol);
+      };
+      if ((r = capture_loop_graph(p, st, corr_tol, body)) == PWF_ERR_UNSUPPORTED) r = capture_step_graph(p, body);
+      if (r) return r;
       std::memcpy(p->graph_key, key, sizeof(key));
       p->graph_tol = corr_tol;
       p->graph_eta_t = joint ? eta_t : -1.0;
     }
-    const int check_every = 16;
-    for (int k = 0; k < max_iter; k++) {
+    if (p->graph_loop) {
+      const int ctl[2] = {max_iter, 0};
+      PWF_CUDA(p, cudaMemcpyAsync(p->loop_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, p->stream));
       PWF_CUDA(p, cudaGraphLaunch(p->graph, p->stream));
-      p->launches += p->graph_kernels;
-      if (corr_tol > 0.0 && (k + 1) % check_every == 0 && k + 1 < max_iter) {
-        DevIter it;
-        PWF_CUDA(p, cudaMemcpyAsync(&it, st->it, sizeof(DevIter), cudaMemcpyDeviceToHost, p->stream));
-        PWF_CUDA(p, cudaStreamSynchronize(p->stream));
-        if (it.n_active == 0) break;
+      p->launches += p->graph_kernels * max_iter;  // at most: the loop may stop early
+    } else {
+      const int check_every = 16;
+      for (int k = 0; k < max_iter; k++) {
+        PWF_CUDA(p, cudaGraphLaunch(p->graph, p->stream));
+        p->launches += p->graph_kernels;
+        if (corr_tol > 0.0 && (k + 1) % check_every == 0 && k + 1 < max_iter) {
+          DevIter it;
+          PWF_CUDA(p, cudaMemcpyAsync(&it, st->it, sizeof(DevIter), cudaMemcpyDeviceToHost, p->stream));
+          PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+          if (it.n_active == 0) break;
+        }
       }
     }
   }
@@ -1814,8 +1912,9 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   auto shape = [&](const ColVariant& v) {
     o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   };
-  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d solver=%s", p->d.ny, p->d.nx, p->d.batch,
-                     p->persist ? "persistent" : "graph");
+  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d solver=%s loop=%s", p->d.ny, p->d.nx,
+                     p->d.batch, p->persist ? "persistent" : "graph",
+                     p->persist ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {
     o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);
@@ -1889,7 +1988,25 @@ struct pwf_group {
   std::vector<const void*> key;
   double tol = 0.0;
   long long graph_kernels = 0;
+  bool loop = false;                 // the graph holds the whole loop (conditional WHILE node)
+  DevIter** d_its = nullptr;         // device array of the classes' iteration records
 };
+
+namespace {
+// The group's device-side loop: ends after ctl[0] bodies (ctl[1] counts them,
+// both written by the host before the launch), or earlier once the stopping
+// rule has retired every projection of every class.
+__global__ void k_group_loop_control(cudaGraphConditionalHandle h, DevIter* const* its, int n, int* ctl,
+                                     double corr_tol) {
+  if (threadIdx.x == 0) {
+    int active = 0;
+    for (int i = 0; i < n; i++) active += its[i]->n_active;
+    const int done = ++ctl[1];
+    const bool more = done < ctl[0] && (corr_tol <= 0.0 || active > 0);
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+}  // namespace
 
 extern "C" {
 
@@ -1928,6 +2045,7 @@ pwf_status pwf_group_create(pwf_plan* const* plans, int32_t n, pwf_group** out) 
 pwf_status pwf_group_destroy(pwf_group* g) {
   if (!g) return PWF_ERR_INVALID_ARG;
   if (g->graph) cudaGraphExecDestroy(g->graph);
+  if (g->d_its) cudaFree(g->d_its);
   for (cudaStream_t s : g->branch) cudaStreamDestroy(s);
   if (g->main) cudaStreamDestroy(g->main);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -1983,6 +2101,32 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
     }
     cudaGraph_t graph = nullptr;
     pwf_plan* p0 = g->plans[0];
+    // the loop on the device: the iteration below is captured into the body of a
+    // conditional WHILE node (falls back to one launch per iteration)
+    std::vector<DevIter*> its;
+    for (pwf_plan* p : g->plans) its.push_back(p->solve_state->it);
+    if (!g->d_its && cudaMalloc(&g->d_its, n * sizeof(DevIter*)) != cudaSuccess) {
+      cudaGetLastError();
+      g->d_its = nullptr;
+    }
+    cudaGraph_t outer = nullptr, loop_body = nullptr;
+    cudaGraphConditionalHandle h{};
+    if (g->d_its && cudaMemcpy(g->d_its, its.data(), n * sizeof(DevIter*), cudaMemcpyHostToDevice) == cudaSuccess &&
+        cudaGraphCreate(&outer, 0) == cudaSuccess &&
+        cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+      cudaGraphNodeParams np{};
+      cudaGraphNode_t node;
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      if (cudaGraphAddNode(&node, outer, nullptr, nullptr, 0, &np) == cudaSuccess) loop_body = np.conditional.phGraph_out[0];
+    }
+    cudaGetLastError();
+    if (!loop_body && outer) {
+      cudaGraphDestroy(outer);
+      outer = nullptr;
+    }
     std::vector<int> chain, side;
     for (int i = 0; i < n; i++)
       ((long long)g->plans[i]->d.batch * g->plans[i]->d.ny * g->plans[i]->d.nx >= kGroupChainPixels ? chain : side)
@@ -1991,7 +2135,10 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
       const pwf_plan_desc &da = g->plans[a]->d, &db = g->plans[b]->d;
       return (long long)da.batch * da.ny * da.nx > (long long)db.batch * db.ny * db.nx;
     });
-    PWF_CUDA(p0, cudaStreamBeginCapture(g->main, cudaStreamCaptureModeThreadLocal));
+    if (loop_body)
+      PWF_CUDA(p0, cudaStreamBeginCaptureToGraph(g->main, loop_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    else
+      PWF_CUDA(p0, cudaStreamBeginCapture(g->main, cudaStreamCaptureModeThreadLocal));
     r = PWF_OK;
     cudaError_t ce = cudaEventRecord(g->ev[0], g->main);
     long long kernels = 0;
@@ -2019,21 +2166,35 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
       if (r != PWF_OK || ce != cudaSuccess) break;
       ce = cudaStreamWaitEvent(g->main, g->ev[1 + i], 0);
     }
+    if (loop_body && r == PWF_OK && ce == cudaSuccess) {
+      k_group_loop_control<<<1, 32, 0, g->main>>>(h, g->d_its, n, p0->loop_ctl, corr_tol);
+      ce = cudaGetLastError();
+      kernels++;
+    }
     cudaError_t ce2 = cudaStreamEndCapture(g->main, &graph);
     for (pwf_plan* p : g->plans) p->stream = user;
     if (r || ce != cudaSuccess || ce2 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
+      if (outer) cudaGraphDestroy(outer);
+      else if (graph) cudaGraphDestroy(graph);
       if (r) return r;
       return cuda_fail(p0, ce != cudaSuccess ? ce : ce2, "group capture");
     }
-    ce = cudaGraphInstantiate(&g->graph, graph, 0);
-    cudaGraphDestroy(graph);
+    ce = cudaGraphInstantiate(&g->graph, outer ? outer : graph, 0);
+    cudaGraphDestroy(outer ? outer : graph);
     if (ce != cudaSuccess) return cuda_fail(p0, ce, "group graph instantiate");
+    g->loop = outer != nullptr;
     g->key = key;
     g->tol = corr_tol;
     g->graph_kernels = kernels;
   }
   pwf_plan* p0 = g->plans[0];
+  if (g->loop) {
+    const int ctl[2] = {max_iter, 0};
+    PWF_CUDA(p0, cudaMemcpyAsync(p0->loop_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, user));
+    PWF_CUDA(p0, cudaGraphLaunch(g->graph, user));
+    p0->launches += g->graph_kernels * max_iter;  // at most: the loop may stop early
+    return PWF_OK;
+  }
   for (int k = 0; k < max_iter; k++) {
     PWF_CUDA(p0, cudaGraphLaunch(g->graph, user));
     p0->launches += g->graph_kernels;

@@ -44,7 +44,9 @@ __device__ __forceinline__ int finalize_projection(int p, const double* a, int* 
   loss[p] = L;
   corr[p] = c;
   iters[p] += 1;
-  if (!isfinite(L)) nonfinite = 1;
+  // the correlation sums run over every element of exp(psi) of both
+  // iterates, so a non-finite iterate shows here even where the loss is finite
+  if (!isfinite(L) || !isfinite(c)) nonfinite = 1;
   if (corr_tol > 0.0 && c > corr_tol) {
     active[p] = 0;
     return 0;

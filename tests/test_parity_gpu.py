@@ -142,6 +142,29 @@ def test_step_matches_solve_and_oracle_losses(pwf):
     assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
 
 
+def test_device_side_loop_counts_and_replays(pwf):
+    # The graph path runs the whole loop on the device (a conditional WHILE
+    # node closed by a loop-control kernel): its iteration count follows the
+    # limit passed to each solve, and the same captured loop replayed with
+    # another limit, or again with the same one, gives the same iterates.
+    w = W2
+    geom, t, y = _solve_case(w, 2, 128, 128)
+    Y, T = dev(y), dev(t)
+    with plan_for(pwf, geom, 2, pwf.FLAG_GRAPH) as plan:
+        out = {}
+        for n in (7, 1, 7, 3):
+            psi = torch.zeros((2, 128, 128), dtype=torch.complex64, device="cuda")
+            iters, loss = plan.solve(Y, T, psi, n)
+            assert list(iters) == [n, n]
+            assert "loop=device" in pwf.pwf_plan_describe(plan.handle)
+            if n in out:
+                assert torch.equal(out[n], psi)
+            out[n] = psi
+    for n in (1, 3, 7):
+        ref = O.solve(y[0].astype(np.float64), t.astype(np.complex128), geom, n)
+        assert phase_rms(out[n].cpu().numpy()[0], ref.psi) <= PHASE_TOL
+
+
 def test_plain_baseline_matches_fused(pwf):
     w = W2
     geom, t, y = _solve_case(w, 2, 128, 128)
@@ -236,6 +259,19 @@ def test_bad_checkpoint_rejected(pwf):
         with pytest.raises(pwf.PWFError) as e:
             pwf.pwf_state_load(other.handle, other.state, blob)
         assert e.value.status == 6
+
+
+def test_nonfinite_iterate_reported_in_the_same_iteration(pwf):
+    # a step size of 1e30 overflows the first update: the loss (taken at the
+    # starting point) is finite, the new iterate is not, and the correlation
+    # sums over exp(psi) flag it at once
+    geom, t, y = _solve_case(W1, 1)
+    g = O.Geometry(**{**geom.__dict__, "eta": 1e30})
+    with plan_for(pwf, g, 1) as plan:
+        psi = torch.zeros((1, 128, 128), dtype=torch.complex64, device="cuda")
+        with pytest.raises(pwf.PWFError) as e:
+            plan.solve(dev(y), dev(t), psi, 1)
+        assert e.value.status == 5
 
 
 def test_nonfinite_measurement_reported(pwf):
