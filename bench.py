@@ -447,10 +447,12 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
 def run_small(P, S, torch, dev, stream, reps=5):
     """The single-projection workloads: 128^2 coherent (50 iterations) and
     512^2 with partial coherence (100 iterations; IOTF form and K = 9 source
-    modes). One solve call of the workload's iterations is timed, graph replay
-    (the default) and the persistent launch. At these sizes an iteration is a
-    chain of ~13 kernels on a field that sits in L2: launch latency, not HBM,
-    sets the time, so no HBM fraction is reported."""
+    modes). One solve call of the workload's iterations is timed: the graph
+    holding the loop (the default), the persistent cooperative launch and the
+    cluster-resident launch (one thread-block cluster per projection; every
+    cluster size that fits is timed, the default size gives the line). At these
+    sizes an iteration is a chain of ~13 passes over a field that sits in L2:
+    latency, not HBM, sets the time, so no HBM fraction is reported."""
     import numpy as np
     out = {}
     cases = (("blob128_coherent", 0), ("blob512_iotf", 0), ("blob512_iotf", 9))
@@ -459,14 +461,11 @@ def run_small(P, S, torch, dev, stream, reps=5):
         psi_true = torch.from_numpy(S.complex_phase_from(S.blob_phase(w.ny, w.nx, S.rng_for(w.config, 0)))
                                     .astype(np.complex64))[None].to(dev)
         t = torch.from_numpy(S.diffuser(w.ny, w.nx, S.rng_for(w.config, 99)).astype(np.complex64)).to(dev)
-        paths = (("graph", P.FLAG_GRAPH), ("persistent", P.FLAG_PERSISTENT)) if K == 0 else (("graph", 0),)
-        for path, flags in paths:
-            plan = P.Plan(P.PlanDesc(1, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
-                                     w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags, K, 2.0 if K else 0.0))
-            f = plan.forward(psi_true, t)
-            g = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config)
-            y = (torch.poisson(f.clamp_min(0) * w.photons, generator=g) / w.photons).contiguous()
-            psi = torch.zeros_like(psi_true)
+        paths = ((("graph", P.FLAG_GRAPH), ("graph_no_pdl", P.FLAG_GRAPH | P.FLAG_NO_PDL),
+                  ("persistent", P.FLAG_PERSISTENT), ("cluster", P.FLAG_CLUSTER))
+                 if K == 0 else (("graph", 0), ("graph_no_pdl", P.FLAG_NO_PDL)))
+
+        def timed_solve(plan, y, psi):
             for _ in range(3):
                 psi.zero_()
                 plan.solve(y, t, psi, w.n_iter, read_back=False)
@@ -478,12 +477,32 @@ def run_small(P, S, torch, dev, stream, reps=5):
                 plan.solve(y, t, psi, w.n_iter, read_back=False)
             e1.record(stream)
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
+            return e0.elapsed_time(e1) / reps
+
+        for path, flags in paths:
+            plan = P.Plan(P.PlanDesc(1, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
+                                     w.gamma, w.alpha.real, w.alpha.imag, w.eta, flags, K, 2.0 if K else 0.0))
+            f = plan.forward(psi_true, t)
+            g = torch.Generator(device=dev).manual_seed(20146000 + 100 * w.config)
+            y = (torch.poisson(f.clamp_min(0) * w.photons, generator=g) / w.photons).contiguous()
+            psi = torch.zeros_like(psi_true)
+            ms = timed_solve(plan, y, psi)
             key = f"{name}{'_k%d' % K if K else ''}_{path}"
             out[key] = {"value": w.ny * w.nx * w.n_iter / 1e6 / (ms / 1e3), "unit": UNIT,
                         "iterations_per_s": w.n_iter / (ms / 1e3), "us_per_iteration": 1e3 * ms / w.n_iter,
                         "ms_per_solve": ms, "iterations": w.n_iter, "ny": w.ny, "nx": w.nx, "n_modes": K,
-                        "hbm_fraction": "not applicable (launch-latency bound, field resident in L2)"}
+                        "hbm_fraction": "not applicable (latency bound, field resident in L2)"}
+            if path == "cluster":
+                default = P.pwf_plan_cluster_size(plan.handle)
+                sweep = {}
+                for cs in (1, 2, 4, 8, 16):
+                    try:
+                        P.pwf_plan_set_cluster_size(plan.handle, cs)
+                    except P.PWFError:
+                        continue
+                    sweep[str(cs)] = round(1e3 * timed_solve(plan, y, psi) / w.n_iter, 2)
+                P.pwf_plan_set_cluster_size(plan.handle, default)
+                out[key].update({"cluster_ctas": default, "us_per_iteration_by_cluster_ctas": sweep})
             plan.close()
     return out
 

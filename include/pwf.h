@@ -67,8 +67,18 @@ typedef struct pwf_state pwf_state;
                                     iterations (grid barriers between the passes,
                                     every wait bounded); square grids of 64, 128, 256
                                     or 512 only, else PWF_ERR_UNSUPPORTED           */
-#define PWF_FLAG_GRAPH 0x40u     /* pwf_solve by CUDA-graph replay of one iteration
-                                    (the default; excludes PWF_FLAG_PERSISTENT)     */
+#define PWF_FLAG_GRAPH 0x40u     /* pwf_solve as one CUDA graph holding the whole
+                                    iteration loop (the default)                   */
+#define PWF_FLAG_CLUSTER 0x80u   /* pwf_solve as ONE launch of one thread-block
+                                    cluster per projection for all iterations
+                                    (hardware cluster barriers between the passes);
+                                    square grids of 64, 128, 256 or 512 only, else
+                                    PWF_ERR_UNSUPPORTED. At most one of PERSISTENT,
+                                    GRAPH and CLUSTER (else PWF_ERR_INVALID_ARG)  */
+#define PWF_FLAG_NO_PDL 0x100u   /* launch the passes without programmatic dependent
+                                    launch (by default each pass is scheduled once
+                                    the CTAs of the one before it have exited and
+                                    waits on the device for that pass's writes)    */
 
 /* Inputs of Algorithm S1 other than y and t. All lengths in metres. */
 typedef struct {
@@ -168,16 +178,23 @@ pwf_status pwf_state_read(pwf_plan* plan, const pwf_state* state, double* loss_h
 
 /* Algorithm S1 from the caller's psi (Algorithm S1 starts from psi = 0; the
  * caller zeroes psi for that): up to max_iter iterations, with the stopping
- * rule when corr_tol > 0. Fused, batched passes, run one of two ways:
- *  - CUDA-graph replay: one iteration (its passes and the end-of-iteration
- *    kernel) captured once and launched max_iter times;
+ * rule when corr_tol > 0. Fused, batched passes, run one of three ways:
+ *  - one CUDA graph (the default): one iteration (its passes and the
+ *    end-of-iteration kernel) captured once into the body of a conditional
+ *    WHILE node, whose condition a last kernel sets after each iteration, so
+ *    the loop runs on the device: one graph launch per call. Where the driver
+ *    refuses conditional nodes, the one-iteration graph is launched from a host
+ *    loop instead;
  *  - one persistent cooperative launch for all iterations (PWF_FLAG_PERSISTENT;
  *    square IOTF/coherent plans of 64^2..512^2): the passes are split into
  *    warp-sized items over every SM, with grid barriers between passes. Each
  *    barrier waits at most the plan's wait limit; when a wait runs out the
  *    launch ends early, and the call (or the next pwf_state_read) returns
- *    PWF_ERR_TIMEOUT. Graph replay is the default: it measured faster at every
- *    size the persistent launch serves.
+ *    PWF_ERR_TIMEOUT;
+ *  - one launch of one thread-block cluster per projection (PWF_FLAG_CLUSTER;
+ *    the same plans): each cluster runs its projection's iterations on its
+ *    own, with the hardware cluster barrier between passes, and no cluster
+ *    waits on another.
  * iters_host / loss_host: HOST arrays of length B (may be NULL); when either is
  * given the call synchronises. psi is updated in place. */
 pwf_status pwf_solve(pwf_plan* plan, const float* y, const void* t, void* psi, int32_t max_iter,
@@ -320,6 +337,15 @@ pwf_status pwf_profile_iteration(pwf_plan* plan, const float* y, const void* t, 
  * this plan, 0 if it replays the graph, -1 for NULL. */
 pwf_status pwf_plan_set_wait_limit(pwf_plan* plan, int64_t cycles);
 int32_t pwf_plan_uses_persistent(const pwf_plan* plan);
+/* CTAs per cluster of a PWF_FLAG_CLUSTER plan: 1..16, or 0 for the default
+ * (the largest cluster the device holds, up to 16 and to one CTA per
+ * warp-sized item of a pass). PWF_ERR_INVALID_ARG for another
+ * plan or a size outside 0..16, PWF_ERR_UNSUPPORTED when the device cannot
+ * hold such a cluster. pwf_plan_cluster_size returns the size in use (0 for
+ * other plans, -1 for NULL); pwf_plan_uses_persistent returns 2 for these
+ * plans. */
+pwf_status pwf_plan_set_cluster_size(pwf_plan* plan, int32_t ctas);
+int32_t pwf_plan_cluster_size(const pwf_plan* plan);
 
 /* Forward model for callers that cannot allocate device memory. The paper has
  * no counterpart: this is an interface choice, not part of the method.

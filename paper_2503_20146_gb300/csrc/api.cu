@@ -90,6 +90,7 @@ __global__ void k_max_abs2(const float2* __restrict__ t, size_t n, float* out) {
 // accumulator reset, and the Nesterov coefficients of the next iteration.
 __global__ void k_finalize(double* acc, int B, int* active, int* iters, double* loss, double* corr,
                            DevIter* it, double corr_tol) {
+  pdl_wait();
   __shared__ int s_active;
   if (threadIdx.x == 0) s_active = 0;
   __syncthreads();
@@ -128,6 +129,7 @@ __global__ void k_state_reset(DevIter* it, int* active, int* iters, double* loss
 // before the launch); the loop ends after ctl[0] bodies whatever the solver
 // state holds, or earlier once the stopping rule has retired every projection.
 __global__ void k_loop_control(cudaGraphConditionalHandle h, const DevIter* it, int* ctl, double corr_tol) {
+  pdl_wait();
   if (threadIdx.x == 0) {
     const int done = ++ctl[1];
     const bool more = done < ctl[0] && (corr_tol <= 0.0 || it->n_active > 0);
@@ -415,6 +417,8 @@ struct pwf_plan {
   double* gpart = nullptr;       // [persist_grid][B][NACC]
   unsigned* bar = nullptr;       // grid barrier words
   PersistPhase* phases = nullptr;  // device copy of the iteration's passes
+  int cluster = 0;               // cluster-resident variant: CTAs per cluster (0: not used)
+  DevIter* cit = nullptr;        // [B] per-projection iteration records of that variant
 };
 
 namespace {
@@ -506,6 +510,9 @@ int grid_for(size_t n) {
   return (int)(g > 152 * 16 ? 152 * 16 : (g == 0 ? 1 : g));
 }
 
+// passes and end-of-iteration kernels take programmatic dependent launch
+int pdl_of(const pwf_plan* p) { return (p->d.flags & PWF_FLAG_NO_PDL) ? 0 : 1; }
+
 PassArgs base_args(pwf_plan* p) {
   PassArgs a{};
   a.B = p->d.batch;
@@ -523,6 +530,7 @@ PassArgs base_args(pwf_plan* p) {
   a.gscale = 1.0f;
   a.mode_w = 1.0f;
   a.proj0 = 0;
+  a.pdl = pdl_of(p);
   return a;
 }
 
@@ -696,6 +704,7 @@ std::vector<Mode> source_modes(const pwf_plan_desc& d) {
 
 // e = y - I; loss += e^2 per projection; I <- -e (= f - y)
 __global__ void k_modal_resid(float* I, const float* __restrict__ y, size_t per_proj, double* acc, int proj0) {
+  pdl_wait();
   const int proj = blockIdx.y + proj0;
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_proj; i += (size_t)gridDim.x * blockDim.x) {
@@ -800,8 +809,7 @@ pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
   const size_t per = (size_t)p->d.ny * p->d.nx;
   dim3 grid((unsigned)((per + 255) / 256 > 64 ? 64 : (per + 255) / 256), (unsigned)nproj_of(p));
   return enqueue(p, "modal_resid", [&] {
-           k_modal_resid<<<grid, 256, 0, p->stream>>>(p->IBUF, y, per, p->acc, 0);
-           return cudaGetLastError();
+           return launch_pass(k_modal_resid, grid, dim3(256), 0, p->stream, pdl_of(p), p->IBUF, y, per, p->acc, 0);
          }) == cudaSuccess
              ? PWF_OK
              : cuda_fail(p, cudaGetLastError(), "k_modal_resid");
@@ -834,9 +842,8 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     a.phi = st->phi;
     LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
     LAUNCH(p, enqueue(p, "finalize", [&] {
-        k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it,
-                                             corr_tol);
-        return cudaGetLastError();
+        return launch_pass(k_finalize, dim3(1), dim3(256), 0, p->stream, pdl_of(p), p->acc, a.B, st->active, st->iters,
+                           st->loss, st->corr, st->it, corr_tol);
       }));
     return PWF_OK;
   }
@@ -866,8 +873,8 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
   a.phi = st->phi;
   LAUNCH(p, row(p, next_fft ? ROW_NESTEROV_FFT : ROW_NESTEROV, a, nproj_of(p)));
   LAUNCH(p, enqueue(p, "finalize", [&] {
-      k_finalize<<<1, 256, 0, p->stream>>>(p->acc, a.B, st->active, st->iters, st->loss, st->corr, st->it, corr_tol);
-      return cudaGetLastError();
+      return launch_pass(k_finalize, dim3(1), dim3(256), 0, p->stream, pdl_of(p), p->acc, a.B, st->active, st->iters,
+                         st->loss, st->corr, st->it, corr_tol);
     }));
   if (joint) {
     // joint refinement: step t along the batch sum of g_t (max|t|^2 of the
@@ -938,7 +945,7 @@ pwf_status persist_solve(pwf_plan* p, pwf_state* st, const float* y, const float
   if ((int)ph.size() > PERSIST_MAX_PHASES) return fail(p, PWF_ERR_STATE, "too many passes for the persistent solver");
   PWF_CUDA(p, cudaMemcpyAsync(p->phases, ph.data(), ph.size() * sizeof(PersistPhase), cudaMemcpyHostToDevice,
                               p->stream));
-  PWF_CUDA(p, cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
+  if (p->cluster == 0) PWF_CUDA(p, cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
   PersistArgs pa{};
   pa.phases = p->phases;
   pa.nphases = (int)ph.size();
@@ -953,7 +960,13 @@ pwf_status persist_solve(pwf_plan* p, pwf_state* st, const float* y, const float
   pa.loss = st->loss;
   pa.corr = st->corr;
   pa.it = st->it;
-  LAUNCH(p, enqueue(p, "persist", [&] { return p->kcol->persist(pa, p->persist_grid, p->stream); }));
+  pa.cit = p->cit;
+  if (p->cluster > 0) {
+    LAUNCH(p, enqueue(p, "persist_cluster", [&] { return p->kcol->persist_cluster(pa, p->cluster, p->stream); }));
+    p->launches++;  // the closing k_persist_cluster_finish
+  } else {
+    LAUNCH(p, enqueue(p, "persist", [&] { return p->kcol->persist(pa, p->persist_grid, p->stream); }));
+  }
   return PWF_OK;
 }
 
@@ -1161,8 +1174,9 @@ pwf_status capture_loop_graph(pwf_plan* p, pwf_state* st, double corr_tol, F&& b
   const long long before = p->launches;
   pwf_status r = body();
   if (r == PWF_OK) {
-    k_loop_control<<<1, 32, 0, p->stream>>>(h, st->it, p->loop_ctl, corr_tol);
-    if ((ce = cudaGetLastError()) != cudaSuccess) r = cuda_fail(p, ce, "k_loop_control");
+    ce = launch_pass(k_loop_control, dim3(1), dim3(32), 0, p->stream, pdl_of(p), h, (const DevIter*)st->it, p->loop_ctl,
+                     corr_tol);
+    if (ce != cudaSuccess) r = cuda_fail(p, ce, "k_loop_control");
     p->launches++;
   }
   p->graph_kernels = p->launches - before;
@@ -1223,9 +1237,12 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
       (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE |
-                   PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH)))
+                   PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER | PWF_FLAG_NO_PDL)))
     return PWF_ERR_INVALID_ARG;
-  if ((d.flags & PWF_FLAG_PERSISTENT) && (d.flags & PWF_FLAG_GRAPH)) return PWF_ERR_INVALID_ARG;
+  {
+    const uint32_t solver = d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER);
+    if (solver & (solver - 1)) return PWF_ERR_INVALID_ARG;  // at most one way to run pwf_solve
+  }
   if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
     return PWF_ERR_INVALID_ARG;
   if (d.n_modes > 1 && (d.flags & PWF_FLAG_PLAIN)) return PWF_ERR_UNSUPPORTED;  // baseline is the paper's form
@@ -1293,9 +1310,17 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
     const bool eligible = p->kcol->persist != nullptr && d.nx == d.ny && p->modes.empty() &&
                           !(d.flags & PWF_FLAG_PLAIN);
     const bool want = (d.flags & PWF_FLAG_PERSISTENT) != 0;
-    if ((d.flags & PWF_FLAG_PERSISTENT) && !eligible) {
+    if ((d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_CLUSTER)) && !eligible) {
       pwf_plan_destroy(p);
       return PWF_ERR_UNSUPPORTED;
+    }
+    if (d.flags & PWF_FLAG_CLUSTER) {
+      if ((r = dalloc(p, &p->gpart, (size_t)d.batch * PERSIST_MAX_CLUSTER * NACC)) ||
+          (r = dalloc(p, &p->cit, (size_t)d.batch)) || (r = dalloc(p, &p->phases, PERSIST_MAX_PHASES)) ||
+          (r = pwf_plan_set_cluster_size(p, 0))) {
+        pwf_plan_destroy(p);
+        return r;
+      }
     }
     if (eligible && want) {
       int per_sm = 0;
@@ -1675,7 +1700,7 @@ static pwf_status solve_impl(pwf_plan* p, const float* y, const void* t, void* p
     a.psi = P;
     a.out = p->X;
     LAUNCH(p, row(p, ROW_EXP_FFT, a, a.B));
-    if (p->persist && !joint) {
+    if ((p->persist || p->cluster > 0) && !joint) {
       if ((r = persist_solve(p, st, y, (const float2*)t, P, max_iter, corr_tol))) return r;
       if (iters_host || loss_host) return pwf_state_read(p, st, loss_host, nullptr, iters_host, nullptr);
       return PWF_OK;
@@ -1888,7 +1913,40 @@ pwf_status pwf_plan_set_wait_limit(pwf_plan* p, int64_t cycles) {
   return PWF_OK;
 }
 
-int32_t pwf_plan_uses_persistent(const pwf_plan* p) { return p ? (p->persist ? 1 : 0) : -1; }
+int32_t pwf_plan_uses_persistent(const pwf_plan* p) { return p ? (p->cluster > 0 ? 2 : p->persist ? 1 : 0) : -1; }
+
+pwf_status pwf_plan_set_cluster_size(pwf_plan* p, int32_t ctas) {
+  if (!p || !p->kcol || !p->kcol->persist_cluster || !p->cit || ctas < 0 || ctas > PERSIST_MAX_CLUSTER)
+    return PWF_ERR_INVALID_ARG;
+  if (ctas == 0) {
+    // One warp-sized item (32 / (threads per transform) rows or columns) runs
+    // as a serial chain on its warp, so the pass takes as long as its longest
+    // chain: the default spreads the items over as many SMs as one cluster
+    // can hold (measured at 128^2: 105 us per iteration on 2 CTAs, 71 on 8,
+    // 71 on 16), at most one CTA per item.
+    const int per_item = 32 / tpf_for(p->d.nx);
+    const int items = p->d.nx / per_item;
+    int cs = PERSIST_MAX_CLUSTER;
+    while (cs > 1 && cs > items) cs /= 2;
+    for (; cs >= 1; cs /= 2) {
+      int maxc = 0;
+      if (p->kcol->persist_cluster_prep(p->d.batch, cs, &maxc) == cudaSuccess && maxc > 0) break;
+      cudaGetLastError();
+    }
+    if (cs < 1) return fail(p, PWF_ERR_UNSUPPORTED, "no cluster shape of the cluster-resident solver fits");
+    p->cluster = cs;
+    return PWF_OK;
+  }
+  int maxc = 0;
+  if (p->kcol->persist_cluster_prep(p->d.batch, ctas, &maxc) != cudaSuccess || maxc < 1) {
+    cudaGetLastError();
+    return fail(p, PWF_ERR_UNSUPPORTED, "this cluster shape does not fit on the device");
+  }
+  p->cluster = ctas;
+  return PWF_OK;
+}
+
+int32_t pwf_plan_cluster_size(const pwf_plan* p) { return p ? p->cluster : -1; }
 
 int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
   if (!p || pass < 0 || pass >= NUM_COL_OPS) return -1;
@@ -1913,8 +1971,9 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
     o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
   };
   o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d solver=%s loop=%s", p->d.ny, p->d.nx,
-                     p->d.batch, p->persist ? "persistent" : "graph",
-                     p->persist ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
+                     p->d.batch, p->cluster > 0 ? "cluster" : p->persist ? "persistent" : "graph",
+                     p->persist || p->cluster > 0 ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
+  if (p->cluster > 0) o += std::snprintf(tmp + o, sizeof(tmp) - o, " cluster_ctas=%d", p->cluster);
   for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {
     o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);
@@ -1998,6 +2057,7 @@ namespace {
 // rule has retired every projection of every class.
 __global__ void k_group_loop_control(cudaGraphConditionalHandle h, DevIter* const* its, int n, int* ctl,
                                      double corr_tol) {
+  pdl_wait();
   if (threadIdx.x == 0) {
     int active = 0;
     for (int i = 0; i < n; i++) active += its[i]->n_active;
@@ -2167,8 +2227,8 @@ pwf_status pwf_group_solve(pwf_group* g, void* stream, const float* const* y, co
       ce = cudaStreamWaitEvent(g->main, g->ev[1 + i], 0);
     }
     if (loop_body && r == PWF_OK && ce == cudaSuccess) {
-      k_group_loop_control<<<1, 32, 0, g->main>>>(h, g->d_its, n, p0->loop_ctl, corr_tol);
-      ce = cudaGetLastError();
+      ce = launch_pass(k_group_loop_control, dim3(1), dim3(32), 0, g->main, pdl_of(p0), h, (DevIter* const*)g->d_its, n,
+                       p0->loop_ctl, corr_tol);
       kernels++;
     }
     cudaError_t ce2 = cudaStreamEndCapture(g->main, &graph);

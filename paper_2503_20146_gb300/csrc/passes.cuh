@@ -84,6 +84,7 @@ struct PassArgs {
   float mode_w;
   int accumulate;
   int* kstatus;            // device word set to PWF_ERR_TIMEOUT (7) when a bounded wait runs out
+  int pdl;                 // launch with the programmatic stream-serialization attribute
   CUtensorMap tmap;        // TMA map of `in` (filled by the launcher of a TMA-staged shape)
 };
 
@@ -128,6 +129,35 @@ struct RowT {
   static constexpr int nred = (OP == ROW_RESID || OP == ROW_COH_RESID) ? 1
                               : (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) ? 5 : 0;
 };
+
+// Programmatic dependent launch. A pass launched with the programmatic
+// stream-serialization attribute is scheduled as soon as the CTAs of the pass
+// before it have exited, without waiting for that grid's completion to be
+// processed; it waits here until that pass has completed and its writes are
+// visible. No pass signals its dependents early: resident CTAs of the next
+// pass waiting beside the running one measured slower at 512^2 and above.
+// Launched without the attribute, the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch of a pass, with the programmatic attribute when pdl is set.
+template <class... P, class... A>
+cudaError_t launch_pass(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int pdl, A&&... args) {
+  if (!pdl) {
+    k<<<grid, block, smem, s>>>(static_cast<A&&>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
 
 // Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, multiple of 16).
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -396,6 +426,7 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
 
 template <int N, int OP>
 __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_kernel(const PassArgs a) {
+  pdl_wait();
   constexpr int TPF = tpf_for(N), ROWS = rows_for(N);
   using T = RowT<OP>;
   extern __shared__ float2 smem[];
@@ -534,6 +565,7 @@ __device__ __forceinline__ void col_body(const PassArgs& a, int proj, int col, i
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
     col_kernel(const PassArgs a) {
+  pdl_wait();
   extern __shared__ float2 smem[];
   const int tid = threadIdx.x;
   const int c = tid % C, t = tid / C;
@@ -560,6 +592,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_threads(N, C), ept_for(N)))
     col_kernel_pipe(const PassArgs a, int nproj) {
+  pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int NT = col_threads(N, C);
   constexpr int RS = first_radix<N, FWD>();
@@ -714,6 +747,7 @@ __device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int co
 // the current one is done, and the overlap comes from the second CTA on the SM.
 template <int N, int OP, int C, int NBUF>
 __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const PassArgs a, int nproj) {
+  pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int NT = col2_threads(N, C);
   constexpr int RS = first_radix<N, FWD>();
@@ -879,6 +913,7 @@ __host__ __device__ constexpr size_t tma_smem_bytes(int n, int c) { return (size
 
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_tma2(const __grid_constant__ PassArgs a, int nproj) {
+  pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
@@ -963,6 +998,7 @@ bool encode_field_tmap(CUtensorMap* m, const void* base, int B, int ny, int nx, 
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_kernel_t(const PassArgs a, int nproj) {
+  pdl_wait();
   constexpr int EPT = ept_for(N), TPF = tpf_for(N);
   constexpr int NT = col_threads(N, C);
   constexpr int RS = first_radix<N, FWD>();
@@ -1075,6 +1111,7 @@ __device__ __forceinline__ int wrap_sub(int k, int m, int n) { return k >= m ? k
 template <int N, int MOP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
     col_mode_kernel(const PassArgs a) {
+  pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
@@ -1124,6 +1161,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 // two 8-byte accesses.
 template <int N, int MOP, int C>
 __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const PassArgs a) {
+  pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
@@ -1216,8 +1254,7 @@ template <int N, int OP>
 cudaError_t launch_row(const PassArgs& a, int nproj, cudaStream_t s) {
   constexpr int ROWS = rows_for(N);
   const long long nrows = (long long)nproj * a.ny;
-  row_kernel<N, OP><<<(unsigned)(nrows / ROWS), row_threads(N), row_smem_bytes(N), s>>>(a);
-  return cudaGetLastError();
+  return launch_pass(row_kernel<N, OP>, dim3((unsigned)(nrows / ROWS)), dim3(row_threads(N)), row_smem_bytes(N), s, a.pdl, a);
 }
 
 // column-pass shape variants: tile width C, pipelined or not
@@ -1274,20 +1311,24 @@ struct ColShape {
       if constexpr (PIPE == 5) {
         PassArgs b = a;
         if (!encode_field_tmap(&b.tmap, a.in, a.proj0 + nproj, a.ny, a.nx, C)) return cudaErrorInvalidValue;
-        col_kernel_tma2<N, OP, C><<<grid, col2_threads(N, C), tma_smem_bytes(N, C), s>>>(b, nproj);
+        return launch_pass(col_kernel_tma2<N, OP, C>, dim3(grid), dim3(col2_threads(N, C)), tma_smem_bytes(N, C), s, a.pdl, b,
+                           nproj);
       } else if constexpr (PIPE == 3)
-        col_kernel_pipe2<N, OP, C, 2><<<grid, col2_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+        return launch_pass(col_kernel_pipe2<N, OP, C, 2>, dim3(grid), dim3(col2_threads(N, C)), colp_smem_bytes(N, C), s,
+                           a.pdl, a, nproj);
       else if constexpr (PIPE == 4)
-        col_kernel_pipe2<N, OP, C, 1><<<grid, col2_threads(N, C), col_smem_bytes(N, C), s>>>(a, nproj);
+        return launch_pass(col_kernel_pipe2<N, OP, C, 1>, dim3(grid), dim3(col2_threads(N, C)), col_smem_bytes(N, C), s,
+                           a.pdl, a, nproj);
       else if constexpr (PIPE == 2)
-        col_kernel_t<N, OP, C><<<grid, col_threads(N, C), colt_smem_bytes(N, C), s>>>(a, nproj);
+        return launch_pass(col_kernel_t<N, OP, C>, dim3(grid), dim3(col_threads(N, C)), colt_smem_bytes(N, C), s, a.pdl, a,
+                           nproj);
       else
-        col_kernel_pipe<N, OP, C><<<grid, col_threads(N, C), colp_smem_bytes(N, C), s>>>(a, nproj);
+        return launch_pass(col_kernel_pipe<N, OP, C>, dim3(grid), dim3(col_threads(N, C)), colp_smem_bytes(N, C), s, a.pdl,
+                           a, nproj);
     } else {
       dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
-      col_kernel<N, OP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+      return launch_pass(col_kernel<N, OP, C>, grid, dim3(col_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a);
     }
-    return cudaGetLastError();
   }
 };
 template <int N, int OP, int C, int PIPE>
@@ -1297,6 +1338,9 @@ struct PersistArgs;  // persist.cuh
 using PersistFn = cudaError_t (*)(const PersistArgs&, int grid, cudaStream_t);
 using PersistPrepFn = cudaError_t (*)(int batch);
 using PersistOccFn = cudaError_t (*)(int batch, int* per_sm);
+// cluster-resident variant: a grid of batch clusters of `cluster` CTAs
+using PersistClusterFn = cudaError_t (*)(const PersistArgs&, int cluster, cudaStream_t);
+using PersistClusterPrepFn = cudaError_t (*)(int batch, int cluster, int* max_clusters);
 
 struct ColVariant {
   PassFn launch;
@@ -1319,6 +1363,8 @@ struct LengthKernels {
   PersistFn persist;
   PersistPrepFn persist_prep;
   PersistOccFn persist_occupancy;
+  PersistClusterFn persist_cluster;
+  PersistClusterPrepFn persist_cluster_prep;
 };
 
 // the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
@@ -1341,10 +1387,9 @@ cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
   constexpr int C = colmode_pair(N) ? 8 : colmode_c(N);
   dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
   if constexpr (colmode_pair(N))
-    col_mode_kernel2<N, MOP, C><<<grid, col2_threads(N, C), col_smem_bytes(N, C), s>>>(a);
+    return launch_pass(col_mode_kernel2<N, MOP, C>, grid, dim3(col2_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a);
   else
-    col_mode_kernel<N, MOP, C><<<grid, col_threads(N, C), col_smem_bytes(N, C), s>>>(a);
-  return cudaGetLastError();
+    return launch_pass(col_mode_kernel<N, MOP, C>, grid, dim3(col_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a);
 }
 
 // a shape is offered when its CTA has 16..512 threads and its buffers fit

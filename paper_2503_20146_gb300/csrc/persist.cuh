@@ -140,6 +140,7 @@ struct PersistArgs {
   double* loss;
   double* corr;
   DevIter* it;
+  DevIter* cit;                // [B] per-projection iteration records (cluster-resident variant)
 };
 
 __host__ __device__ constexpr size_t persist_smem_bytes(int n, int batch) {
@@ -157,12 +158,15 @@ __device__ __forceinline__ double warp_sum(float x) {
 
 // rows of a row pass: item = 32/TPF consecutive rows (one projection)
 template <int N, int OP>
-__device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc) {
+__device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc,
+                                             int only) {
   constexpr int TPF = tpf_for(N), RPW = 32 / TPF;
   const int sub = lane / TPF, t = lane - sub * TPF;
   const RowLayout<TPF, 32> sm{wsm + sub * row_smem_len(N), 0};
-  const long long items = (long long)a.B * a.ny / RPW;
-  for (long long it = gw; it < items; it += GW) {
+  // every projection's rows, or (only >= 0) those of projection `only`
+  const long long per = (long long)a.ny / RPW;
+  const long long i0 = only < 0 ? 0 : only * per, items = only < 0 ? a.B * per : i0 + per;
+  for (long long it = i0 + gw; it < items; it += GW) {
     const long long row = it * RPW + sub;
     const int proj = (int)((it * RPW) / a.ny);
     if (a.active != nullptr && a.active[proj] == 0) continue;  // uniform per warp
@@ -185,12 +189,14 @@ __device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, 
 // columns of a column pass: item = 32/TPF adjacent columns of one projection;
 // lane = t * CPW + c, so that a warp's loads cover CPW adjacent columns
 template <int N, int OP>
-__device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc) {
+__device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc,
+                                             int only) {
   constexpr int TPF = tpf_for(N), CPW = 32 / TPF;
   const int c = lane % CPW, t = lane / CPW;
   const RowLayout<TPF, 32> sm{wsm + c * row_smem_len(N), 0};
-  const long long items = (long long)a.B * a.nx / CPW;
-  for (long long it = gw; it < items; it += GW) {
+  const long long per = (long long)a.nx / CPW;
+  const long long i0 = only < 0 ? 0 : only * per, items = only < 0 ? a.B * per : i0 + per;
+  for (long long it = i0 + gw; it < items; it += GW) {
     const long long cg = it * CPW;
     const int proj = (int)(cg / a.nx);
     const int col = (int)(cg - (long long)proj * a.nx) + c;
@@ -207,25 +213,25 @@ __device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, 
 
 template <int N>
 __device__ __forceinline__ void persist_row_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
-                                               double* s_acc) {
+                                               double* s_acc, int only = -1) {
   switch (op) {
-    case ROW_MUL_T: persist_rows<N, ROW_MUL_T>(a, gw, GW, lane, wsm, s_acc); break;
-    case ROW_INTENSITY: persist_rows<N, ROW_INTENSITY>(a, gw, GW, lane, wsm, s_acc); break;
-    case ROW_MUL_V: persist_rows<N, ROW_MUL_V>(a, gw, GW, lane, wsm, s_acc); break;
-    case ROW_COH_RESID: persist_rows<N, ROW_COH_RESID>(a, gw, GW, lane, wsm, s_acc); break;
-    case ROW_GRAD_PACK: persist_rows<N, ROW_GRAD_PACK>(a, gw, GW, lane, wsm, s_acc); break;
-    case ROW_NESTEROV_FFT: persist_rows<N, ROW_NESTEROV_FFT>(a, gw, GW, lane, wsm, s_acc); break;
+    case ROW_MUL_T: persist_rows<N, ROW_MUL_T>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_INTENSITY: persist_rows<N, ROW_INTENSITY>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_MUL_V: persist_rows<N, ROW_MUL_V>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_COH_RESID: persist_rows<N, ROW_COH_RESID>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_GRAD_PACK: persist_rows<N, ROW_GRAD_PACK>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_NESTEROV_FFT: persist_rows<N, ROW_NESTEROV_FFT>(a, gw, GW, lane, wsm, s_acc, only); break;
     default: break;
   }
 }
 
 template <int N>
 __device__ __forceinline__ void persist_col_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
-                                               double* s_acc) {
+                                               double* s_acc, int only = -1) {
   switch (op) {
-    case COL_Q: persist_cols<N, COL_Q>(a, gw, GW, lane, wsm, s_acc); break;
-    case COL_RESID_IOTF2: persist_cols<N, COL_RESID_IOTF2>(a, gw, GW, lane, wsm, s_acc); break;
-    case COL_PRECOND_REG: persist_cols<N, COL_PRECOND_REG>(a, gw, GW, lane, wsm, s_acc); break;
+    case COL_Q: persist_cols<N, COL_Q>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case COL_RESID_IOTF2: persist_cols<N, COL_RESID_IOTF2>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case COL_PRECOND_REG: persist_cols<N, COL_PRECOND_REG>(a, gw, GW, lane, wsm, s_acc, only); break;
     default: break;
   }
 }
@@ -288,6 +294,178 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 1) persist_kernel(const Persi
   }
 }
 
+// ---------------------------------------------------------------------------
+// cluster-resident persistent solver
+// ---------------------------------------------------------------------------
+// One thread-block cluster per projection runs all of that projection's
+// iterations: its CTAs split the rows and columns of every pass, and the
+// hardware cluster barrier (release/acquire at cluster scope, which orders the
+// pass's global-memory writes before the next pass's reads) separates the
+// passes. No CTA waits on another cluster, so clusters start and finish on
+// their own, and the wait at a barrier ends once every thread of the cluster,
+// all of which run the same sequence of barriers, has arrived. The end of an
+// iteration (Algorithm S1's loss, correlation, stopping rule and Nesterov's
+// mu) is taken by the cluster's first CTA from the CTAs' partial sums in a
+// fixed order, into the projection's own iteration record, whose beta the
+// Nesterov pass of the cluster reads.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_count() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+constexpr int PERSIST_MAX_CLUSTER = 16;
+
+// dynamic shared memory: the warps' transform buffers, the sums, then a copy
+// of the passes' arguments (128-byte aligned)
+__host__ __device__ constexpr size_t persist_cluster_phase_offset(int n, int batch) {
+  return (persist_smem_bytes(n, batch) + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t persist_cluster_smem_bytes(int n, int batch) {
+  return persist_cluster_phase_offset(n, batch) + PERSIST_MAX_PHASES * sizeof(PersistPhase);
+}
+
+template <int N>
+__global__ void __launch_bounds__(PERSIST_THREADS, 1) persist_cluster_kernel(const PersistArgs pa) {
+  constexpr int W = PERSIST_THREADS / 32, RPW = 32 / tpf_for(N);
+  static_assert(sizeof(PersistPhase) % 16 == 0, "phases are copied in 16-byte words");
+  extern __shared__ __align__(128) float2 smem[];
+  double* s_acc = reinterpret_cast<double*>(smem + W * RPW * row_smem_len(N));
+  PersistPhase* s_ph = reinterpret_cast<PersistPhase*>(reinterpret_cast<char*>(smem) +
+                                                       persist_cluster_phase_offset(N, pa.B));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int CS = (int)cluster_count(), cr = (int)cluster_rank();
+  const int proj = (int)cluster_index();
+  const int gw = warp * CS + cr, GW = CS * W;  // consecutive items on different CTAs
+  float2* wsm = smem + warp * RPW * row_smem_len(N);
+  DevIter* cit = pa.cit + proj;
+
+  {
+    const int4* src = reinterpret_cast<const int4*>(pa.phases);
+    int4* dst = reinterpret_cast<int4*>(s_ph);
+    const int words = pa.nphases * (int)(sizeof(PersistPhase) / 16);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  for (int i = threadIdx.x; i < pa.B * NACC; i += blockDim.x) s_acc[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the Nesterov pass reads this projection's beta
+    for (int ph = 0; ph < pa.nphases; ph++)
+      if (s_ph[ph].a.beta == &pa.it->beta) s_ph[ph].a.beta = &cit->beta;
+    if (cr == 0) {
+      *cit = *pa.it;
+      cit->n_active = pa.active[proj] ? 1 : 0;
+    }
+  }
+  cluster_barrier();
+
+  for (int iter = 0; iter < pa.max_iter; iter++) {
+    for (int ph = 0; ph < pa.nphases; ph++) {
+      const PersistPhase& P = s_ph[ph];
+      if (P.kind == PK_ROW) {
+        persist_row_op<N>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
+      } else if (P.kind == PK_COL) {
+        persist_col_op<N>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
+      } else if (P.kind == PK_FINALIZE && cr == 0 && threadIdx.x == 0) {
+        double sums[NACC] = {};
+        const int b0 = (int)blockIdx.x - cr;
+        for (int g = 0; g < CS; g++) {  // fixed order: deterministic
+          const double* q = pa.gpart + (size_t)(b0 + g) * NACC;
+#pragma unroll
+          for (int k = 0; k < 5; k++) sums[k] += q[k];
+        }
+        int nf = 0;
+        const int na = finalize_projection(proj, sums, pa.active, pa.iters, pa.loss, pa.corr, pa.corr_tol, nf);
+        if (nf) pa.it->nonfinite = 1;
+        finalize_momentum(cit, na);
+      }
+      if (P.flush) {
+        // this CTA's sums of the iteration to its slot (read by the cluster's
+        // first CTA after the barrier); zeroed for the next iteration
+        __syncthreads();
+        double* g = pa.gpart + (size_t)blockIdx.x * NACC;
+        if (threadIdx.x < NACC) {
+          g[threadIdx.x] = s_acc[proj * NACC + threadIdx.x];
+          s_acc[proj * NACC + threadIdx.x] = 0.0;
+        }
+      }
+      cluster_barrier();
+    }
+    if (pa.corr_tol > 0.0 && ld_volatile_i32(&cit->n_active) == 0) break;
+  }
+}
+
+// The plan's iteration record after a cluster-resident solve: iteration count,
+// mu and beta of the projection that iterated longest, active count summed.
+static __global__ void k_persist_cluster_finish(const DevIter* cit, int B, DevIter* it) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int best = 0, na = 0;
+    for (int p = 0; p < B; p++) {
+      if (cit[p].iter > cit[best].iter) best = p;
+      na += cit[p].n_active;
+    }
+    it->mu = cit[best].mu;
+    it->beta = cit[best].beta;
+    it->iter = cit[best].iter;
+    it->n_active = na;
+  }
+}
+
+template <int N>
+cudaLaunchConfig_t persist_cluster_config(int batch, int cluster, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(batch * cluster));
+  cfg.blockDim = dim3(PERSIST_THREADS);
+  cfg.dynamicSmemBytes = persist_cluster_smem_bytes(N, batch);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Sets the kernel's attributes for `cluster` CTAs per cluster and reports how
+// many such clusters the device holds at once (0: the shape does not fit).
+template <int N>
+cudaError_t prep_persist_cluster(int batch, int cluster, int* max_clusters) {
+  *max_clusters = 0;
+  if (cluster < 1 || cluster > PERSIST_MAX_CLUSTER) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(persist_cluster_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)persist_cluster_smem_bytes(N, batch));
+  if (e == cudaSuccess && cluster > 8)
+    e = cudaFuncSetAttribute(persist_cluster_kernel<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = persist_cluster_config<N>(batch, cluster, nullptr, attr);
+  return cudaOccupancyMaxActiveClusters(max_clusters, persist_cluster_kernel<N>, &cfg);
+}
+
+template <int N>
+cudaError_t launch_persist_cluster(const PersistArgs& pa, int cluster, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = persist_cluster_config<N>(pa.B, cluster, s, attr);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, persist_cluster_kernel<N>, pa);
+  if (e != cudaSuccess) return e;
+  k_persist_cluster_finish<<<1, 32, 0, s>>>(pa.cit, pa.B, pa.it);
+  return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t prep_persist(int batch) {
   return cudaFuncSetAttribute(persist_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -313,6 +491,8 @@ LengthKernels with_persist(LengthKernels k) {
     k.persist = launch_persist<N>;
     k.persist_prep = prep_persist<N>;
     k.persist_occupancy = occupancy_persist<N>;
+    k.persist_cluster = launch_persist_cluster<N>;
+    k.persist_cluster_prep = prep_persist_cluster<N>;
   }
   return k;
 }

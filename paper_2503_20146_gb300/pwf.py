@@ -23,6 +23,8 @@ FLAG_PLAIN = 0x4
 FLAG_NO_TUNE = 0x8
 FLAG_PERSISTENT = 0x20
 FLAG_GRAPH = 0x40
+FLAG_CLUSTER = 0x80
+FLAG_NO_PDL = 0x100
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
           4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE", 7: "PWF_ERR_TIMEOUT"}
@@ -111,6 +113,8 @@ def load(path: str | None = None):
         "pwf_diffuser_from_reference": ([_P, _P, f64, _P], i32),
         "pwf_plan_set_wait_limit": ([_P, ctypes.c_int64], i32),
         "pwf_plan_uses_persistent": ([_P], i32),
+        "pwf_plan_set_cluster_size": ([_P, i32], i32),
+        "pwf_plan_cluster_size": ([_P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +238,15 @@ def pwf_plan_set_wait_limit(plan, cycles: int):
 
 def pwf_plan_uses_persistent(plan) -> int:
     return int(load().pwf_plan_uses_persistent(plan))
+
+
+def pwf_plan_set_cluster_size(plan, ctas: int):
+    """CTAs per cluster of a cluster-resident plan (0: the default)."""
+    _check(load().pwf_plan_set_cluster_size(plan, int(ctas)), "pwf_plan_set_cluster_size", plan)
+
+
+def pwf_plan_cluster_size(plan) -> int:
+    return int(load().pwf_plan_cluster_size(plan))
 
 
 def pwf_gradient(plan, psi, t, y, g, loss=None):

@@ -42,7 +42,9 @@ def _desc(**kw):
     (dict(batch=0), 1),
     (dict(eta=0.0), 1),
     (dict(pixel_m=-1.0), 1),
-    (dict(flags=0x80), 1),
+    (dict(flags=0x200), 1),        # not a flag
+    (dict(flags=0x80 | 0x40), 1),  # two ways to run pwf_solve
+    (dict(flags=0x80 | 0x20), 1),
     (dict(wavelength_m=2e-6), 2),  # evanescent bins at this pixel pitch
     (dict(L2_m=5e3), 2),           # separable-propagator bound exceeded
     (dict(n_modes=4, mode_sigma_px=2.0), 1),   # mode count must be 0, 1, 9 or 25

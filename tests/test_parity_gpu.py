@@ -165,6 +165,19 @@ def test_device_side_loop_counts_and_replays(pwf):
         assert phase_rms(out[n].cpu().numpy()[0], ref.psi) <= PHASE_TOL
 
 
+def test_programmatic_launch_changes_no_value(pwf):
+    # passes launched with and without programmatic dependent launch run the
+    # same arithmetic: the iterates agree bit for bit
+    geom, t, y = _solve_case(W2, 2, 128, 128)
+    out = []
+    for flags in (pwf.FLAG_GRAPH, pwf.FLAG_GRAPH | pwf.FLAG_NO_PDL):
+        with plan_for(pwf, geom, 2, flags) as plan:
+            psi = torch.zeros((2, 128, 128), dtype=torch.complex64, device="cuda")
+            plan.solve(dev(y), dev(t), psi, 9)
+            out.append(psi.cpu())
+    assert torch.equal(out[0], out[1])
+
+
 def test_plain_baseline_matches_fused(pwf):
     w = W2
     geom, t, y = _solve_case(w, 2, 128, 128)

@@ -9,7 +9,10 @@ oracle and against the graph replay of the same plan.
 * a wait limit of zero makes the first barrier time out: the call returns
   PWF_ERR_TIMEOUT without hanging, and the next solve on the same plan, with
   the limit restored, is correct;
-* which plans take the persistent launch.
+* which plans take the persistent launch;
+* the cluster-resident launch (one thread-block cluster per projection):
+  against the oracle, bit for bit against the cooperative launch and across
+  cluster sizes, the stopping rule per projection, and its plan rules.
 """
 import numpy as np
 import pytest
@@ -143,3 +146,89 @@ def test_which_plans_take_the_persistent_launch(pwf):
     with pytest.raises(pwf.PWFError) as e:
         pwf.Plan(d)
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# cluster-resident launch: one thread-block cluster per projection
+# ---------------------------------------------------------------------------
+def _solve_with(pwf, geom, t, y, n, flags, cluster=None, corr_tol=0.0):
+    with pwf.Plan(desc_for(pwf, geom, y.shape[0], flags)) as plan:
+        if cluster is not None:
+            pwf.pwf_plan_set_cluster_size(plan.handle, cluster)
+        psi = torch.zeros((y.shape[0], geom.ny, geom.nx), dtype=torch.complex64, device="cuda")
+        iters, loss = plan.solve(dev(y), dev(t), psi, n, corr_tol=corr_tol)
+        return psi.cpu().numpy(), iters, loss, pwf.pwf_plan_describe(plan.handle)
+
+
+@pytest.mark.parametrize("w", [W1, W2], ids=["blob128_coherent_50it", "blob512_iotf_100it"])
+def test_cluster_solve_matches_oracle_and_persistent(pwf, w):
+    # the same passes as the cooperative launch, item for item: psi agrees
+    # bit for bit; losses (FP64 sums in another order) to rounding
+    geom, t, y = case(w, 1)
+    ref = O.solve(y[0].astype(np.float64), t.astype(np.complex128), geom, w.n_iter)
+    got, iters, loss, desc = _solve_with(pwf, geom, t, y, w.n_iter, pwf.FLAG_CLUSTER)
+    assert "solver=cluster" in desc
+    assert int(iters[0]) == w.n_iter
+    assert phase_rms(got[0], ref.psi) <= PHASE_TOL
+    assert abs(loss[0] - ref.losses[-1]) <= 1e-3 * ref.losses[-1]
+    per, _, loss_p, _ = _solve_with(pwf, geom, t, y, w.n_iter, pwf.FLAG_PERSISTENT)
+    assert np.array_equal(got, per)
+    assert abs(loss[0] - loss_p[0]) <= 1e-9 * loss_p[0]
+
+
+def test_cluster_sizes_agree_bitwise(pwf):
+    geom, t, y = case(W2, 2, 256)
+    n = 6
+    out = {}
+    for cs in (1, 2, 4, 8, 16):
+        try:
+            out[cs] = _solve_with(pwf, geom, t, y, n, pwf.FLAG_CLUSTER, cluster=cs)[0]
+        except pwf.PWFError as e:      # a shape the device cannot hold
+            assert e.status == 2
+    assert 1 in out and 8 in out
+    for cs, psi in out.items():
+        assert np.array_equal(psi, out[1]), cs
+    for b in range(2):
+        ref = O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, n)
+        assert phase_rms(out[1][b], ref.psi) <= PHASE_TOL
+
+
+def test_cluster_stopping_rule_matches_oracle(pwf):
+    # a batch of two: each cluster applies the rule to its own projection
+    geom, t, y = case(W1, 1)
+    y64, t128 = y[0].astype(np.float64), t.astype(np.complex128)
+    c = np.array(O.solve(y64, t128, geom, 80).correlations)
+    margin, k = max((c[k] - np.max(c[:k]), k) for k in range(10, len(c)))
+    assert margin >= 1e-6
+    tol = float(np.max(c[:k]) + margin / 2)
+    ref = O.solve(y64, t128, geom, 200, corr_tol=tol)
+    y2 = np.concatenate([y, y])
+    got, iters, _, _ = _solve_with(pwf, geom, t, y2, 200, pwf.FLAG_CLUSTER, corr_tol=tol)
+    assert [int(i) for i in iters] == [ref.iterations, ref.iterations]
+    assert phase_rms(got[0], ref.psi) <= PHASE_TOL
+    # one projection capped earlier by a lower limit on a second solve
+    few, iters, _, _ = _solve_with(pwf, geom, t, y, 5, pwf.FLAG_CLUSTER, corr_tol=tol)
+    assert int(iters[0]) == 5
+
+
+def test_cluster_plan_rules(pwf):
+    g128 = geometry(W1)
+    with pwf.Plan(desc_for(pwf, g128, 1, pwf.FLAG_CLUSTER)) as plan:
+        assert pwf.pwf_plan_uses_persistent(plan.handle) == 2
+        assert pwf.pwf_plan_cluster_size(plan.handle) in (8, 16)   # the largest cluster that fits
+        for bad in (-1, 17):
+            with pytest.raises(pwf.PWFError) as e:
+                pwf.pwf_plan_set_cluster_size(plan.handle, bad)
+            assert e.value.status == 1
+    with pwf.Plan(desc_for(pwf, g128, 1)) as plan:
+        assert pwf.pwf_plan_cluster_size(plan.handle) == 0
+        with pytest.raises(pwf.PWFError) as e:
+            pwf.pwf_plan_set_cluster_size(plan.handle, 2)
+        assert e.value.status == 1
+    for flags in (pwf.FLAG_CLUSTER | pwf.FLAG_GRAPH, pwf.FLAG_CLUSTER | pwf.FLAG_PERSISTENT):
+        with pytest.raises(pwf.PWFError) as e:
+            pwf.Plan(desc_for(pwf, g128, 1, flags))
+        assert e.value.status == 1
+    with pytest.raises(pwf.PWFError) as e:
+        pwf.Plan(desc_for(pwf, geometry(W2, 1024, 1024), 1, pwf.FLAG_CLUSTER))
+    assert e.value.status == 2
