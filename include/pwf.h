@@ -49,9 +49,12 @@ typedef enum {
   PWF_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
   PWF_ERR_NONFINITE = 5,    /* a non-finite loss was produced */
   PWF_ERR_STATE = 6,        /* state / plan mismatch or bad checkpoint buffer */
-  PWF_ERR_TIMEOUT = 7       /* a device-side wait of the persistent solver ran
+  PWF_ERR_TIMEOUT = 7,      /* a device-side wait of the persistent solver ran
                                out (pwf_plan_set_wait_limit); the GPU context
                                stays usable, psi and the state are not defined */
+  PWF_ERR_BOUNDS = 8        /* bounds-checked builds (PWF_BOUNDS_CHECK): a pass
+                               met an index outside the plan's arrays and
+                               skipped it; results are not defined            */
 } pwf_status;
 
 typedef struct pwf_plan pwf_plan;
@@ -75,6 +78,13 @@ typedef struct pwf_state pwf_state;
                                     square grids of 64, 128, 256 or 512 only, else
                                     PWF_ERR_UNSUPPORTED. At most one of PERSISTENT,
                                     GRAPH and CLUSTER (else PWF_ERR_INVALID_ARG)  */
+#define PWF_FLAG_CHECK_FINITE 0x200u /* debug: after every pass a scan of what it
+                                    wrote; pwf_state_read (and pwf_solve) then
+                                    return PWF_ERR_NONFINITE naming, in
+                                    pwf_plan_last_error, the first pass whose
+                                    output held a NaN or an infinity. Graph
+                                    solver only (PWF_ERR_UNSUPPORTED with
+                                    PERSISTENT or CLUSTER)                        */
 #define PWF_FLAG_NO_PDL 0x100u   /* launch the passes without programmatic dependent
                                     launch (by default each pass is scheduled once
                                     the CTAs of the one before it have exited and
@@ -346,6 +356,21 @@ int32_t pwf_plan_uses_persistent(const pwf_plan* plan);
  * plans. */
 pwf_status pwf_plan_set_cluster_size(pwf_plan* plan, int32_t ctas);
 int32_t pwf_plan_cluster_size(const pwf_plan* plan);
+
+/* Debug aid for the out-of-memory paths: the device allocation `after`
+ * allocations from now (0: the next one) fails as if cudaMalloc had, so the
+ * call making it returns PWF_ERR_NOMEM after freeing what it had allocated. A
+ * negative value turns it off. Process-wide; not thread-safe against
+ * concurrent plan creation. */
+void pwf_debug_fail_alloc(int32_t after);
+
+/* Debug aid for bounds-checked builds (compiled with PWF_BOUNDS_CHECK: every
+ * pass checks the projection index of each CTA against the plan's batch
+ * before touching memory, records PWF_ERR_BOUNDS and skips the work). Runs
+ * one row transform of the plan's work field over one projection more than
+ * the plan holds and synchronises: PWF_ERR_BOUNDS when the checks caught the
+ * extra rows. Other builds launch nothing and return PWF_ERR_UNSUPPORTED. */
+pwf_status pwf_debug_overrun(pwf_plan* plan);
 
 /* Forward model for callers that cannot allocate device memory. The paper has
  * no counterpart: this is an interface choice, not part of the method.

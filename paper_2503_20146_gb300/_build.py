@@ -34,26 +34,35 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libpwf.so; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+LIB_BOUNDS_CHECK = os.path.join(LIBDIR, "libpwf_bc.so")
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, bounds_check: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libpwf.so; returns its path.
+    bounds_check=True builds libpwf_bc.so instead, with PWF_BOUNDS_CHECK
+    defined: every pass checks its projection index against the plan before
+    touching memory (PWF_ERR_BOUNDS), at the same arithmetic."""
+    lib = LIB_BOUNDS_CHECK if bounds_check else LIB
+    objdir = os.path.join(OBJDIR, "bounds_check") if bounds_check else OBJDIR
+    extra = ["-DPWF_BOUNDS_CHECK"] if bounds_check else []
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *inc, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src).replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *extra, *inc, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -64,13 +73,13 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     jobs = jobs or max(1, min(len(sources()), os.cpu_count() or 4))
     with ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -9,7 +9,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
 #include <new>
 #include <vector>
 
@@ -417,6 +420,8 @@ struct pwf_plan {
   double* gpart = nullptr;       // [persist_grid][B][NACC]
   unsigned* bar = nullptr;       // grid barrier words
   PersistPhase* phases = nullptr;  // device copy of the iteration's passes
+  int* scan_word = nullptr;      // PWF_FLAG_CHECK_FINITE: id of the first pass that wrote a NaN or inf (-1: none)
+  std::vector<const char*> scan_names;  // pass names by id
   int cluster = 0;               // cluster-resident variant: CTAs per cluster (0: not used)
   DevIter* cit = nullptr;        // [B] per-projection iteration records of that variant
 };
@@ -445,10 +450,17 @@ pwf_status cuda_fail(pwf_plan* p, cudaError_t e, const char* where) {
     if (e__ != cudaSuccess) return cuda_fail((p), e__, #call); \
   } while (0)
 
+// pwf_debug_fail_alloc: the allocation that many allocations from now fails
+std::atomic<int> g_fail_alloc{-1};
+
 template <class T>
 pwf_status dalloc(pwf_plan* p, T** ptr, size_t count) {
   void* q = nullptr;
   if (count == 0) count = 1;
+  int left = g_fail_alloc.load();
+  while (left >= 0 && !g_fail_alloc.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 0) return fail(p, PWF_ERR_NOMEM, "device allocation failed (pwf_debug_fail_alloc)");
   cudaError_t e = cudaMalloc(&q, count * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -560,7 +572,9 @@ cudaError_t enqueue(pwf_plan* p, const char* name, F&& launch) {
     e1 = p->ev_pool[p->prof_n + 1];
     cudaEventRecord(e0, p->stream);
   }
+  nvtxRangePushA(name);
   cudaError_t e = launch();
+  nvtxRangePop();
   p->launches++;
   if (p->prof) {
     cudaEventRecord(e1, p->stream);
@@ -599,18 +613,55 @@ PassArgs colq_args(const pwf_plan* p, PassArgs a, int which, int conj) {
 }
 
 // row pass on axis x, column pass on axis y
+// PWF_FLAG_CHECK_FINITE: after every pass a scan of what it wrote; the first
+// pass (in stream order) whose output holds a NaN or an infinity leaves its id
+__global__ void k_scan_finite(const float* v, size_t n, int id, int* word) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(word, -1, id);
+}
+
+cudaError_t scan_output(pwf_plan* p, const char* name, const void* ptr, int proj0, int nproj, int floats_per_px) {
+  if (!p->scan_word || !ptr) return cudaSuccess;
+  int id = 0;
+  while (id < (int)p->scan_names.size() && std::strcmp(p->scan_names[id], name) != 0) id++;
+  if (id == (int)p->scan_names.size()) p->scan_names.push_back(name);
+  const size_t px = (size_t)p->d.ny * p->d.nx;
+  const float* v = static_cast<const float*>(ptr) + (size_t)proj0 * px * floats_per_px;
+  const size_t n = (size_t)nproj * px * floats_per_px;
+  return enqueue(p, "scan_finite", [&] {
+    k_scan_finite<<<grid_for(n), 256, 0, p->stream>>>(v, n, id, p->scan_word);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t scan_pass(pwf_plan* p, const char* name, const PassArgs& a, int nproj, int op, bool is_row) {
+  if (!p->scan_word) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (is_row && (op == ROW_REAL_OUT || op == ROW_INTENSITY_OUT)) return scan_output(p, name, a.f_out, a.proj0, nproj, 1);
+  if (is_row && op == ROW_GRAD_OUT) return scan_output(p, name, a.g_out, a.proj0, nproj, 2);
+  if ((e = scan_output(p, name, a.out, a.proj0, nproj, 2)) != cudaSuccess) return e;
+  if (is_row && (op == ROW_NESTEROV_FFT || op == ROW_NESTEROV)) e = scan_output(p, name, a.psi_out, a.proj0, nproj, 2);
+  return e;
+}
+
 cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
   a = row_args(p, a);
-  return enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
+  cudaError_t e = enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
+  return e != cudaSuccess ? e : scan_pass(p, kRowNames[op], a, nproj, op, true);
 }
 cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a = col_args(p, a);
-  return enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
+  cudaError_t e =
+      enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
+  return e != cudaSuccess ? e : scan_pass(p, kColNames[op], a, nproj, op, false);
 }
 cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
   a = colq_args(p, a, which, conj);
-  return enqueue(p, kColNames[COL_Q],
-                 [&] { return p->kcol->colv[COL_Q][p->colsel[COL_Q]].launch(a, nproj, p->stream); });
+  cudaError_t e = enqueue(p, kColNames[COL_Q],
+                          [&] { return p->kcol->colv[COL_Q][p->colsel[COL_Q]].launch(a, nproj, p->stream); });
+  return e != cudaSuccess ? e : scan_pass(p, kColNames[COL_Q], a, nproj, COL_Q, false);
 }
 
 #define LAUNCH(p, expr)                                    \
@@ -727,8 +778,9 @@ cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumu
   a.mode_my = md.my;
   a.mode_w = md.w;
   a.accumulate = accumulate;
-  return enqueue(p, mop == CM_FWD ? "col_mode_fwd" : "col_mode_back",
-                 [&] { return p->kcol->colmode[mop](a, nproj, p->stream); });
+  const char* name = mop == CM_FWD ? "col_mode_fwd" : "col_mode_back";
+  cudaError_t e = enqueue(p, name, [&] { return p->kcol->colmode[mop](a, nproj, p->stream); });
+  return e != cudaSuccess ? e : scan_pass(p, name, a, nproj, -1, false);
 }
 
 // X (F_row{x}) -> X^ = F_y F_row{x} in place: the modes read shifted spectra
@@ -1224,6 +1276,7 @@ const char* pwf_status_string(pwf_status s) {
     case PWF_ERR_NONFINITE: return "PWF_ERR_NONFINITE";
     case PWF_ERR_STATE: return "PWF_ERR_STATE";
     case PWF_ERR_TIMEOUT: return "PWF_ERR_TIMEOUT";
+    case PWF_ERR_BOUNDS: return "PWF_ERR_BOUNDS";
   }
   return "PWF_ERR_UNKNOWN";
 }
@@ -1237,11 +1290,15 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
   if (d.batch < 1 || d.ny < 1 || d.nx < 1 || !(d.pixel_m > 0) || !(d.wavelength_m > 0) || d.L1_m < 0 ||
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
       (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE |
-                   PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER | PWF_FLAG_NO_PDL)))
+                   PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER | PWF_FLAG_NO_PDL |
+                   PWF_FLAG_CHECK_FINITE)))
     return PWF_ERR_INVALID_ARG;
   {
     const uint32_t solver = d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER);
     if (solver & (solver - 1)) return PWF_ERR_INVALID_ARG;  // at most one way to run pwf_solve
+    // the scans follow the passes one by one: not inside a single-launch solver
+    if ((d.flags & PWF_FLAG_CHECK_FINITE) && (d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_CLUSTER)))
+      return PWF_ERR_UNSUPPORTED;
   }
   if (!(d.n_modes == 0 || d.n_modes == 1 || d.n_modes == 9 || d.n_modes == 25) || !(d.mode_sigma_px >= 0.0))
     return PWF_ERR_INVALID_ARG;
@@ -1271,10 +1328,15 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       (r = dalloc(p, &p->V, n)) || (r = dalloc(p, &p->YH, n)) ||
       (r = dalloc(p, &p->acc, (size_t)d.batch * NACC)) || (r = dalloc(p, &p->maxt2, 1)) ||
       (r = dalloc(p, &p->kstatus, 1)) || (r = dalloc(p, &p->loop_ctl, 2)) ||
+      ((d.flags & PWF_FLAG_CHECK_FINITE) && (r = dalloc(p, &p->scan_word, 1))) ||
       (!p->modes.empty() && ((r = dalloc(p, &p->M, n)) || (r = dalloc(p, &p->ACC, n)) ||
                              (r = dalloc(p, &p->IBUF, n))))) {
     pwf_plan_destroy(p);
     return r;
+  }
+  if (p->scan_word && cudaMemset(p->scan_word, 0xff, sizeof(int)) != cudaSuccess) {  // -1: no pass yet
+    pwf_plan_destroy(p);
+    return PWF_ERR_CUDA;
   }
   for (int op = 0; op < NUM_ROW_OPS; op++)
     if (p->krow->row_prep[op]() != cudaSuccess) {
@@ -1598,6 +1660,7 @@ pwf_status pwf_state_reset(pwf_plan* p, pwf_state* s) {
   if (s->B != p->d.batch || s->ny != p->d.ny || s->nx != p->d.nx) return PWF_ERR_STATE;
   PWF_CUDA(p, cudaMemsetAsync(s->phi, 0, (size_t)s->B * s->ny * s->nx * sizeof(float2), p->stream));
   PWF_CUDA(p, cudaMemsetAsync(p->acc, 0, (size_t)s->B * NACC * sizeof(double), p->stream));
+  if (p->scan_word) PWF_CUDA(p, cudaMemsetAsync(p->scan_word, 0xff, sizeof(int), p->stream));  // -1: none yet
   k_state_reset<<<1, 256, 0, p->stream>>>(s->it, s->active, s->iters, s->loss, s->corr, s->B);
   p->launches++;
   PWF_CUDA(p, cudaGetLastError());
@@ -1651,10 +1714,20 @@ pwf_status pwf_state_read(pwf_plan* p, const pwf_state* s, double* loss_host, do
   PWF_CUDA(p, cudaMemcpy(&ks, p->kstatus, sizeof(int), cudaMemcpyDeviceToHost));
   if (ks != 0) {
     cudaMemset(p->kstatus, 0, sizeof(int));
+    if (ks == PWF_ERR_BOUNDS) return fail(p, PWF_ERR_BOUNDS, "an index check of a pass failed");
     return fail(p, PWF_ERR_TIMEOUT, "a bounded wait for a tile copy ran out");
   }
   if (it.status == PWF_ERR_TIMEOUT) return fail(p, PWF_ERR_TIMEOUT, "a grid barrier of the persistent solver ran out");
-  if (it.nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss");
+  if (p->scan_word) {
+    int id = -1;
+    PWF_CUDA(p, cudaMemcpy(&id, p->scan_word, sizeof(int), cudaMemcpyDeviceToHost));
+    if (id >= 0 && id < (int)p->scan_names.size()) {
+      char msg[96];
+      std::snprintf(msg, sizeof(msg), "first non-finite values written by pass %s", p->scan_names[id]);
+      return fail(p, PWF_ERR_NONFINITE, msg);
+    }
+  }
+  if (it.nonfinite) return fail(p, PWF_ERR_NONFINITE, "non-finite loss or iterate");
   return PWF_OK;
 }
 
@@ -1947,6 +2020,30 @@ pwf_status pwf_plan_set_cluster_size(pwf_plan* p, int32_t ctas) {
 }
 
 int32_t pwf_plan_cluster_size(const pwf_plan* p) { return p ? p->cluster : -1; }
+
+void pwf_debug_fail_alloc(int32_t after) { g_fail_alloc.store(after < 0 ? -1 : after); }
+
+pwf_status pwf_debug_overrun(pwf_plan* p) {
+  pwf_status r = check_plan(p);
+  if (r) return r;
+#ifndef PWF_BOUNDS_CHECK
+  return fail(p, PWF_ERR_UNSUPPORTED, "only a bounds-checked build (PWF_BOUNDS_CHECK) runs the overrun check");
+#else
+  // every row of the extra projection fails its index check before any access
+  PassArgs a = base_args(p);
+  a.in = p->X;
+  a.out = p->X;
+  a.pdl = 0;
+  const PassArgs ra = row_args(p, a);
+  PWF_CUDA(p, p->krow->row[ROW_FFT](ra, p->d.batch + 1, p->stream));
+  PWF_CUDA(p, cudaStreamSynchronize(p->stream));
+  int ks = 0;
+  PWF_CUDA(p, cudaMemcpy(&ks, p->kstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  PWF_CUDA(p, cudaMemset(p->kstatus, 0, sizeof(int)));
+  if (ks == PWF_ERR_BOUNDS) return fail(p, PWF_ERR_BOUNDS, "rows beyond the plan's batch were caught and skipped");
+  return ks ? fail(p, (pwf_status)ks, "unexpected status word") : PWF_OK;
+#endif
+}
 
 int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
   if (!p || pass < 0 || pass >= NUM_COL_OPS) return -1;

@@ -130,6 +130,19 @@ struct RowT {
                               : (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) ? 5 : 0;
 };
 
+// A projection a pass leaves alone: retired by the stopping rule, or, in
+// bounds-checked builds (PWF_BOUNDS_CHECK), outside the plan's batch, which
+// also records PWF_ERR_BOUNDS (8) in the status word before any access.
+__device__ __forceinline__ bool skip_proj(const PassArgs& a, int proj) {
+#ifdef PWF_BOUNDS_CHECK
+  if (proj < 0 || proj >= a.B) {
+    if (a.kstatus != nullptr) atomicCAS(a.kstatus, 0, 8);
+    return true;
+  }
+#endif
+  return a.active != nullptr && a.active[proj] == 0;
+}
+
 // Programmatic dependent launch. A pass launched with the programmatic
 // stream-serialization attribute is scheduled as soon as the CTAs of the pass
 // before it have exited, without waiting for that grid's completion to be
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_
   const int rr = tid / TPF, t = tid - rr * TPF;
   const long long row = (long long)blockIdx.x * ROWS + rr + (long long)a.proj0 * a.ny;
   const int proj = (int)(row / a.ny);
-  if (a.active != nullptr && a.active[proj] == 0) return;  // uniform per CTA (ny % ROWS == 0)
+  if (skip_proj(a, proj)) return;  // uniform per CTA (ny % ROWS == 0)
   const RowLayout<TPF, ROWS * TPF> sm{smem + rr * row_smem_len(N), 1 + rr};
   float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   row_body<N, OP>(a, row, t, sm, part);
@@ -571,7 +584,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_t
   const int c = tid % C, t = tid / C;
   const int proj = blockIdx.y + a.proj0;
   const int col = blockIdx.x * C + c;
-  if (a.active != nullptr && a.active[proj] == 0) return;
+  if (skip_proj(a, proj)) return;
   const ColLayout<C> sm{smem + c};
   float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   col_body<N, OP>(a, proj, col, t, sm, part);
@@ -616,7 +629,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_t
   auto prefetch = [&](int tile, float2* buf) {
     int proj, col0;
     const size_t b = tile_base(tile, proj, col0);
-    if (a.active != nullptr && a.active[proj] == 0) return;
+    if (skip_proj(a, proj)) return;
 #pragma unroll
     for (int k = 0; k < CHUNKS / NT; k++) {
       const int q = tid + k * NT;  // chunk q: row q / (C/2), column pair q % (C/2)
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks_op<OP>(col_t
     int proj, col0;
     const size_t base = tile_base(tile, proj, col0) + c;
     const int col = col0 + c;
-    if (a.active != nullptr && a.active[proj] == 0) {
+    if (skip_proj(a, proj)) {
       __syncthreads();
       continue;
     }
@@ -772,7 +785,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
   auto prefetch = [&](int tile, float2* buf) {
     int proj, col0;
     const size_t b = tile_base(tile, proj, col0);
-    if (a.active != nullptr && a.active[proj] == 0) return;
+    if (skip_proj(a, proj)) return;
 #pragma unroll
     for (int k = 0; k < CHUNKS / NT; k++) {
       const int q = tid + k * NT;  // chunk q: row q / (C/2), column pair q % (C/2)
@@ -802,7 +815,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const 
     int proj, col0;
     const size_t base = tile_base(tile, proj, col0) + 2 * c2;
     const int col = col0 + 2 * c2;
-    if (a.active != nullptr && a.active[proj] == 0) {
+    if (skip_proj(a, proj)) {
       __syncthreads();
       continue;
     }
@@ -941,7 +954,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_tma2(const _
   for (int tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
     const int proj = a.proj0 + tile_i / tiles_per_proj;
     const int col0 = (tile_i % tiles_per_proj) * C;
-    if (a.active != nullptr && a.active[proj] == 0) continue;  // uniform per CTA
+    if (skip_proj(a, proj)) continue;  // uniform per CTA
     if (tid == 0) {
       fence_proxy_async_shared();  // the previous tile's exchanges precede the copy
       mbar_arrive_expect_tx(&bar, TILE_BYTES);
@@ -1025,7 +1038,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
   auto prefetch = [&](int tile, float2* buf) {
     int proj, col0;
     const size_t b = tile_base(tile, proj, col0);
-    if (a.active != nullptr && a.active[proj] == 0) return;
+    if (skip_proj(a, proj)) return;
 #pragma unroll 8
     for (int k = 0; k < ELEMS / NT; k++) {
       const int q = tid + k * NT;  // row-major over the tile: row q / C, column q % C
@@ -1048,7 +1061,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 
     int proj, col0;
     const size_t tb = tile_base(tile, proj, col0);
-    if (a.active != nullptr && a.active[proj] == 0) {
+    if (skip_proj(a, proj)) {
       __syncthreads();
       continue;
     }
@@ -1120,7 +1133,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
   const int c = tid % C, t = tid / C;
   const int proj = blockIdx.y + a.proj0;
   const int col = blockIdx.x * C + c;
-  if (a.active != nullptr && a.active[proj] == 0) return;
+  if (skip_proj(a, proj)) return;
   const int shifted = ((col - a.mode_mx) % a.nx + a.nx) % a.nx;
   const size_t pb = (size_t)proj * a.ny * a.nx;
   const size_t ld = (size_t)a.nx;
@@ -1170,7 +1183,7 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
   const int c2 = tid % (C / 2), t = tid / (C / 2);
   const int proj = blockIdx.y + a.proj0;
   const int col = blockIdx.x * C + 2 * c2;  // the thread's aligned pair of columns
-  if (a.active != nullptr && a.active[proj] == 0) return;
+  if (skip_proj(a, proj)) return;
   // the other pair: CM_FWD reads columns col - mx, CM_BACK reads col + mx
   // (and writes the aligned pair), so the read-modify-write of the
   // accumulated spectrum stays 16-byte aligned

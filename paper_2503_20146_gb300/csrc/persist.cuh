@@ -169,7 +169,7 @@ __device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, 
   for (long long it = i0 + gw; it < items; it += GW) {
     const long long row = it * RPW + sub;
     const int proj = (int)((it * RPW) / a.ny);
-    if (a.active != nullptr && a.active[proj] == 0) continue;  // uniform per warp
+    if (skip_proj(a, proj)) continue;  // uniform per warp
     float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     row_body<N, OP>(a, row, t, sm, part);
     if constexpr (RowT<OP>::nred == 1) {
@@ -200,7 +200,7 @@ __device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, 
     const long long cg = it * CPW;
     const int proj = (int)(cg / a.nx);
     const int col = (int)(cg - (long long)proj * a.nx) + c;
-    if (a.active != nullptr && a.active[proj] == 0) continue;
+    if (skip_proj(a, proj)) continue;
     float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     col_body<N, OP>(a, proj, col, t, sm, part);
     if constexpr (OP == COL_RESID_IOTF2) {

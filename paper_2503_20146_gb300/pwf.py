@@ -25,9 +25,11 @@ FLAG_PERSISTENT = 0x20
 FLAG_GRAPH = 0x40
 FLAG_CLUSTER = 0x80
 FLAG_NO_PDL = 0x100
+FLAG_CHECK_FINITE = 0x200
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
-          4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE", 7: "PWF_ERR_TIMEOUT"}
+          4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE", 7: "PWF_ERR_TIMEOUT",
+          8: "PWF_ERR_BOUNDS"}
 
 SIZES = (16, 32, 64, 96, 128, 256, 512, 768, 1024, 1536, 2048)
 
@@ -71,7 +73,14 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _LIB_PATH
+    _lib = open_library(path or _LIB_PATH)
+    return _lib
+
+
+def open_library(path: str):
+    """A separately loaded build of the library (for instance the
+    bounds-checked one), with the same signatures; the module's own calls keep
+    using the library load() returns."""
     if not os.path.exists(path):
         raise RuntimeError(f"libpwf.so is not built ({path}); run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
@@ -115,12 +124,13 @@ def load(path: str | None = None):
         "pwf_plan_uses_persistent": ([_P], i32),
         "pwf_plan_set_cluster_size": ([_P, i32], i32),
         "pwf_plan_cluster_size": ([_P], i32),
+        "pwf_debug_fail_alloc": ([i32], None),
+        "pwf_debug_overrun": ([_P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = lib
     return lib
 
 
@@ -247,6 +257,11 @@ def pwf_plan_set_cluster_size(plan, ctas: int):
 
 def pwf_plan_cluster_size(plan) -> int:
     return int(load().pwf_plan_cluster_size(plan))
+
+
+def pwf_debug_fail_alloc(after: int):
+    """Make the device allocation `after` allocations from now fail (< 0: off)."""
+    load().pwf_debug_fail_alloc(int(after))
 
 
 def pwf_gradient(plan, psi, t, y, g, loss=None):

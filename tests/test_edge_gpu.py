@@ -118,3 +118,62 @@ def test_misaligned_device_arrays_are_rejected_before_any_work(pwf):
         # nothing was queued: the plan still solves
         it, _ = plan.solve(y, td, psi, 2)
         assert list(it) == [2]
+
+
+# ---------------------------------------------------------------------------
+# debug aids: the non-finite scan and the allocation-failure hook
+# ---------------------------------------------------------------------------
+def _flagged_plan(P, g, batch, flags):
+    return P.Plan(P.PlanDesc(batch, g.ny, g.nx, g.pixel, g.wavelength, g.L1, g.L2, g.xcoh, g.ycoh, g.gamma,
+                             g.alpha.real, g.alpha.imag, g.eta, flags))
+
+
+@pytest.mark.parametrize("where,first", [("t", "row_mul_t"), ("psi", "row_exp_fft")])
+def test_check_finite_names_the_first_pass_with_bad_output(pwf, where, first):
+    # one NaN pixel in the diffuser first shows in the output of the diffuser
+    # multiply; one in the starting iterate, in exp(psi) of the first pass
+    g = geometry(W2, 128, 128)
+    psi0, t = blob_batch(W2, 1, 128, 128)
+    psi0, t = to_c64(psi0).copy(), to_c64(t).copy()
+    if where == "t":
+        t[40, 17] = np.nan
+    else:
+        psi0[0, 40, 17] = np.nan
+    y = dev(to_f32(np.ones((1, 128, 128))))
+    with _flagged_plan(pwf, g, 1, pwf.FLAG_CHECK_FINITE) as plan:
+        with pytest.raises(pwf.PWFError) as e:
+            plan.solve(y, dev(t), dev(psi0), 2)
+        assert e.value.status == 5 and f"pass {first}" in str(e.value)
+    with _flagged_plan(pwf, g, 1, 0) as plan:      # without the scan: only that something went non-finite
+        with pytest.raises(pwf.PWFError) as e:
+            plan.solve(y, dev(t), dev(psi0), 2)
+        assert e.value.status == 5 and "pass" not in str(e.value)
+
+
+def test_check_finite_passes_clean_input_bitwise(pwf):
+    g = geometry(W2, 128, 128)
+    psi0, t = blob_batch(W2, 1, 128, 128)
+    y = dev(to_f32(np.ones((1, 128, 128))))
+    out = []
+    for flags in (pwf.FLAG_CHECK_FINITE, 0):
+        with _flagged_plan(pwf, g, 1, flags) as plan:
+            psi = torch.zeros((1, 128, 128), dtype=torch.complex64, device="cuda")
+            plan.solve(y, dev(to_c64(t)), psi, 4)
+            out.append(psi.cpu())
+    assert torch.equal(out[0], out[1])
+
+
+def test_failed_allocation_returns_nomem_and_frees_the_rest(pwf):
+    g = geometry(W2, 256, 256)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (0, 3, 9):
+        pwf.pwf_debug_fail_alloc(k)
+        with pytest.raises(pwf.PWFError) as e:
+            _flagged_plan(pwf, g, 4, 0)
+        assert e.value.status == 3
+    pwf.pwf_debug_fail_alloc(-1)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)   # nothing of the failed plans is left
+    with _flagged_plan(pwf, g, 4, 0) as plan:                  # and the next plan is whole
+        assert plan.handle
