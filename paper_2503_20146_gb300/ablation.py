@@ -110,8 +110,9 @@ def make_series(n_angles: int = 48, n: int = 256, delta_max: float = 2e-7, photo
 
 
 def plan_desc(w: S.Workload, s: Setting) -> P.PlanDesc:
+    # every setting on the untuned column shapes: settings differ only in what they switch
     return P.PlanDesc(w.batch, w.ny, w.nx, w.pixel_m, w.wavelength_m, w.L1_m, w.L2_m, w.xcoh_m, w.ycoh_m,
-                      s.gamma, s.alpha.real, s.alpha.imag, w.eta, s.flags)
+                      s.gamma, s.alpha.real, s.alpha.imag, w.eta, s.flags | P.FLAG_NO_TUNE)
 
 
 def run_setting(series: Series, s: Setting, iters: int):

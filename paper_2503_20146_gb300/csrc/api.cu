@@ -311,6 +311,33 @@ __global__ void k_nesterov_plain(const float* __restrict__ reg, const float2* __
   }
 }
 
+// Twiddle table of the length-n transform with forward radices r[0..s) in
+// direction D (the inverse runs them reversed), in the layout the stage
+// runner reads: stage k >= 1 of radix R after NS points holds W^(q j), q =
+// 1..R-1, j < NS, at (sum of (R_i - 1) NS_i over the stages 1..k-1) + (q - 1)
+// NS + j; computed in double precision and rounded once.
+bool host_twiddles_radices(int n, const int* r, int s, int D, std::vector<float2>& tab) {
+  auto radix = [&](int k) { return D == FWD ? r[k] : r[s - 1 - k]; };
+  int prod = 1;
+  for (int k = 0; k < s; k++) prod *= radix(k);
+  if (prod != n) return false;
+  size_t len = 0;
+  for (int k = 1, ns = radix(0); k < s; ns *= radix(k), k++) len += (size_t)(radix(k) - 1) * ns;
+  tab.assign(len > 0 ? len : 1, make_float2(1.f, 0.f));
+  size_t off = 0;
+  for (int k = 1, ns = radix(0); k < s; ns *= radix(k), k++) {
+    const int R = radix(k);
+    for (int q = 1; q < R; q++)
+      for (int j = 0; j < ns; j++) {
+        const long m = ((long)q * j) % ((long)ns * R);
+        const double ang = 2.0 * M_PI * (double)m / (double)(ns * R);
+        tab[off + (size_t)(q - 1) * ns + j] = make_float2((float)std::cos(ang), (float)(D * std::sin(ang)));
+      }
+    off += (size_t)(R - 1) * ns;
+  }
+  return true;
+}
+
 // Twiddle table of the length-n transform in direction D, in the layout the
 // stage runner reads (stage k >= 1 of radix R after NS points: W^(r j) at
 // stage_twoff + (r - 1) NS + j), computed in double precision.
@@ -342,6 +369,8 @@ struct AxisTables {
   int n = 0;
   float2* tw_fwd = nullptr;
   float2* tw_inv = nullptr;
+  float2* tw_fwd_alt = nullptr;  // twiddles of the alternative radix schedule (column shapes built with it)
+  float2* tw_inv_alt = nullptr;
   float2* q1 = nullptr;  // exp(i phi_{L1}) restricted to this axis
   float2* q2 = nullptr;
   float* iotf = nullptr;
@@ -509,6 +538,15 @@ pwf_status build_axis(pwf_plan* p, AxisTables& A, int n, double pixel, double co
     return r;
   PWF_CUDA(p, cudaMemcpy(A.tw_fwd, twf.data(), tlf * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.tw_inv, twi.data(), tli * sizeof(float2), cudaMemcpyHostToDevice));
+  if (const LengthKernels* k = kernels_for_length(n); k && k->sched_stages[1] > 0) {
+    std::vector<float2> af, ai;
+    if (!host_twiddles_radices(n, k->sched_radix[1], k->sched_stages[1], FWD, af) ||
+        !host_twiddles_radices(n, k->sched_radix[1], k->sched_stages[1], INV, ai))
+      return fail(p, PWF_ERR_UNSUPPORTED, "alternative twiddle table layout");
+    if ((r = dalloc(p, &A.tw_fwd_alt, af.size())) || (r = dalloc(p, &A.tw_inv_alt, ai.size()))) return r;
+    PWF_CUDA(p, cudaMemcpy(A.tw_fwd_alt, af.data(), af.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    PWF_CUDA(p, cudaMemcpy(A.tw_inv_alt, ai.data(), ai.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   PWF_CUDA(p, cudaMemcpy(A.q1, q1.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.q2, q2.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
   PWF_CUDA(p, cudaMemcpy(A.iotf, io.data(), n * sizeof(float), cudaMemcpyHostToDevice));
@@ -651,14 +689,21 @@ cudaError_t row(pwf_plan* p, int op, PassArgs a, int nproj) {
   cudaError_t e = enqueue(p, kRowNames[op], [&] { return p->krow->row[op](a, nproj, p->stream); });
   return e != cudaSuccess ? e : scan_pass(p, kRowNames[op], a, nproj, op, true);
 }
+// the column-axis twiddles of the radix schedule a column shape was built with
+PassArgs sched_tables(const pwf_plan* p, PassArgs a, int sched) {
+  a.tw_fwd = sched == 1 ? p->ay.tw_fwd_alt : p->ay.tw_fwd;
+  a.tw_inv = sched == 1 ? p->ay.tw_inv_alt : p->ay.tw_inv;
+  return a;
+}
+
 cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
-  a = col_args(p, a);
+  a = sched_tables(p, col_args(p, a), p->kcol->colv[op][p->colsel[op]].sched);
   cudaError_t e =
       enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
   return e != cudaSuccess ? e : scan_pass(p, kColNames[op], a, nproj, op, false);
 }
 cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {
-  a = colq_args(p, a, which, conj);
+  a = sched_tables(p, colq_args(p, a, which, conj), p->kcol->colv[COL_Q][p->colsel[COL_Q]].sched);
   cudaError_t e = enqueue(p, kColNames[COL_Q],
                           [&] { return p->kcol->colv[COL_Q][p->colsel[COL_Q]].launch(a, nproj, p->stream); });
   return e != cudaSuccess ? e : scan_pass(p, kColNames[COL_Q], a, nproj, COL_Q, false);
@@ -1135,15 +1180,16 @@ pwf_status tune_columns(pwf_plan* p) {
     float best = 1e30f;
     for (int v = 0; v < p->kcol->ncolv[op] && err == cudaSuccess; v++) {
       const PassFn fn = p->kcol->colv[op][v].launch;
-      if (p->kcol->colv[op][v].pipe == 5 && fn(a, a.B, p->stream) != cudaSuccess) {
+      const PassArgs av = sched_tables(p, a, p->kcol->colv[op][v].sched);
+      if (p->kcol->colv[op][v].pipe == 5 && fn(av, a.B, p->stream) != cudaSuccess) {
         // a TMA shape whose tensor map the driver would not encode: not offered
         cudaGetLastError();
         p->coltime[op][v] = 1e30f;
         continue;
       }
-      if ((err = fn(a, a.B, p->stream)) != cudaSuccess) break;
+      if ((err = fn(av, a.B, p->stream)) != cudaSuccess) break;
       cudaEventRecord(e0, p->stream);
-      for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) err = fn(a, a.B, p->stream);
+      for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) err = fn(av, a.B, p->stream);
       cudaEventRecord(e1, p->stream);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -2062,29 +2108,36 @@ pwf_status pwf_plan_set_column_shape(pwf_plan* p, int32_t pass, int32_t shape) {
 
 size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   if (!p) return 0;
-  char tmp[2048];
+  char tmp[8192];
   size_t o = 0;
-  auto shape = [&](const ColVariant& v) {
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, "C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+  // appends while room is left (a longer description is cut, never overrun)
+  auto put = [&](const char* fmt, auto... args) {
+    if (o >= sizeof(tmp) - 1) return;
+    const int w = std::snprintf(tmp + o, sizeof(tmp) - o, fmt, args...);
+    if (w > 0) o = std::min(sizeof(tmp) - 1, o + (size_t)w);
   };
-  o += std::snprintf(tmp + o, sizeof(tmp) - o, "ny=%d nx=%d batch=%d solver=%s loop=%s", p->d.ny, p->d.nx,
-                     p->d.batch, p->cluster > 0 ? "cluster" : p->persist ? "persistent" : "graph",
-                     p->persist || p->cluster > 0 ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
-  if (p->cluster > 0) o += std::snprintf(tmp + o, sizeof(tmp) - o, " cluster_ctas=%d", p->cluster);
-  for (int op = 0; op < NUM_COL_OPS && o < sizeof(tmp) - 64; op++) {
-    o += std::snprintf(tmp + o, sizeof(tmp) - o, " %s=", kColNames[op]);
+  auto shape = [&](const ColVariant& v) {
+    put("C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+    if (v.sched == 1)  // built with the alternative radix schedule: its radices
+      for (int i = 0; i < p->kcol->sched_stages[1]; i++) put("%s%d", i ? "." : "@", p->kcol->sched_radix[1][i]);
+  };
+  tmp[0] = 0;
+  put("ny=%d nx=%d batch=%d solver=%s loop=%s", p->d.ny, p->d.nx, p->d.batch,
+      p->cluster > 0 ? "cluster" : p->persist ? "persistent" : "graph",
+      p->persist || p->cluster > 0 ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
+  if (p->cluster > 0) put(" cluster_ctas=%d", p->cluster);
+  for (int op = 0; op < NUM_COL_OPS; op++) {
+    put(" %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);
     if (p->coltime[op][0] > 0.f) {  // tuned: all candidates with their times
-      o += std::snprintf(tmp + o, sizeof(tmp) - o, "[");
-      for (int v = 0; v < p->kcol->ncolv[op] && o < sizeof(tmp) - 32; v++) {
+      put("[");
+      for (int v = 0; v < p->kcol->ncolv[op]; v++) {
         shape(p->kcol->colv[op][v]);
-        o += std::snprintf(tmp + o, sizeof(tmp) - o, ":%.3f%s", p->coltime[op][v], v + 1 < p->kcol->ncolv[op] ? "," : "]");
+        put(":%.3f%s", p->coltime[op][v], v + 1 < p->kcol->ncolv[op] ? "," : "]");
       }
     }
   }
-  if (buf && len) {
-    std::snprintf(buf, len, "%s", tmp);
-  }
+  if (buf && len) std::snprintf(buf, len, "%s", tmp);
   return std::strlen(tmp) + 1;
 }
 

@@ -21,7 +21,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Radix schedule set of this translation unit: 0 (the default, every pass)
+// or 1 (the alternative schedules some column shapes are also built with, in
+// translation units of their own). Everything schedule-dependent lives in the
+// inline namespace named after the set, so both sets link side by side.
+#ifndef PWF_SCHED_VARIANT
+#define PWF_SCHED_VARIANT 0
+#endif
+#if PWF_SCHED_VARIANT == 0
+#define PWF_KNS sched0
+#else
+#define PWF_KNS sched1
+#endif
+
 namespace pwf {
+inline namespace PWF_KNS {
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -239,27 +253,54 @@ __device__ __forceinline__ void dft(float2* x) {
 // compile-time radix schedules (forward order; the inverse runs them reversed)
 // ---------------------------------------------------------------------------
 struct Sched {
-  int n, s, r0, r1, r2, r3;
-  __host__ __device__ constexpr int r(int i) const { return i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : r3; }
+  int n, s, r0, r1, r2, r3, r4;
+  __host__ __device__ constexpr int r(int i) const {
+    return i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : i == 3 ? r3 : r4;
+  }
 };
 
-__host__ __device__ constexpr Sched sched_for(int n) {
+// The alternative schedules (set 1): the same stages in another order where
+// that keeps the values per thread, or smaller radices where it halves them
+// (fewer registers per transform, more warps per SM, one more exchange).
+__host__ __device__ constexpr Sched sched_alt(int n) {
   switch (n) {
-    case 16: return {16, 1, 16, 1, 1, 1};
-    case 32: return {32, 2, 8, 4, 1, 1};
-    case 64: return {64, 2, 8, 8, 1, 1};
-    case 96: return {96, 3, 8, 4, 3, 1};
-    case 128: return {128, 2, 16, 8, 1, 1};
-    case 192: return {192, 3, 8, 8, 3, 1};
-    case 256: return {256, 2, 16, 16, 1, 1};
-    case 384: return {384, 4, 8, 8, 2, 3};
-    case 512: return {512, 3, 16, 8, 4, 1};
-    case 768: return {768, 4, 8, 8, 4, 3};
-    case 1024: return {1024, 3, 16, 8, 8, 1};
-    case 1536: return {1536, 4, 8, 8, 8, 3};
-    case 2048: return {2048, 3, 16, 16, 8, 1};
-    default: return {0, 0, 1, 1, 1, 1};
+    case 128: return {128, 3, 4, 4, 8, 1, 1};
+    case 256: return {256, 3, 4, 8, 8, 1, 1};
+    case 512: return {512, 3, 8, 8, 8, 1, 1};
+    case 768: return {768, 5, 4, 4, 4, 4, 3};
+    case 1024: return {1024, 3, 8, 8, 16, 1, 1};
+    case 2048: return {2048, 3, 8, 16, 16, 1, 1};
+    default: return {0, 0, 1, 1, 1, 1, 1};
   }
+}
+
+__host__ __device__ constexpr Sched sched_default(int n) {
+  switch (n) {
+    case 16: return {16, 1, 16, 1, 1, 1, 1};
+    case 32: return {32, 2, 8, 4, 1, 1, 1};
+    case 64: return {64, 2, 8, 8, 1, 1, 1};
+    case 96: return {96, 3, 8, 4, 3, 1, 1};
+    case 128: return {128, 2, 16, 8, 1, 1, 1};
+    case 192: return {192, 3, 8, 8, 3, 1, 1};
+    case 256: return {256, 2, 16, 16, 1, 1, 1};
+    case 384: return {384, 4, 8, 8, 2, 3, 1};
+    case 512: return {512, 3, 16, 8, 4, 1, 1};
+    case 768: return {768, 4, 8, 8, 4, 3, 1};
+    case 1024: return {1024, 3, 16, 8, 8, 1, 1};
+    case 1536: return {1536, 4, 8, 8, 8, 3, 1};
+    case 2048: return {2048, 3, 16, 16, 8, 1, 1};
+    default: return {0, 0, 1, 1, 1, 1, 1};
+  }
+}
+
+// the schedule of length n in this translation unit's set (set 1 falls back to
+// the default for lengths without an alternative)
+__host__ __device__ constexpr Sched sched_for(int n) {
+#if PWF_SCHED_VARIANT == 1
+  return sched_alt(n).s > 0 ? sched_alt(n) : sched_default(n);
+#else
+  return sched_default(n);
+#endif
 }
 
 __host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
@@ -533,4 +574,5 @@ __device__ __forceinline__ int slot_index(int t, int j) {
   return t + (j / R) * TPF + (j % R) * (N / R);
 }
 
+}  // namespace PWF_KNS
 }  // namespace pwf

@@ -14,9 +14,13 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "fft.cuh"
+#include "pass_types.h"
 
 namespace pwf {
+inline namespace PWF_KNS {
 
 // ---------------------------------------------------------------------------
 // launch shapes
@@ -30,96 +34,8 @@ __host__ __device__ constexpr size_t row_smem_bytes(int n) {
   return (size_t)rows_for(n) * row_smem_len(n) * sizeof(float2);
 }
 
-// per-projection accumulators (float64)
-enum Acc : int { ACC_LOSS = 0, ACC_XR = 1, ACC_XI = 2, ACC_XNEW = 3, ACC_XOLD = 4, NACC = 8 };
 
-// ---------------------------------------------------------------------------
-// pass arguments (one struct for every pass; unused fields are null)
-// ---------------------------------------------------------------------------
-struct PassArgs {
-  int B, ny, nx;
-  const float2* in;        // primary input (in-place passes: in == out)
-  float2* out;             // primary output
-  const float2* tw_fwd;    // twiddles of this pass's axis
-  const float2* tw_inv;
-  // fields
-  const float2* psi;       // complex phase psi (read)
-  float2* psi_out;         // psi after the Nesterov update
-  float2* phi;             // phi_prev in, phi out (Nesterov)
-  const float2* t;         // diffuser [ny][nx]
-  const float* y;          // measurement
-  float2* v;               // detector field v (written by ROW_INTENSITY, read by ROW_MUL_V)
-  float2* u1;              // P1{x} (stored for the diffuser gradient)
-  float2* aux;             // second output (ROW_GRAD_PACK: F_row{Im g})
-  const float2* aux_in;    // second input (COL_PRECOND_REG)
-  float* reg;              // Re g
-  float* f_out;            // real output (forward model)
-  float2* g_out;           // complex output (gradient)
-  float2* gt_scratch;      // per-projection diffuser-gradient terms
-  const float* maxt2;      // device scalar max |t|^2
-  double* acc;             // [B][NACC]
-  const int* active;       // [B] convergence flags (null: all active)
-  const float* beta;       // device scalar Nesterov coefficient (mu_prev - 1)/mu
-  // column-pass filter tables (length nx for *x, ny for *y)
-  const float2* qx;
-  const float2* qy;
-  const float* ix;         // IOTF factors
-  const float* iy;
-  const float* u2x;        // squared frequency, cycles/pixel
-  const float* u2y;
-  const float* ex;         // STF - 1 along x (and y): exp(-pi gamma u^2 xcoh^2) - 1, Eq. (14)
-  const float* ey;
-  const float2* yhat;      // 2-D spectrum of y
-  float scale;             // 1/(nx ny), the inverse-transform normalisation
-  float eta;
-  float alpha_re, alpha_im;
-  float gscale;            // ROW_GRAD_OUT: extra factor
-  int conj_q;              // use conj(Q): back-propagation P(-L)
-  int conj_t;              // multiply by conj(t)
-  int div_maxt2;           // ROW_GRAD_OUT / PACK: divide by max|t|^2
-  int no_precond;          // P^-1 := 1
-  int proj0;               // first projection of this launch (plain path)
-  // source-mode variant: tilt bins, weight, accumulate flag
-  int mode_mx, mode_my;
-  float mode_w;
-  int accumulate;
-  int* kstatus;            // device word set to PWF_ERR_TIMEOUT (7) when a bounded wait runs out
-  int pdl;                 // launch with the programmatic stream-serialization attribute
-  CUtensorMap tmap;        // TMA map of `in` (filled by the launcher of a TMA-staged shape)
-};
 
-enum RowOp : int {
-  ROW_EXP_FFT = 0,     // x = exp(psi) -> FFT                           (first pass)
-  ROW_REAL_FFT,        // y (real) -> FFT                                (F{y})
-  ROW_FFT,             // complex field -> FFT                           (plain)
-  ROW_IFFT,            // IFFT -> complex field                          (plain)
-  ROW_MUL_T,           // IFFT -> [store u1] -> * t (or conj t) -> FFT
-  ROW_INTENSITY,       // IFFT -> v (stored) -> |v|^2 -> FFT
-  ROW_INTENSITY_OUT,   // IFFT -> f = |v|^2                              (coherent forward)
-  ROW_REAL_OUT,        // IFFT -> f = Re                                 (IOTF forward)
-  ROW_RESID,           // IFFT -> f = Re; e = y - f; loss; -e -> FFT
-  ROW_COH_RESID,       // IFFT -> v; e = y - |v|^2; loss; v * (-e) -> FFT   (coherent)
-  ROW_COH_VJP,         // IFFT -> v; v * grad_f -> FFT                   (coherent VJP)
-  ROW_MUL_V,           // IFFT -> G = Re; v * G -> FFT
-  ROW_GRAD_OUT,        // IFFT -> g = conj(exp psi) g1 * scale -> g_out
-  ROW_GRAD_PACK,       // IFFT -> g; store Re g; FFT(alpha o psi) -> out, FFT(Im g) -> aux
-  ROW_NESTEROV_FFT,    // IFFT -> Nesterov update; exp(psi_new) -> FFT
-  ROW_NESTEROV,        // IFFT -> Nesterov update
-  ROW_GRADT,           // IFFT -> g2; scratch (+)= 2 w conj(u1) g2; conj(t) g2 -> FFT
-  ROW_MODE_INT,        // IFFT -> v_j (stored); I (+)= w |v_j|^2          (mode variant)
-  ROW_MODE_VG,         // v_j G (both real-space inputs) -> FFT           (mode variant)
-  NUM_ROW_OPS
-};
-
-enum ColOp : int {
-  COL_Q = 0,           // FFT -> * Q (or conj Q) -> IFFT
-  COL_IOTF,            // FFT -> * IOTF -> IFFT
-  COL_RESID_IOTF2,     // FFT -> R = IOTF I - Y; loss; * IOTF -> IFFT
-  COL_PRECOND_REG,     // FFT(H), FFT(S) -> Gamma^2 H + i P^-1 S -> IFFT
-  COL_FFT,             // FFT only
-  COL_IFFT,            // IFFT only (scaled)
-  NUM_COL_OPS
-};
 
 template <int OP>
 struct RowT {
@@ -1006,7 +922,6 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_tma2(const _
 // The TMA map of a batch of complex64 fields [B][ny][nx] seen as float32
 // [B][ny][2 nx]: box = 2C floats (C columns) x min(ny, 256) rows x 1 field.
 // Encoded on the host through the driver entry point (no libcuda link).
-bool encode_field_tmap(CUtensorMap* m, const void* base, int B, int ny, int nx, int C);
 
 template <int N, int OP, int C>
 __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(N, C), ept_for(N)))
@@ -1117,7 +1032,6 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 // spectral domain; one inverse column pass after the last mode replaces the
 // per-mode inverse transforms and modulations. Reads and writes go to
 // different buffers.
-enum ColModeOp : int { CM_FWD = 0, CM_BACK = 1 };
 
 __device__ __forceinline__ int wrap_sub(int k, int m, int n) { return k >= m ? k - m : k - m + n; }
 
@@ -1241,8 +1155,6 @@ __global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const 
 // ---------------------------------------------------------------------------
 // host-side launch for one transform length
 // ---------------------------------------------------------------------------
-using PassFn = cudaError_t (*)(const PassArgs&, int nproj, cudaStream_t);
-using PrepFn = cudaError_t (*)();
 
 // number of SMs of the current device (persistent grids)
 inline int device_sms() {
@@ -1347,38 +1259,6 @@ struct ColShape {
 template <int N, int OP, int C, int PIPE>
 int ColShape<N, OP, C, PIPE>::resident = 1;
 
-struct PersistArgs;  // persist.cuh
-using PersistFn = cudaError_t (*)(const PersistArgs&, int grid, cudaStream_t);
-using PersistPrepFn = cudaError_t (*)(int batch);
-using PersistOccFn = cudaError_t (*)(int batch, int* per_sm);
-// cluster-resident variant: a grid of batch clusters of `cluster` CTAs
-using PersistClusterFn = cudaError_t (*)(const PersistArgs&, int cluster, cudaStream_t);
-using PersistClusterPrepFn = cudaError_t (*)(int batch, int cluster, int* max_clusters);
-
-struct ColVariant {
-  PassFn launch;
-  PrepFn prep;
-  int C;
-  int pipe;
-};
-constexpr int MAX_COL_VARIANTS = 14;
-
-// tables of launchers for one length, filled by the per-length translation units
-struct LengthKernels {
-  int n;
-  PassFn row[NUM_ROW_OPS];
-  PrepFn row_prep[NUM_ROW_OPS];
-  ColVariant colv[NUM_COL_OPS][MAX_COL_VARIANTS];
-  int ncolv[NUM_COL_OPS];
-  PassFn colmode[2];
-  PrepFn colmode_prep[2];
-  // persistent solver (square grids of the sizes persist_size accepts; null otherwise)
-  PersistFn persist;
-  PersistPrepFn persist_prep;
-  PersistOccFn persist_occupancy;
-  PersistClusterFn persist_cluster;
-  PersistClusterPrepFn persist_cluster_prep;
-};
 
 // the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
 __host__ __device__ constexpr int colmode_c(int n) { return n >= 1024 ? (tpf_for(n) * 8 <= 512 ? 8 : 4) : 16; }
@@ -1423,7 +1303,8 @@ template <int N, int OP, int C, int PIPE>
 void add_col_variant(LengthKernels& k) {
   if constexpr (col_shape_ok<N, OP, C, PIPE>()) {
     int& n = k.ncolv[OP];
-    if (n < MAX_COL_VARIANTS) k.colv[OP][n++] = {ColShape<N, OP, C, PIPE>::launch, ColShape<N, OP, C, PIPE>::prep, C, PIPE};
+    if (n < MAX_COL_VARIANTS)
+      k.colv[OP][n++] = {ColShape<N, OP, C, PIPE>::launch, ColShape<N, OP, C, PIPE>::prep, C, PIPE, PWF_SCHED_VARIANT};
   }
 }
 
@@ -1446,10 +1327,43 @@ void add_col_op(LengthKernels& k) {
   add_col_variant<N, OP, 4, 5>(k);
 }
 
+// the radices of this translation unit's schedule of length N into slot `set`
+template <int N>
+void record_schedule(LengthKernels& k, int set) {
+  constexpr Sched S = sched_for(N);
+  k.sched_stages[set] = S.s;
+  for (int i = 0; i < MAX_SCHED_STAGES; i++) k.sched_radix[set][i] = i < S.s ? S.r(i) : 1;
+}
+
+// Column shapes built with this translation unit's schedule set (1: the
+// alternative) for every column op, appended after the default set's shapes
+// so that the plan-time tuner times both schedules; the shapes that measured
+// best with the default schedule.
+template <int N>
+void add_schedule_shapes(LengthKernels& k) {
+  record_schedule<N>(k, PWF_SCHED_VARIANT);
+  auto op_shapes = [&](auto op_tag) {
+    constexpr int OP = decltype(op_tag)::value;
+    add_col_variant<N, OP, 8, 4>(k);
+    add_col_variant<N, OP, 8, 3>(k);
+    add_col_variant<N, OP, 4, 4>(k);
+    add_col_variant<N, OP, 8, 1>(k);
+    add_col_variant<N, OP, 16, 0>(k);
+    add_col_variant<N, OP, 8, 0>(k);
+  };
+  op_shapes(std::integral_constant<int, COL_Q>{});
+  op_shapes(std::integral_constant<int, COL_IOTF>{});
+  op_shapes(std::integral_constant<int, COL_RESID_IOTF2>{});
+  op_shapes(std::integral_constant<int, COL_PRECOND_REG>{});
+  op_shapes(std::integral_constant<int, COL_FFT>{});
+  op_shapes(std::integral_constant<int, COL_IFFT>{});
+}
+
 template <int N>
 LengthKernels make_length_kernels() {
   LengthKernels k{};
   k.n = N;
+  record_schedule<N>(k, 0);
 #define PWF_ROW(OP)                  \
   k.row[OP] = launch_row<N, OP>;     \
   k.row_prep[OP] = prep_row<N, OP>;
@@ -1471,7 +1385,6 @@ LengthKernels make_length_kernels() {
   return k;
 }
 
-// defined in the per-length translation units
-const LengthKernels* kernels_for_length(int n);
 
+}  // namespace PWF_KNS
 }  // namespace pwf

@@ -23,15 +23,8 @@
 #include "passes.cuh"
 
 namespace pwf {
+inline namespace PWF_KNS {
 
-struct DevIter {
-  double mu;       // mu of Algorithm S1 after the last completed iteration
-  float beta;      // (mu_prev - 1)/mu for the next iteration
-  int iter;        // completed iterations
-  int n_active;    // projections still iterating
-  int nonfinite;   // a non-finite loss was seen
-  int status;      // PWF_OK, or PWF_ERR_TIMEOUT once a device-side wait ran out
-};
 
 // Per-projection end of an iteration from its five sums (loss and the three
 // correlation sums): loss, correlation, iteration count and the stopping rule.
@@ -114,34 +107,8 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, long long 
 // ---------------------------------------------------------------------------
 // persistent solver
 // ---------------------------------------------------------------------------
-enum PersistKind : int { PK_ROW = 0, PK_COL = 1, PK_FINALIZE = 2 };
-constexpr int PERSIST_THREADS = 512;
-constexpr int PERSIST_MAX_PHASES = 16;
 __host__ __device__ constexpr bool persist_size(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
 
-struct PersistPhase {
-  int kind;
-  int op;
-  int flush;   // after this pass, write the CTA's sums of the iteration out
-  PassArgs a;
-};
-
-struct PersistArgs {
-  const PersistPhase* phases;  // device array of nphases
-  int nphases;
-  int B;
-  int max_iter;
-  double corr_tol;
-  double* gpart;               // [gridDim.x][B][NACC] per-CTA partial sums
-  unsigned* bar;               // grid barrier (2 words, zeroed before the launch)
-  long long cap;               // clock64 cycles a barrier may wait
-  int* active;
-  int* iters;
-  double* loss;
-  double* corr;
-  DevIter* it;
-  DevIter* cit;                // [B] per-projection iteration records (cluster-resident variant)
-};
 
 __host__ __device__ constexpr size_t persist_smem_bytes(int n, int batch) {
   return (size_t)(PERSIST_THREADS / 32) * (32 / tpf_for(n)) * row_smem_len(n) * sizeof(float2) +
@@ -497,4 +464,5 @@ LengthKernels with_persist(LengthKernels k) {
   return k;
 }
 
+}  // namespace PWF_KNS
 }  // namespace pwf

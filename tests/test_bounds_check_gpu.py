@@ -3,7 +3,7 @@ it: every pass checks the projection index of each CTA against the plan's
 batch before it touches memory. The checked library is built beside the
 normal one; a row pass over one projection more than the plan holds is caught
 (PWF_ERR_BOUNDS, nothing accessed), the checked build computes the same bits
-as the normal one, and the normal build refuses the overrun without
+as the normal one (both on the untuned column shapes), and the normal build refuses the overrun without
 launching anything."""
 import ctypes
 
@@ -32,7 +32,7 @@ def pwf():
 
 def _desc(P, g, batch):
     return P.PlanDesc(batch, g.ny, g.nx, g.pixel, g.wavelength, g.L1, g.L2, g.xcoh, g.ycoh, g.gamma,
-                      g.alpha.real, g.alpha.imag, g.eta, P.FLAG_GRAPH)
+                      g.alpha.real, g.alpha.imag, g.eta, P.FLAG_GRAPH | P.FLAG_NO_TUNE)
 
 
 def _inputs(g, batch):

@@ -50,7 +50,7 @@ def test_group_matches_individual_solves_and_oracle(pwf):
     for k, (ny, nx, batch, K) in enumerate(CLASSES):
         geom, t, y = _class_inputs(ny, nx, batch, 10 * k)
         d = pwf.PlanDesc(batch, ny, nx, geom.pixel, geom.wavelength, geom.L1, geom.L2, geom.xcoh, geom.ycoh,
-                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta, 0, K, 2.0)
+                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta, pwf.FLAG_NO_TUNE, K, 2.0)
         plans.append(pwf.Plan(d))
         ys.append(dev(y))
         ts.append(dev(t))
@@ -92,7 +92,7 @@ def test_group_chains_large_classes_and_matches_individual_solves(pwf):
     for ny, nx, batch in classes:
         geom = geometry(W2, ny, nx)
         d = pwf.PlanDesc(batch, ny, nx, geom.pixel, geom.wavelength, geom.L1, geom.L2, geom.xcoh, geom.ycoh,
-                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta)
+                         geom.gamma, geom.alpha.real, geom.alpha.imag, geom.eta, pwf.FLAG_NO_TUNE)
         plans.append(pwf.Plan(d))
         ys.append(0.5 + torch.rand((batch, ny, nx), generator=gen, device="cuda"))
         ts.append(dev(to_c64(S.diffuser(ny, nx, S.rng_for(5, ny)))))

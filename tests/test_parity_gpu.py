@@ -170,8 +170,8 @@ def test_programmatic_launch_changes_no_value(pwf):
     # same arithmetic: the iterates agree bit for bit
     geom, t, y = _solve_case(W2, 2, 128, 128)
     out = []
-    for flags in (pwf.FLAG_GRAPH, pwf.FLAG_GRAPH | pwf.FLAG_NO_PDL):
-        with plan_for(pwf, geom, 2, flags) as plan:
+    for flags in (pwf.FLAG_GRAPH, pwf.FLAG_GRAPH | pwf.FLAG_NO_PDL):   # untuned shapes in both plans
+        with plan_for(pwf, geom, 2, flags | pwf.FLAG_NO_TUNE) as plan:
             psi = torch.zeros((2, 128, 128), dtype=torch.complex64, device="cuda")
             plan.solve(dev(y), dev(t), psi, 9)
             out.append(psi.cpu())
@@ -333,8 +333,9 @@ def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
 # ----------------------------------------------------------------------------
 # every column-pass shape the tuner may choose, forced one at a time
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("ny,nx,batch", [(1024, 256, 6), (512, 128, 8), (128, 96, 4), (2048, 64, 2)],
-                         ids=["1024x256", "512x128", "128x96", "2048x64"])
+@pytest.mark.parametrize("ny,nx,batch", [(1024, 256, 6), (512, 128, 8), (128, 96, 4), (2048, 64, 2), (768, 128, 3),
+                                           (256, 64, 5)],
+                         ids=["1024x256", "512x128", "128x96", "2048x64", "768x128", "256x64"])
 def test_every_column_shape_matches_oracle(pwf, ny, nx, batch):
     w = W2
     geom = geometry(w, ny, nx)

@@ -152,7 +152,8 @@ def test_which_plans_take_the_persistent_launch(pwf):
 # cluster-resident launch: one thread-block cluster per projection
 # ---------------------------------------------------------------------------
 def _solve_with(pwf, geom, t, y, n, flags, cluster=None, corr_tol=0.0):
-    with pwf.Plan(desc_for(pwf, geom, y.shape[0], flags)) as plan:
+    # untuned column shapes (F{y} takes one), so that plans compared bit for bit run the same arithmetic
+    with pwf.Plan(desc_for(pwf, geom, y.shape[0], flags | pwf.FLAG_NO_TUNE)) as plan:
         if cluster is not None:
             pwf.pwf_plan_set_cluster_size(plan.handle, cluster)
         psi = torch.zeros((y.shape[0], geom.ny, geom.nx), dtype=torch.complex64, device="cuda")
