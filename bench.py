@@ -77,6 +77,9 @@ def parse_args():
     ap.add_argument("--workload", default="tomo180x1024_iotf")
     ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
+    ap.add_argument("--column-shapes", default=None,
+                    help="comma list of six column-shape indices (one per column op) forced after the plan-time "
+                         "tuning of the main plan, e.g. the column_shape_ids of an earlier line")
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run (plain,e2e,modal,small,mixed,autograd,fbp,ablation,cpu) "
                          "or all")
@@ -218,13 +221,24 @@ def plan_desc(P, w, batch, flags=0, n_modes=None):
                       w.n_modes if n_modes is None else n_modes, w.mode_sigma_px)
 
 
+def selected_shape_ids(describe: str):
+    """Index of the chosen shape of every column op in its candidate list, read
+    from pwf_plan_describe ("op=NAME[NAME:ms,...]"); None where not tuned."""
+    import re
+    ids = []
+    for m in re.finditer(r" col_[a-z0-9_]+=([^\[ ]+)(?:\[([^\]]*)\])?", describe):
+        names = [c.rsplit(":", 1)[0] for c in m.group(2).split(",")] if m.group(2) else []
+        ids.append(names.index(m.group(1)) if m.group(1) in names else None)
+    return ids
+
+
 def source_hash():
     """Hash of the files that define the pass kernels (templates and their
     per-length instantiations): stored DRAM counters stay valid while it holds."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2503_20146_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if not (name in ("fft.cuh", "passes.cuh") or name.startswith("len_")):
+        if not (name in ("fft.cuh", "passes.cuh", "pass_types.h") or name.startswith("len_")):
             continue
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())
@@ -493,16 +507,24 @@ def run_small(P, S, torch, dev, stream, reps=5):
                         "ms_per_solve": ms, "iterations": w.n_iter, "ny": w.ny, "nx": w.nx, "n_modes": K,
                         "hbm_fraction": "not applicable (latency bound, field resident in L2)"}
             if path == "cluster":
-                default = P.pwf_plan_cluster_size(plan.handle)
+                default, dsched = P.pwf_plan_cluster_size(plan.handle), P.pwf_plan_cluster_schedule(plan.handle)
                 sweep = {}
-                for cs in (1, 2, 4, 8, 16):
+                for sched in (0, 1):
                     try:
-                        P.pwf_plan_set_cluster_size(plan.handle, cs)
+                        P.pwf_plan_set_cluster_schedule(plan.handle, sched)
                     except P.PWFError:
                         continue
-                    sweep[str(cs)] = round(1e3 * timed_solve(plan, y, psi) / w.n_iter, 2)
+                    for cs in (1, 2, 4, 8, 16):
+                        try:
+                            P.pwf_plan_set_cluster_size(plan.handle, cs)
+                        except P.PWFError:
+                            continue
+                        sweep[f"set{sched}_{cs}"] = round(1e3 * timed_solve(plan, y, psi) / w.n_iter, 2)
+                P.pwf_plan_set_cluster_schedule(plan.handle, dsched)
                 P.pwf_plan_set_cluster_size(plan.handle, default)
-                out[key].update({"cluster_ctas": default, "us_per_iteration_by_cluster_ctas": sweep})
+                out[key].update({"cluster_ctas": default, "cluster_schedule_set": dsched,
+                                 "schedule": P.pwf_plan_describe(plan.handle).split("cluster_schedule=")[1].split()[0],
+                                 "us_per_iteration_by_schedule_set_and_ctas": sweep})
             plan.close()
     return out
 
@@ -606,7 +628,11 @@ def main():
     del f, psi_true
     psi = torch.zeros((batch, w.ny, w.nx), dtype=torch.complex64, device=dev)
 
+    if args.column_shapes:
+        for op, k in enumerate(int(v) for v in args.column_shapes.split(",")):
+            P.pwf_plan_set_column_shape(plan.handle, op, k)
     tuned = P.pwf_plan_describe(plan.handle)
+    shape_ids = selected_shape_ids(tuned)
 
     # warm-up (captures the iteration graph)
     plan.solve(y, t, psi, args.warmup, read_back=False)
@@ -806,7 +832,7 @@ def main():
                        "coherence": "IOTF, Gaussian sigma = 2 px" if w.xcoh_m > 0 else "coherent",
                        "eta": w.eta, "l2_flush": "inputs larger than L2 (state ~1.5 GB per field)",
                        "step": "one PWF iteration over all projections",
-                       "column_shapes": tuned},
+                       "column_shapes": tuned, "column_shape_ids": shape_ids},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "iteration": iteration,

@@ -71,13 +71,18 @@ typedef struct pwf_state pwf_state;
                                     every wait bounded); square grids of 64, 128, 256
                                     or 512 only, else PWF_ERR_UNSUPPORTED           */
 #define PWF_FLAG_GRAPH 0x40u     /* pwf_solve as one CUDA graph holding the whole
-                                    iteration loop (the default)                   */
+                                    iteration loop (the default, but see CLUSTER)  */
 #define PWF_FLAG_CLUSTER 0x80u   /* pwf_solve as ONE launch of one thread-block
                                     cluster per projection for all iterations
                                     (hardware cluster barriers between the passes);
                                     square grids of 64, 128, 256 or 512 only, else
                                     PWF_ERR_UNSUPPORTED. At most one of PERSISTENT,
-                                    GRAPH and CLUSTER (else PWF_ERR_INVALID_ARG)  */
+                                    GRAPH and CLUSTER (else PWF_ERR_INVALID_ARG).
+                                    With none of the three, a plan takes this
+                                    solver where it measured faster: square
+                                    128^2 IOTF/coherent plans whose batch one
+                                    wave of clusters holds (not with
+                                    PWF_FLAG_CHECK_FINITE)                         */
 #define PWF_FLAG_CHECK_FINITE 0x200u /* debug: after every pass a scan of what it
                                     wrote; pwf_state_read (and pwf_solve) then
                                     return PWF_ERR_NONFINITE naming, in
@@ -356,6 +361,15 @@ int32_t pwf_plan_uses_persistent(const pwf_plan* plan);
  * plans. */
 pwf_status pwf_plan_set_cluster_size(pwf_plan* plan, int32_t ctas);
 int32_t pwf_plan_cluster_size(const pwf_plan* plan);
+/* Radix schedule set of a PWF_FLAG_CLUSTER plan's kernel: 0 the default
+ * schedule of the length, 1 its alternative (128 = 4.4.4.2, 256 = 4.8.8: one
+ * transform per warp, fewer values per thread, so shorter dependent chains in
+ * every pass item), -1 the alternative where built, else 0 (the plan's
+ * choice). Also resets the cluster size to its default. PWF_ERR_UNSUPPORTED
+ * when that set is not built for the length; pwf_plan_cluster_schedule
+ * returns the set in use (-1 for other plans). */
+pwf_status pwf_plan_set_cluster_schedule(pwf_plan* plan, int32_t set);
+int32_t pwf_plan_cluster_schedule(const pwf_plan* plan);
 
 /* Debug aid for the out-of-memory paths: the device allocation `after`
  * allocations from now (0: the next one) fails as if cudaMalloc had, so the

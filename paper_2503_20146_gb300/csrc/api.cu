@@ -452,6 +452,8 @@ struct pwf_plan {
   int* scan_word = nullptr;      // PWF_FLAG_CHECK_FINITE: id of the first pass that wrote a NaN or inf (-1: none)
   std::vector<const char*> scan_names;  // pass names by id
   int cluster = 0;               // cluster-resident variant: CTAs per cluster (0: not used)
+  int cluster_sched = 0;         // its radix schedule set (LengthKernels::sched_radix)
+  bool cluster_plan = false;     // pwf_solve takes the cluster-resident solver
   DevIter* cit = nullptr;        // [B] per-projection iteration records of that variant
 };
 
@@ -1040,6 +1042,12 @@ pwf_status persist_solve(pwf_plan* p, pwf_state* st, const float* y, const float
   std::vector<PersistPhase> ph;
   persist_schedule(p, st, y, t, psi, ph);
   if ((int)ph.size() > PERSIST_MAX_PHASES) return fail(p, PWF_ERR_STATE, "too many passes for the persistent solver");
+  if (p->cluster > 0 && p->cluster_sched == 1)  // the kernel's transforms run the alternative schedule
+    for (PersistPhase& q : ph) {
+      const AxisTables& A = q.kind == PK_COL ? p->ay : p->ax;
+      q.a.tw_fwd = A.tw_fwd_alt;
+      q.a.tw_inv = A.tw_inv_alt;
+    }
   PWF_CUDA(p, cudaMemcpyAsync(p->phases, ph.data(), ph.size() * sizeof(PersistPhase), cudaMemcpyHostToDevice,
                               p->stream));
   if (p->cluster == 0) PWF_CUDA(p, cudaMemsetAsync(p->bar, 0, 2 * sizeof(unsigned), p->stream));
@@ -1059,7 +1067,8 @@ pwf_status persist_solve(pwf_plan* p, pwf_state* st, const float* y, const float
   pa.it = st->it;
   pa.cit = p->cit;
   if (p->cluster > 0) {
-    LAUNCH(p, enqueue(p, "persist_cluster", [&] { return p->kcol->persist_cluster(pa, p->cluster, p->stream); }));
+    LAUNCH(p, enqueue(p, "persist_cluster",
+                      [&] { return p->kcol->persist_cluster[p->cluster_sched](pa, p->cluster, p->stream); }));
     p->launches++;  // the closing k_persist_cluster_finish
   } else {
     LAUNCH(p, enqueue(p, "persist", [&] { return p->kcol->persist(pa, p->persist_grid, p->stream); }));
@@ -1422,13 +1431,39 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       pwf_plan_destroy(p);
       return PWF_ERR_UNSUPPORTED;
     }
-    if (d.flags & PWF_FLAG_CLUSTER) {
+    // With no solver asked for, the cluster-resident solver takes the plans it
+    // measured faster on: lengths with its one-warp-per-transform schedule
+    // (128^2: 50 against 58 us per iteration, IOTF), batches that one wave of
+    // clusters holds (9 x 128^2 needed two waves: 99 against 58 us).
+    const bool no_solver = !(d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER));
+    const bool try_cluster = eligible && no_solver && !(d.flags & PWF_FLAG_CHECK_FINITE) &&
+                             p->kcol->persist_cluster[1] != nullptr && p->ax.tw_fwd_alt && p->ay.tw_fwd_alt;
+    if ((d.flags & PWF_FLAG_CLUSTER) || try_cluster) {
       if ((r = dalloc(p, &p->gpart, (size_t)d.batch * PERSIST_MAX_CLUSTER * NACC)) ||
-          (r = dalloc(p, &p->cit, (size_t)d.batch)) || (r = dalloc(p, &p->phases, PERSIST_MAX_PHASES)) ||
-          (r = pwf_plan_set_cluster_size(p, 0))) {
+          (r = dalloc(p, &p->cit, (size_t)d.batch)) || (r = dalloc(p, &p->phases, PERSIST_MAX_PHASES))) {
         pwf_plan_destroy(p);
         return r;
       }
+      p->cluster_plan = true;
+      r = pwf_plan_set_cluster_schedule(p, -1);
+      int maxc = 0;
+      if (r == PWF_OK && try_cluster &&
+          (p->kcol->persist_cluster_prep[p->cluster_sched](d.batch, p->cluster, &maxc) != cudaSuccess ||
+           maxc < d.batch)) {
+        cudaGetLastError();
+        p->cluster = 0;  // more than one wave of clusters: the graph
+        p->cluster_plan = false;
+      } else if (r != PWF_OK && try_cluster) {
+        cudaGetLastError();
+        p->cluster = 0;
+        p->cluster_plan = false;
+        r = PWF_OK;
+      }
+      if (r) {
+        pwf_plan_destroy(p);
+        return r;
+      }
+      p->err[0] = 0;
     }
     if (eligible && want) {
       int per_sm = 0;
@@ -2034,22 +2069,39 @@ pwf_status pwf_plan_set_wait_limit(pwf_plan* p, int64_t cycles) {
 
 int32_t pwf_plan_uses_persistent(const pwf_plan* p) { return p ? (p->cluster > 0 ? 2 : p->persist ? 1 : 0) : -1; }
 
+// threads per transform of length n in schedule set `set` of its kernels
+int set_tpf(const LengthKernels* k, int set, int n) {
+  int e = 1;
+  for (int i = 0; i < k->sched_stages[set]; i++) {
+    int a = e, b = k->sched_radix[set][i];
+    while (b) {
+      const int r = a % b;
+      a = b;
+      b = r;
+    }
+    e = e / a * k->sched_radix[set][i];
+  }
+  return n / e;
+}
+
 pwf_status pwf_plan_set_cluster_size(pwf_plan* p, int32_t ctas) {
-  if (!p || !p->kcol || !p->kcol->persist_cluster || !p->cit || ctas < 0 || ctas > PERSIST_MAX_CLUSTER)
+  if (!p || !p->kcol || !p->kcol->persist_cluster[p->cluster_sched] || !p->cluster_plan || ctas < 0 ||
+      ctas > PERSIST_MAX_CLUSTER)
     return PWF_ERR_INVALID_ARG;
+  PersistClusterPrepFn prep = p->kcol->persist_cluster_prep[p->cluster_sched];
   if (ctas == 0) {
     // One warp-sized item (32 / (threads per transform) rows or columns) runs
     // as a serial chain on its warp, so the pass takes as long as its longest
     // chain: the default spreads the items over as many SMs as one cluster
     // can hold (measured at 128^2: 105 us per iteration on 2 CTAs, 71 on 8,
     // 71 on 16), at most one CTA per item.
-    const int per_item = 32 / tpf_for(p->d.nx);
+    const int per_item = 32 / set_tpf(p->kcol, p->cluster_sched, p->d.nx);
     const int items = p->d.nx / per_item;
     int cs = PERSIST_MAX_CLUSTER;
     while (cs > 1 && cs > items) cs /= 2;
     for (; cs >= 1; cs /= 2) {
       int maxc = 0;
-      if (p->kcol->persist_cluster_prep(p->d.batch, cs, &maxc) == cudaSuccess && maxc > 0) break;
+      if (prep(p->d.batch, cs, &maxc) == cudaSuccess && maxc > 0) break;
       cudaGetLastError();
     }
     if (cs < 1) return fail(p, PWF_ERR_UNSUPPORTED, "no cluster shape of the cluster-resident solver fits");
@@ -2057,7 +2109,7 @@ pwf_status pwf_plan_set_cluster_size(pwf_plan* p, int32_t ctas) {
     return PWF_OK;
   }
   int maxc = 0;
-  if (p->kcol->persist_cluster_prep(p->d.batch, ctas, &maxc) != cudaSuccess || maxc < 1) {
+  if (prep(p->d.batch, ctas, &maxc) != cudaSuccess || maxc < 1) {
     cudaGetLastError();
     return fail(p, PWF_ERR_UNSUPPORTED, "this cluster shape does not fit on the device");
   }
@@ -2066,6 +2118,21 @@ pwf_status pwf_plan_set_cluster_size(pwf_plan* p, int32_t ctas) {
 }
 
 int32_t pwf_plan_cluster_size(const pwf_plan* p) { return p ? p->cluster : -1; }
+
+pwf_status pwf_plan_set_cluster_schedule(pwf_plan* p, int32_t set) {
+  if (!p || !p->kcol || !p->cluster_plan || set < -1 || set > 1) return PWF_ERR_INVALID_ARG;
+  const bool alt = p->kcol->persist_cluster[1] != nullptr && p->ax.tw_fwd_alt != nullptr && p->ay.tw_fwd_alt != nullptr;
+  if (set == -1) set = alt ? 1 : 0;  // the shorter chains per thread where built
+  if (set == 1 && !alt) return fail(p, PWF_ERR_UNSUPPORTED, "no alternative schedule of the cluster solver here");
+  if (!p->kcol->persist_cluster[set]) return fail(p, PWF_ERR_UNSUPPORTED, "cluster solver not built for this length");
+  const int old = p->cluster_sched;
+  p->cluster_sched = set;
+  const pwf_status r = pwf_plan_set_cluster_size(p, 0);
+  if (r) p->cluster_sched = old;
+  return r;
+}
+
+int32_t pwf_plan_cluster_schedule(const pwf_plan* p) { return p ? (p->cluster > 0 ? p->cluster_sched : -1) : -1; }
 
 void pwf_debug_fail_alloc(int32_t after) { g_fail_alloc.store(after < 0 ? -1 : after); }
 
@@ -2125,7 +2192,11 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
   put("ny=%d nx=%d batch=%d solver=%s loop=%s", p->d.ny, p->d.nx, p->d.batch,
       p->cluster > 0 ? "cluster" : p->persist ? "persistent" : "graph",
       p->persist || p->cluster > 0 ? "device" : !p->graph ? "none" : p->graph_loop ? "device" : "host");
-  if (p->cluster > 0) put(" cluster_ctas=%d", p->cluster);
+  if (p->cluster > 0) {
+    put(" cluster_ctas=%d cluster_schedule=", p->cluster);
+    for (int i = 0; i < p->kcol->sched_stages[p->cluster_sched]; i++)
+      put("%s%d", i ? "." : "", p->kcol->sched_radix[p->cluster_sched][i]);
+  }
   for (int op = 0; op < NUM_COL_OPS; op++) {
     put(" %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 // Radix schedule set of this translation unit: 0 (the default, every pass)
 // or 1 (the alternative schedules some column shapes are also built with, in
 // translation units of their own). Everything schedule-dependent lives in the
@@ -260,11 +262,13 @@ struct Sched {
 };
 
 // The alternative schedules (set 1): the same stages in another order where
-// that keeps the values per thread, or smaller radices where it halves them
-// (fewer registers per transform, more warps per SM, one more exchange).
+// that keeps the values per thread, or smaller radices where it cuts them
+// (fewer registers per transform, more warps per SM, shorter dependent chains
+// per thread, at the price of more exchanges: 128 = 4.4.4.2 runs one
+// transform per warp with four values per thread).
 __host__ __device__ constexpr Sched sched_alt(int n) {
   switch (n) {
-    case 128: return {128, 3, 4, 4, 8, 1, 1};
+    case 128: return {128, 4, 4, 4, 4, 2, 1};
     case 256: return {256, 3, 4, 8, 8, 1, 1};
     case 512: return {512, 3, 8, 8, 8, 1, 1};
     case 768: return {768, 5, 4, 4, 4, 4, 3};
@@ -342,8 +346,9 @@ __host__ __device__ constexpr int twiddle_len(int n, int dir) { return stage_two
 // the only ones that touch it, so a stage barrier covers just them: a named
 // barrier (id 1 + row) when they span several warps, a warp barrier when the
 // row fits in one warp (NT = threads of the block).
-template <int TPF, int NT>
+template <int TPF, int NT, bool TWS = false>
 struct RowLayout {
+  static constexpr bool kTwShared = TWS;  // the twiddle table handed to the transforms is in shared memory
   float2* base;
   int bar;
   __device__ __forceinline__ float2& operator[](int p) const { return base[p + (p >> 4)]; }
@@ -386,7 +391,18 @@ struct ColLayout {
 // a field: on smooth objects it adds up coherently in the lowest spatial
 // frequencies of the modelled intensity. PWF_TWIDDLE_PRODUCTS restores the
 // products (for measurement).
-template <int R>
+// layouts that say so take their twiddle table from shared memory (a plain
+// load); every other table is global and read through the read-only path
+template <class L, class = void>
+struct tw_in_smem {
+  static constexpr bool value = false;
+};
+template <class L>
+struct tw_in_smem<L, std::void_t<decltype(L::kTwShared)>> {
+  static constexpr bool value = L::kTwShared;
+};
+
+template <int R, bool TWS = false>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int off, int ns, int k, int r,
                                           const float2 (&w)[R]) {
 #ifdef PWF_TWIDDLE_PRODUCTS
@@ -397,7 +413,8 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int off
 #else
   (void)w;
 #endif
-  return __ldg(&tw[off + (r - 1) * ns + k]);
+  if constexpr (TWS) return tw[off + (r - 1) * ns + k];
+  else return __ldg(&tw[off + (r - 1) * ns + k]);
 }
 
 // Runs stages [K, S) of the length-N transform with direction DIR on the slot
@@ -436,7 +453,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[ept_for(N)], const L& sm,
       // precision, rounded once)
       float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; r++) w[r] = twiddle<R>(tw, OFF, NS, k, r, w);
+      for (int r = 1; r < R; r++) w[r] = twiddle<R, tw_in_smem<L>::value>(tw, OFF, NS, k, r, w);
 #pragma unroll
       for (int r = 1; r < R; r++) v[i * R + r] = cmul(v[i * R + r], w[r]);
       dft<R, DIR>(&v[i * R]);
@@ -520,7 +537,7 @@ __device__ __forceinline__ void fft_stages2(float2 (&v)[ept_for(N)], float2 (&u)
       const int k = b % NS;
       float2 w[R];
 #pragma unroll
-      for (int r = 1; r < R; r++) w[r] = twiddle<R>(tw, OFF, NS, k, r, w);
+      for (int r = 1; r < R; r++) w[r] = twiddle<R, tw_in_smem<L>::value>(tw, OFF, NS, k, r, w);
 #pragma unroll
       for (int r = 1; r < R; r++) {
         v[i * R + r] = cmul(v[i * R + r], w[r]);

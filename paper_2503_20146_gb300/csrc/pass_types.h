@@ -143,8 +143,9 @@ struct LengthKernels {
   PersistFn persist;
   PersistPrepFn persist_prep;
   PersistOccFn persist_occupancy;
-  PersistClusterFn persist_cluster;
-  PersistClusterPrepFn persist_cluster_prep;
+  // cluster-resident solver, per radix schedule set (null where not built)
+  PersistClusterFn persist_cluster[2];
+  PersistClusterPrepFn persist_cluster_prep[2];
 };
 
 // defined in the per-length translation units

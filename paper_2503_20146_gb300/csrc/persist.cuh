@@ -124,12 +124,12 @@ __device__ __forceinline__ double warp_sum(float x) {
 }
 
 // rows of a row pass: item = 32/TPF consecutive rows (one projection)
-template <int N, int OP>
+template <int N, int OP, bool TWS>
 __device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc,
                                              int only) {
   constexpr int TPF = tpf_for(N), RPW = 32 / TPF;
   const int sub = lane / TPF, t = lane - sub * TPF;
-  const RowLayout<TPF, 32> sm{wsm + sub * row_smem_len(N), 0};
+  const RowLayout<TPF, 32, TWS> sm{wsm + sub * row_smem_len(N), 0};
   // every projection's rows, or (only >= 0) those of projection `only`
   const long long per = (long long)a.ny / RPW;
   const long long i0 = only < 0 ? 0 : only * per, items = only < 0 ? a.B * per : i0 + per;
@@ -155,12 +155,12 @@ __device__ __forceinline__ void persist_rows(const PassArgs& a, int gw, int GW, 
 
 // columns of a column pass: item = 32/TPF adjacent columns of one projection;
 // lane = t * CPW + c, so that a warp's loads cover CPW adjacent columns
-template <int N, int OP>
+template <int N, int OP, bool TWS>
 __device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, int lane, float2* wsm, double* s_acc,
                                              int only) {
   constexpr int TPF = tpf_for(N), CPW = 32 / TPF;
   const int c = lane % CPW, t = lane / CPW;
-  const RowLayout<TPF, 32> sm{wsm + c * row_smem_len(N), 0};
+  const RowLayout<TPF, 32, TWS> sm{wsm + c * row_smem_len(N), 0};
   const long long per = (long long)a.nx / CPW;
   const long long i0 = only < 0 ? 0 : only * per, items = only < 0 ? a.B * per : i0 + per;
   for (long long it = i0 + gw; it < items; it += GW) {
@@ -178,27 +178,27 @@ __device__ __forceinline__ void persist_cols(const PassArgs& a, int gw, int GW, 
   }
 }
 
-template <int N>
+template <int N, bool TWS = false>
 __device__ __forceinline__ void persist_row_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
                                                double* s_acc, int only = -1) {
   switch (op) {
-    case ROW_MUL_T: persist_rows<N, ROW_MUL_T>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case ROW_INTENSITY: persist_rows<N, ROW_INTENSITY>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case ROW_MUL_V: persist_rows<N, ROW_MUL_V>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case ROW_COH_RESID: persist_rows<N, ROW_COH_RESID>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case ROW_GRAD_PACK: persist_rows<N, ROW_GRAD_PACK>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case ROW_NESTEROV_FFT: persist_rows<N, ROW_NESTEROV_FFT>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_MUL_T: persist_rows<N, ROW_MUL_T, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_INTENSITY: persist_rows<N, ROW_INTENSITY, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_MUL_V: persist_rows<N, ROW_MUL_V, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_COH_RESID: persist_rows<N, ROW_COH_RESID, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_GRAD_PACK: persist_rows<N, ROW_GRAD_PACK, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case ROW_NESTEROV_FFT: persist_rows<N, ROW_NESTEROV_FFT, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
     default: break;
   }
 }
 
-template <int N>
+template <int N, bool TWS = false>
 __device__ __forceinline__ void persist_col_op(int op, const PassArgs& a, int gw, int GW, int lane, float2* wsm,
                                                double* s_acc, int only = -1) {
   switch (op) {
-    case COL_Q: persist_cols<N, COL_Q>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case COL_RESID_IOTF2: persist_cols<N, COL_RESID_IOTF2>(a, gw, GW, lane, wsm, s_acc, only); break;
-    case COL_PRECOND_REG: persist_cols<N, COL_PRECOND_REG>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case COL_Q: persist_cols<N, COL_Q, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case COL_RESID_IOTF2: persist_cols<N, COL_RESID_IOTF2, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
+    case COL_PRECOND_REG: persist_cols<N, COL_PRECOND_REG, TWS>(a, gw, GW, lane, wsm, s_acc, only); break;
     default: break;
   }
 }
@@ -301,8 +301,14 @@ constexpr int PERSIST_MAX_CLUSTER = 16;
 __host__ __device__ constexpr size_t persist_cluster_phase_offset(int n, int batch) {
   return (persist_smem_bytes(n, batch) + 127) / 128 * 128;
 }
-__host__ __device__ constexpr size_t persist_cluster_smem_bytes(int n, int batch) {
+// then the forward and inverse twiddle tables of the length (rows and columns
+// of a square plan share them)
+__host__ __device__ constexpr size_t persist_cluster_tw_offset(int n, int batch) {
   return persist_cluster_phase_offset(n, batch) + PERSIST_MAX_PHASES * sizeof(PersistPhase);
+}
+__host__ __device__ constexpr size_t persist_cluster_smem_bytes(int n, int batch) {
+  return persist_cluster_tw_offset(n, batch) +
+         (size_t)(twiddle_len(n, FWD) + twiddle_len(n, INV) + 2) * sizeof(float2);
 }
 
 template <int N>
@@ -328,10 +334,23 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 1) persist_cluster_kernel(con
   }
   for (int i = threadIdx.x; i < pa.B * NACC; i += blockDim.x) s_acc[i] = 0.0;
   __syncthreads();
+  // The twiddle tables into shared memory: after a cluster barrier the
+  // transforms of the next pass then find them at shared-memory latency. The
+  // first phase is a column pass of the plan's column axis; a square plan's
+  // row axis has the same tables.
+  constexpr int TWF = twiddle_len(N, FWD), TWI = twiddle_len(N, INV);
+  float2* s_twf = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + persist_cluster_tw_offset(N, pa.B));
+  float2* s_twi = s_twf + (TWF > 0 ? TWF : 1);
+  for (int i = threadIdx.x; i < TWF; i += blockDim.x) s_twf[i] = s_ph[0].a.tw_fwd[i];
+  for (int i = threadIdx.x; i < TWI; i += blockDim.x) s_twi[i] = s_ph[0].a.tw_inv[i];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    // the Nesterov pass reads this projection's beta
-    for (int ph = 0; ph < pa.nphases; ph++)
+    for (int ph = 0; ph < pa.nphases; ph++) {
+      // the Nesterov pass reads this projection's beta
       if (s_ph[ph].a.beta == &pa.it->beta) s_ph[ph].a.beta = &cit->beta;
+      s_ph[ph].a.tw_fwd = s_twf;
+      s_ph[ph].a.tw_inv = s_twi;
+    }
     if (cr == 0) {
       *cit = *pa.it;
       cit->n_active = pa.active[proj] ? 1 : 0;
@@ -343,9 +362,9 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 1) persist_cluster_kernel(con
     for (int ph = 0; ph < pa.nphases; ph++) {
       const PersistPhase& P = s_ph[ph];
       if (P.kind == PK_ROW) {
-        persist_row_op<N>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
+        persist_row_op<N, true>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
       } else if (P.kind == PK_COL) {
-        persist_col_op<N>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
+        persist_col_op<N, true>(P.op, P.a, gw, GW, lane, wsm, s_acc, proj);
       } else if (P.kind == PK_FINALIZE && cr == 0 && threadIdx.x == 0) {
         double sums[NACC] = {};
         const int b0 = (int)blockIdx.x - cr;
@@ -458,10 +477,20 @@ LengthKernels with_persist(LengthKernels k) {
     k.persist = launch_persist<N>;
     k.persist_prep = prep_persist<N>;
     k.persist_occupancy = occupancy_persist<N>;
-    k.persist_cluster = launch_persist_cluster<N>;
-    k.persist_cluster_prep = prep_persist_cluster<N>;
+    k.persist_cluster[0] = launch_persist_cluster<N>;
+    k.persist_cluster_prep[0] = prep_persist_cluster<N>;
   }
   return k;
+}
+
+// The cluster-resident solver built with this translation unit's schedule
+// set, registered in that set's slot (lengths whose transform fits one warp).
+template <int N>
+void add_schedule_cluster(LengthKernels& k) {
+  if constexpr (persist_size(N) && tpf_for(N) <= 32) {
+    k.persist_cluster[PWF_SCHED_VARIANT] = launch_persist_cluster<N>;
+    k.persist_cluster_prep[PWF_SCHED_VARIANT] = prep_persist_cluster<N>;
+  }
 }
 
 }  // namespace PWF_KNS

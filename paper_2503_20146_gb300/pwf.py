@@ -124,6 +124,8 @@ def open_library(path: str):
         "pwf_plan_uses_persistent": ([_P], i32),
         "pwf_plan_set_cluster_size": ([_P, i32], i32),
         "pwf_plan_cluster_size": ([_P], i32),
+        "pwf_plan_set_cluster_schedule": ([_P, i32], i32),
+        "pwf_plan_cluster_schedule": ([_P], i32),
         "pwf_debug_fail_alloc": ([i32], None),
         "pwf_debug_overrun": ([_P], i32),
     }
@@ -257,6 +259,15 @@ def pwf_plan_set_cluster_size(plan, ctas: int):
 
 def pwf_plan_cluster_size(plan) -> int:
     return int(load().pwf_plan_cluster_size(plan))
+
+
+def pwf_plan_set_cluster_schedule(plan, sched: int):
+    """Radix schedule set of a cluster-resident plan (0, 1, or -1 for the plan's choice)."""
+    _check(load().pwf_plan_set_cluster_schedule(plan, int(sched)), "pwf_plan_set_cluster_schedule", plan)
+
+
+def pwf_plan_cluster_schedule(plan) -> int:
+    return int(load().pwf_plan_cluster_schedule(plan))
 
 
 def pwf_debug_fail_alloc(after: int):

@@ -45,3 +45,10 @@ def test_instruction_count_only_for_the_captured_sources(monkeypatch):
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
     assert bench.measured_instructions_per_px("col_q") is None
     assert bench.measured_traffic("col_q") is None
+
+
+def test_selected_shape_ids_parse_the_plan_description():
+    import bench
+    d = ("ny=1024 nx=1024 batch=180 solver=graph loop=none col_q=C8s2[C8p:0.98,C8s2:0.88,C8s2@8.8.16:0.90] "
+         "col_iotf=C8s2@8.8.16[C8p:0.92,C8s2:0.87,C8s2@8.8.16:0.85] col_fft=C8p")
+    assert bench.selected_shape_ids(d) == [1, 2, None]

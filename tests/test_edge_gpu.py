@@ -155,7 +155,7 @@ def test_check_finite_passes_clean_input_bitwise(pwf):
     psi0, t = blob_batch(W2, 1, 128, 128)
     y = dev(to_f32(np.ones((1, 128, 128))))
     out = []
-    for flags in (pwf.FLAG_CHECK_FINITE, 0):      # both on the untuned column shapes: the same arithmetic
+    for flags in (pwf.FLAG_CHECK_FINITE, pwf.FLAG_GRAPH):   # both graphs on the untuned column shapes
         with _flagged_plan(pwf, g, 1, flags | pwf.FLAG_NO_TUNE) as plan:
             psi = torch.zeros((1, 128, 128), dtype=torch.complex64, device="cuda")
             plan.solve(y, dev(to_c64(t)), psi, 4)

@@ -129,9 +129,16 @@ def test_wait_limit_zero_times_out_and_the_plan_recovers(pwf):
 
 
 def test_which_plans_take_the_persistent_launch(pwf):
-    # graph replay by default (it measured faster); the persistent launch on
-    # request, for square IOTF/coherent plans of the built sizes only
-    expect = [(geometry(W1), 1, 0, 0),
+    # by default the graph, except the cluster-resident solver at 128^2 for
+    # batches one wave of clusters holds (where it measured faster); the
+    # persistent launch on request, for square IOTF/coherent plans of the
+    # built sizes only
+    expect = [(geometry(W1), 1, 0, 2),
+              (geometry(W1), 4, 0, 2),
+              (geometry(W1), 64, 0, 0),
+              (geometry(W2, 512, 512), 1, 0, 0),
+              (geometry(W1), 1, pwf.FLAG_GRAPH, 0),
+              (geometry(W1), 1, pwf.FLAG_CHECK_FINITE, 0),
               (geometry(W1), 1, pwf.FLAG_PERSISTENT, 1),
               (geometry(W2, 512, 512), 16, pwf.FLAG_PERSISTENT, 1),
               (geometry(W2, 512, 512), 1, pwf.FLAG_GRAPH, 0)]
@@ -151,9 +158,11 @@ def test_which_plans_take_the_persistent_launch(pwf):
 # ---------------------------------------------------------------------------
 # cluster-resident launch: one thread-block cluster per projection
 # ---------------------------------------------------------------------------
-def _solve_with(pwf, geom, t, y, n, flags, cluster=None, corr_tol=0.0):
+def _solve_with(pwf, geom, t, y, n, flags, cluster=None, corr_tol=0.0, sched=None):
     # untuned column shapes (F{y} takes one), so that plans compared bit for bit run the same arithmetic
     with pwf.Plan(desc_for(pwf, geom, y.shape[0], flags | pwf.FLAG_NO_TUNE)) as plan:
+        if sched is not None:
+            pwf.pwf_plan_set_cluster_schedule(plan.handle, sched)
         if cluster is not None:
             pwf.pwf_plan_set_cluster_size(plan.handle, cluster)
         psi = torch.zeros((y.shape[0], geom.ny, geom.nx), dtype=torch.complex64, device="cuda")
@@ -167,8 +176,14 @@ def test_cluster_solve_matches_oracle_and_persistent(pwf, w):
     # bit for bit; losses (FP64 sums in another order) to rounding
     geom, t, y = case(w, 1)
     ref = O.solve(y[0].astype(np.float64), t.astype(np.complex128), geom, w.n_iter)
-    got, iters, loss, desc = _solve_with(pwf, geom, t, y, w.n_iter, pwf.FLAG_CLUSTER)
+    # the plan's choice of schedule (the alternative at 128^2) against the oracle
+    alt, iters_a, loss_a, desc = _solve_with(pwf, geom, t, y, w.n_iter, pwf.FLAG_CLUSTER)
     assert "solver=cluster" in desc
+    assert int(iters_a[0]) == w.n_iter
+    assert phase_rms(alt[0], ref.psi) <= PHASE_TOL
+    assert abs(loss_a[0] - ref.losses[-1]) <= 1e-3 * ref.losses[-1]
+    # the default schedule: also bit for bit against the cooperative launch
+    got, iters, loss, desc = _solve_with(pwf, geom, t, y, w.n_iter, pwf.FLAG_CLUSTER, sched=0)
     assert int(iters[0]) == w.n_iter
     assert phase_rms(got[0], ref.psi) <= PHASE_TOL
     assert abs(loss[0] - ref.losses[-1]) <= 1e-3 * ref.losses[-1]
@@ -177,13 +192,16 @@ def test_cluster_solve_matches_oracle_and_persistent(pwf, w):
     assert abs(loss[0] - loss_p[0]) <= 1e-9 * loss_p[0]
 
 
-def test_cluster_sizes_agree_bitwise(pwf):
+@pytest.mark.parametrize("sched", [0, 1], ids=["default_schedule", "alternative_schedule"])
+def test_cluster_sizes_agree_bitwise(pwf, sched):
+    # within one radix schedule set every cluster size computes the same bits;
+    # both sets (256 = 16.16 and 4.8.8) against the oracle
     geom, t, y = case(W2, 2, 256)
     n = 6
     out = {}
     for cs in (1, 2, 4, 8, 16):
         try:
-            out[cs] = _solve_with(pwf, geom, t, y, n, pwf.FLAG_CLUSTER, cluster=cs)[0]
+            out[cs] = _solve_with(pwf, geom, t, y, n, pwf.FLAG_CLUSTER, cluster=cs, sched=sched)[0]
         except pwf.PWFError as e:      # a shape the device cannot hold
             assert e.status == 2
     assert 1 in out and 8 in out
@@ -217,11 +235,16 @@ def test_cluster_plan_rules(pwf):
     with pwf.Plan(desc_for(pwf, g128, 1, pwf.FLAG_CLUSTER)) as plan:
         assert pwf.pwf_plan_uses_persistent(plan.handle) == 2
         assert pwf.pwf_plan_cluster_size(plan.handle) in (8, 16)   # the largest cluster that fits
+        assert pwf.pwf_plan_cluster_schedule(plan.handle) == 1     # 4.4.4.2 built for 128
+        assert "cluster_schedule=4.4.4.2" in pwf.pwf_plan_describe(plan.handle)
+        with pytest.raises(pwf.PWFError) as e:
+            pwf.pwf_plan_set_cluster_schedule(plan.handle, 2)
+        assert e.value.status == 1
         for bad in (-1, 17):
             with pytest.raises(pwf.PWFError) as e:
                 pwf.pwf_plan_set_cluster_size(plan.handle, bad)
             assert e.value.status == 1
-    with pwf.Plan(desc_for(pwf, g128, 1)) as plan:
+    with pwf.Plan(desc_for(pwf, g128, 1, pwf.FLAG_GRAPH)) as plan:
         assert pwf.pwf_plan_cluster_size(plan.handle) == 0
         with pytest.raises(pwf.PWFError) as e:
             pwf.pwf_plan_set_cluster_size(plan.handle, 2)
