@@ -444,8 +444,18 @@ def run_mixed(P, S, torch, dev, stream, steps=4):
         torch.cuda.synchronize()
         cms = c0.elapsed_time(c1) / 2
         px = S.MIXED_PER_SIZE * n * n
+        # per pass (event pairs around every kernel of one eager iteration):
+        # total ms per pass name and each pass's algorithmic rate against the copy rate
+        tot, cnt = {}, {}
+        for name, pms in P.pwf_profile_iteration(plans[ci].handle, ys[ci], ts[ci], psis[ci], 1):
+            tot[name] = tot.get(name, 0.0) + pms
+            cnt[name] = cnt.get(name, 0) + 1
+        frac = {name: round(PASS_BYTES_PER_PX[name] * px * cnt[name] / (tot[name] / 1e3) / 1e9 / hbm, 3)
+                for name in tot if PASS_BYTES_PER_PX.get(name)}
         per_class.append({"n": n, "ms_per_iter_alone": cms,
-                          "model_frac_of_measured_hbm": px * modal_bytes_per_px(wm.n_modes) / (cms / 1e3) / 1e9 / hbm})
+                          "model_frac_of_measured_hbm": px * modal_bytes_per_px(wm.n_modes) / (cms / 1e3) / 1e9 / hbm,
+                          "pass_ms": {k: round(v, 3) for k, v in sorted(tot.items(), key=lambda kv: -kv[1])},
+                          "pass_frac_of_measured_hbm": frac})
     P.pwf_group_destroy(group)
     for p in plans:
         p.close()

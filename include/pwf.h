@@ -337,8 +337,11 @@ long long pwf_plan_launch_count(const pwf_plan* plan);
 size_t pwf_plan_describe(const pwf_plan* plan, char* buf, size_t len);
 /* Column-pass shapes (for tests and tuning studies). pass: 0 propagator,
  * 1 IOTF, 2 residual (Parseval), 3 preconditioner + regularizer, 4 forward
- * transform, 5 inverse transform. pwf_plan_column_shapes returns how many
- * shapes the plan's column length was built with (-1 on a bad argument);
+ * transform, 5 inverse transform, 6 and 7 the source-mode passes (spectral
+ * shift + Q1 + inverse transform; transform + conj Q1 + shift back,
+ * accumulated). Each pass's shapes cover both radix schedules of the length
+ * where it has two. pwf_plan_column_shapes returns how many shapes the plan's
+ * column length was built with (-1 on a bad argument);
  * pwf_plan_set_column_shape forces one (0-based), replacing the tuned choice. */
 int32_t pwf_plan_column_shapes(const pwf_plan* plan, int32_t pass);
 pwf_status pwf_plan_set_column_shape(pwf_plan* plan, int32_t pass, int32_t shape);

@@ -404,6 +404,8 @@ struct pwf_plan {
   const LengthKernels* kcol = nullptr;  // length ny
   int colsel[NUM_COL_OPS] = {0, 0, 0, 0, 0, 0};  // chosen column-pass shape per op
   float coltime[NUM_COL_OPS][MAX_COL_VARIANTS] = {};  // tuning times (ms per launch)
+  int modesel[2] = {0, 0};                              // chosen mode column-pass shape (CM_FWD, CM_BACK)
+  float modetime[2][MAX_MODE_VARIANTS] = {};            // their tuning times
   AxisTables ax, ay;
   bool coherent = false;
   // source-mode variant
@@ -817,8 +819,8 @@ __global__ void k_modal_resid(float* I, const float* __restrict__ y, size_t per_
 }
 
 cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumulate, int nproj) {
-  a.tw_fwd = p->ay.tw_fwd;
-  a.tw_inv = p->ay.tw_inv;
+  const ColVariant& sh = p->kcol->colmodev[mop][p->modesel[mop]];
+  a = sched_tables(p, a, sh.sched);
   a.qx = p->ax.q1;
   a.qy = p->ay.q1;
   a.mode_mx = md.mx;
@@ -826,7 +828,7 @@ cudaError_t colmode(pwf_plan* p, int mop, PassArgs a, const Mode& md, int accumu
   a.mode_w = md.w;
   a.accumulate = accumulate;
   const char* name = mop == CM_FWD ? "col_mode_fwd" : "col_mode_back";
-  cudaError_t e = enqueue(p, name, [&] { return p->kcol->colmode[mop](a, nproj, p->stream); });
+  cudaError_t e = enqueue(p, name, [&] { return sh.launch(a, nproj, p->stream); });
   return e != cudaSuccess ? e : scan_pass(p, name, a, nproj, -1, false);
 }
 
@@ -1217,6 +1219,55 @@ pwf_status tune_columns(pwf_plan* p) {
   return PWF_OK;
 }
 
+// The mode column passes' shapes timed the same way (source-mode plans): CM_FWD
+// reads the spectrum X at a shift of (3, 5) bins into M, CM_BACK reads M and
+// accumulates into ACC at the same shift.
+pwf_status tune_modes(pwf_plan* p) {
+  const size_t n = (size_t)p->d.batch * p->d.ny * p->d.nx;
+  PWF_CUDA(p, cudaMemsetAsync(p->X, 0, n * sizeof(float2), p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->M, 0, n * sizeof(float2), p->stream));
+  PWF_CUDA(p, cudaMemsetAsync(p->ACC, 0, n * sizeof(float2), p->stream));
+  cudaEvent_t e0, e1;
+  PWF_CUDA(p, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(p, cudaGetLastError(), "cudaEventCreate");
+  }
+  PassArgs a = base_args(p);
+  a.qx = p->ax.q1;
+  a.qy = p->ay.q1;
+  a.mode_mx = 3;
+  a.mode_my = 5;
+  a.mode_w = 1.0f;
+  cudaError_t err = cudaSuccess;
+  for (int m = 0; m < 2 && err == cudaSuccess; m++) {
+    a.in = m == CM_FWD ? p->X : p->M;
+    a.out = m == CM_FWD ? p->M : p->ACC;
+    a.accumulate = m == CM_BACK;
+    float best = 1e30f;
+    for (int v = 0; v < p->kcol->ncolmodev[m] && err == cudaSuccess; v++) {
+      const ColVariant& sh = p->kcol->colmodev[m][v];
+      const PassArgs av = sched_tables(p, a, sh.sched);
+      if ((err = sh.launch(av, a.B, p->stream)) != cudaSuccess) break;
+      cudaEventRecord(e0, p->stream);
+      for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) err = sh.launch(av, a.B, p->stream);
+      cudaEventRecord(e1, p->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      p->modetime[m][v] = ms / 2.0f;
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        p->modesel[m] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(p, err, "mode column-pass tuning");
+  return PWF_OK;
+}
+
 // One iteration (enqueued by `body` on the capture stream) as a graph replayed
 // once per iteration from the host.
 template <class F>
@@ -1400,11 +1451,12 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       return PWF_ERR_CUDA;
     }
   for (int m = 0; m < 2; m++)
-    if (p->kcol->colmode_prep[m]() != cudaSuccess) {
-      cudaGetLastError();
-      pwf_plan_destroy(p);
-      return PWF_ERR_CUDA;
-    }
+    for (int v = 0; v < p->kcol->ncolmodev[m]; v++)
+      if (p->kcol->colmodev[m][v].prep() != cudaSuccess) {
+        cudaGetLastError();
+        pwf_plan_destroy(p);
+        return PWF_ERR_CUDA;
+      }
   for (int op = 0; op < NUM_COL_OPS; op++)
     for (int v = 0; v < p->kcol->ncolv[op]; v++)
       if (p->kcol->colv[op][v].prep() != cudaSuccess) {
@@ -1485,7 +1537,8 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       }
     }
   }
-  if (!(d.flags & PWF_FLAG_NO_TUNE) && (r = tune_columns(p)) != PWF_OK) {
+  if (!(d.flags & PWF_FLAG_NO_TUNE) && ((r = tune_columns(p)) != PWF_OK ||
+                                        (!p->modes.empty() && (r = tune_modes(p)) != PWF_OK))) {
     pwf_plan_destroy(p);
     return r;
   }
@@ -2159,13 +2212,17 @@ pwf_status pwf_debug_overrun(pwf_plan* p) {
 }
 
 int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
-  if (!p || pass < 0 || pass >= NUM_COL_OPS) return -1;
-  return p->kcol->ncolv[pass];
+  if (!p || pass < 0 || pass >= NUM_COL_OPS + 2) return -1;
+  return pass < NUM_COL_OPS ? p->kcol->ncolv[pass] : p->kcol->ncolmodev[pass - NUM_COL_OPS];
 }
 
 pwf_status pwf_plan_set_column_shape(pwf_plan* p, int32_t pass, int32_t shape) {
-  if (!p || pass < 0 || pass >= NUM_COL_OPS || shape < 0 || shape >= p->kcol->ncolv[pass]) return PWF_ERR_INVALID_ARG;
-  p->colsel[pass] = shape;
+  if (!p || pass < 0 || pass >= NUM_COL_OPS + 2 || shape < 0 || shape >= pwf_plan_column_shapes(p, pass))
+    return PWF_ERR_INVALID_ARG;
+  if (pass < NUM_COL_OPS)
+    p->colsel[pass] = shape;
+  else
+    p->modesel[pass - NUM_COL_OPS] = shape;
   if (p->graph) {  // the captured iteration used the previous shapes
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
@@ -2184,7 +2241,8 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
     if (w > 0) o = std::min(sizeof(tmp) - 1, o + (size_t)w);
   };
   auto shape = [&](const ColVariant& v) {
-    put("C%d%s", v.C, v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2" : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
+    put("C%d%s", v.C, v.pipe == MODE_PAIR ? "x2" : v.pipe == 5 ? "tma2" : v.pipe == 4 ? "s2" : v.pipe == 3 ? "p2"
+                      : v.pipe == 2 ? "t" : v.pipe ? "p" : "");
     if (v.sched == 1)  // built with the alternative radix schedule: its radices
       for (int i = 0; i < p->kcol->sched_stages[1]; i++) put("%s%d", i ? "." : "@", p->kcol->sched_radix[1][i]);
   };
@@ -2201,10 +2259,21 @@ size_t pwf_plan_describe(const pwf_plan* p, char* buf, size_t len) {
     put(" %s=", kColNames[op]);
     shape(p->kcol->colv[op][p->colsel[op]]);
     if (p->coltime[op][0] > 0.f) {  // tuned: all candidates with their times
-      put("[");
+      put("%s", "[");
       for (int v = 0; v < p->kcol->ncolv[op]; v++) {
         shape(p->kcol->colv[op][v]);
         put(":%.3f%s", p->coltime[op][v], v + 1 < p->kcol->ncolv[op] ? "," : "]");
+      }
+    }
+  }
+  for (int m = 0; m < 2 && !p->modes.empty(); m++) {
+    put(" %s=", m == CM_FWD ? "col_mode_fwd" : "col_mode_back");
+    shape(p->kcol->colmodev[m][p->modesel[m]]);
+    if (p->modetime[m][0] > 0.f) {
+      put("%s", "[");
+      for (int v = 0; v < p->kcol->ncolmodev[m]; v++) {
+        shape(p->kcol->colmodev[m][v]);
+        put(":%.3f%s", p->modetime[m][v], v + 1 < p->kcol->ncolmodev[m] ? "," : "]");
       }
     }
   }

@@ -125,6 +125,7 @@ struct ColVariant {
 };
 constexpr int MAX_COL_VARIANTS = 20;
 constexpr int MAX_SCHED_STAGES = 5;
+constexpr int MAX_MODE_VARIANTS = 12;
 
 // tables of launchers for one length, filled by the per-length translation units
 struct LengthKernels {
@@ -137,8 +138,9 @@ struct LengthKernels {
   PrepFn row_prep[NUM_ROW_OPS];
   ColVariant colv[NUM_COL_OPS][MAX_COL_VARIANTS];
   int ncolv[NUM_COL_OPS];
-  PassFn colmode[2];
-  PrepFn colmode_prep[2];
+  // mode column passes (CM_FWD, CM_BACK): shapes, the default first
+  ColVariant colmodev[2][MAX_MODE_VARIANTS];
+  int ncolmodev[2];
   // persistent solver (square grids of the sizes persist_size accepts; null otherwise)
   PersistFn persist;
   PersistPrepFn persist_prep;

@@ -1260,29 +1260,67 @@ template <int N, int OP, int C, int PIPE>
 int ColShape<N, OP, C, PIPE>::resident = 1;
 
 
-// the mode column passes use one shape: 8 columns per tile from length 1024 on, else 16
+// Mode column pass shapes: tile width C, one column per thread or the pair of
+// adjacent columns. The first one registered is the default before tuning:
+// 8 columns per tile from length 1024 on (4 where 8 would exceed 512
+// threads), else 16; the pair kernel where a transform has 16 values per
+// thread and at most 64 threads.
 __host__ __device__ constexpr int colmode_c(int n) { return n >= 1024 ? (tpf_for(n) * 8 <= 512 ? 8 : 4) : 16; }
-// lengths with 16 values per thread and at most 64 threads per transform take
-// the column-pair kernel (8-column tiles, 256 threads, two CTAs per SM)
 __host__ __device__ constexpr bool colmode_pair(int n) { return ept_for(n) == 16 && tpf_for(n) <= 64 && n >= 128; }
-template <int N, int MOP>
-cudaError_t prep_colmode() {
-  constexpr int C = colmode_pair(N) ? 8 : colmode_c(N);
-  if constexpr (colmode_pair(N))
-    return cudaFuncSetAttribute(col_mode_kernel2<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)col_smem_bytes(N, C));
-  else
-    return cudaFuncSetAttribute(col_mode_kernel<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)col_smem_bytes(N, C));
+
+template <int N, int MOP, int C, bool PAIR>
+constexpr bool mode_shape_ok() {
+  constexpr int th = PAIR ? col2_threads(N, C) : col_threads(N, C);
+  return th >= 32 && th <= (PAIR ? 256 : 512) && col_smem_bytes(N, C) <= 200 * 1024 && N % C == 0 &&
+         (!PAIR || (C >= 4 && ept_for(N) <= 16));
 }
+
+template <int N, int MOP, int C, bool PAIR>
+struct ModeShape {
+  static cudaError_t prep() {
+    if constexpr (PAIR)
+      return cudaFuncSetAttribute(col_mode_kernel2<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem_bytes(N, C));
+    else
+      return cudaFuncSetAttribute(col_mode_kernel<N, MOP, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)col_smem_bytes(N, C));
+  }
+  static cudaError_t launch(const PassArgs& a, int nproj, cudaStream_t s) {
+    dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
+    if constexpr (PAIR)
+      return launch_pass(col_mode_kernel2<N, MOP, C>, grid, dim3(col2_threads(N, C)), col_smem_bytes(N, C), s, a.pdl,
+                         a);
+    else
+      return launch_pass(col_mode_kernel<N, MOP, C>, grid, dim3(col_threads(N, C)), col_smem_bytes(N, C), s, a.pdl,
+                         a);
+  }
+};
+
+// pipe code of a mode shape in ColVariant: 0 one column per thread, 6 the pair
+constexpr int MODE_PAIR = 6;
+
+template <int N, int MOP, int C, bool PAIR>
+void add_mode_variant(LengthKernels& k) {
+  if constexpr (mode_shape_ok<N, MOP, C, PAIR>()) {
+    int& n = k.ncolmodev[MOP];
+    for (int i = 0; i < n; i++)  // once per shape and schedule
+      if (k.colmodev[MOP][i].C == C && k.colmodev[MOP][i].pipe == (PAIR ? MODE_PAIR : 0) &&
+          k.colmodev[MOP][i].sched == PWF_SCHED_VARIANT)
+        return;
+    if (n < MAX_MODE_VARIANTS)
+      k.colmodev[MOP][n++] = {ModeShape<N, MOP, C, PAIR>::launch, ModeShape<N, MOP, C, PAIR>::prep, C,
+                              PAIR ? MODE_PAIR : 0, PWF_SCHED_VARIANT};
+  }
+}
+
 template <int N, int MOP>
-cudaError_t launch_colmode(const PassArgs& a, int nproj, cudaStream_t s) {
-  constexpr int C = colmode_pair(N) ? 8 : colmode_c(N);
-  dim3 grid((unsigned)(a.nx / C), (unsigned)nproj);
-  if constexpr (colmode_pair(N))
-    return launch_pass(col_mode_kernel2<N, MOP, C>, grid, dim3(col2_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a);
-  else
-    return launch_pass(col_mode_kernel<N, MOP, C>, grid, dim3(col_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a);
+void add_mode_op(LengthKernels& k) {
+  add_mode_variant<N, MOP, colmode_pair(N) ? 8 : colmode_c(N), colmode_pair(N)>(k);  // the default first
+  add_mode_variant<N, MOP, 8, true>(k);
+  add_mode_variant<N, MOP, 4, true>(k);
+  add_mode_variant<N, MOP, 16, false>(k);
+  add_mode_variant<N, MOP, 8, false>(k);
+  add_mode_variant<N, MOP, 4, false>(k);
 }
 
 // a shape is offered when its CTA has 16..512 threads and its buffers fit
@@ -1357,6 +1395,8 @@ void add_schedule_shapes(LengthKernels& k) {
   op_shapes(std::integral_constant<int, COL_PRECOND_REG>{});
   op_shapes(std::integral_constant<int, COL_FFT>{});
   op_shapes(std::integral_constant<int, COL_IFFT>{});
+  add_mode_op<N, CM_FWD>(k);  // and the mode column passes
+  add_mode_op<N, CM_BACK>(k);
 }
 
 template <int N>
@@ -1378,10 +1418,8 @@ LengthKernels make_length_kernels() {
   add_col_op<N, COL_PRECOND_REG>(k);
   add_col_op<N, COL_FFT>(k);
   add_col_op<N, COL_IFFT>(k);
-  k.colmode[CM_FWD] = launch_colmode<N, CM_FWD>;
-  k.colmode[CM_BACK] = launch_colmode<N, CM_BACK>;
-  k.colmode_prep[CM_FWD] = prep_colmode<N, CM_FWD>;
-  k.colmode_prep[CM_BACK] = prep_colmode<N, CM_BACK>;
+  add_mode_op<N, CM_FWD>(k);
+  add_mode_op<N, CM_BACK>(k);
   return k;
 }
 

@@ -86,3 +86,33 @@ def test_modal_solve_matches_oracle(pwf, K, n, iters):
     assert int(it[0]) == iters
     assert phase_rms(p.cpu().numpy()[0], ref.psi) <= PHASE_TOL
     assert abs(loss[0] - ref.losses[-1]) <= 1e-3 * ref.losses[-1]
+
+
+# every mode-pass shape of both radix schedules (passes 6 and 7 of the shape
+# control), forward and gradient against the oracle
+SHAPE_CASES = [("k9_1024x64", 9, 2, 1024, 64), ("k9_2048x32", 9, 1, 2048, 32), ("k9_768x96", 9, 1, 768, 96),
+               ("k9_256x128", 9, 2, 256, 128)]
+
+
+@pytest.mark.parametrize("name,K,batch,ny,nx", SHAPE_CASES, ids=[c[0] for c in SHAPE_CASES])
+def test_every_mode_shape_matches_oracle(pwf, name, K, batch, ny, nx):
+    geom = geometry(W2, ny, nx)
+    modes = O.source_modes(geom, K, SIGMA)
+    psi, t = blob_batch(W2, batch, ny, nx)
+    psi, t = to_c64(psi), to_c64(t)
+    y = to_f32(np.clip(1.0 + 0.1 * np.random.default_rng(22).standard_normal((batch, ny, nx)), 0, None))
+    b = batch - 1
+    P64, T64 = psi[b].astype(np.complex128), t.astype(np.complex128)
+    f_ref = O.modal_intensity(P64, T64, geom, modes)
+    g_ref, _ = O.modal_gradient(P64, T64, y[b].astype(np.float64), geom, modes)
+    with modal_plan(pwf, geom, batch, K) as plan:
+        counts = [pwf.pwf_plan_column_shapes(plan.handle, m) for m in (6, 7)]
+        assert min(counts) >= 2
+        for k in range(max(counts)):
+            for m, c in zip((6, 7), counts):
+                pwf.pwf_plan_set_column_shape(plan.handle, m, min(k, c - 1))
+            f = plan.forward(dev(psi), dev(t)).cpu().numpy()
+            g, _ = plan.gradient(dev(psi), dev(t), dev(y))
+            desc = pwf.pwf_plan_describe(plan.handle)
+            assert rel_l2(f[b], f_ref) <= FWD_TOL, (k, desc)
+            assert rel_l2(g.cpu().numpy()[b], g_ref) <= GRAD_TOL, (k, desc)
