@@ -255,9 +255,9 @@ __device__ __forceinline__ void dft(float2* x) {
 // compile-time radix schedules (forward order; the inverse runs them reversed)
 // ---------------------------------------------------------------------------
 struct Sched {
-  int n, s, r0, r1, r2, r3, r4;
+  int n, s, r0, r1, r2, r3, r4, r5;
   __host__ __device__ constexpr int r(int i) const {
-    return i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : i == 3 ? r3 : r4;
+    return i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : i == 3 ? r3 : i == 4 ? r4 : r5;
   }
 };
 
@@ -265,35 +265,37 @@ struct Sched {
 // that keeps the values per thread, or smaller radices where it cuts them
 // (fewer registers per transform, more warps per SM, shorter dependent chains
 // per thread, at the price of more exchanges: 128 = 4.4.4.2 runs one
-// transform per warp with four values per thread).
+// transform per warp with four values per thread; 768 and 1536 keep 12 values
+// per thread instead of 24).
 __host__ __device__ constexpr Sched sched_alt(int n) {
   switch (n) {
-    case 128: return {128, 4, 4, 4, 4, 2, 1};
-    case 256: return {256, 3, 4, 8, 8, 1, 1};
-    case 512: return {512, 3, 8, 8, 8, 1, 1};
-    case 768: return {768, 5, 4, 4, 4, 4, 3};
-    case 1024: return {1024, 3, 8, 8, 16, 1, 1};
-    case 2048: return {2048, 3, 8, 16, 16, 1, 1};
-    default: return {0, 0, 1, 1, 1, 1, 1};
+    case 128: return {128, 4, 4, 4, 4, 2, 1, 1};
+    case 256: return {256, 3, 4, 8, 8, 1, 1, 1};
+    case 512: return {512, 3, 8, 8, 8, 1, 1, 1};
+    case 768: return {768, 5, 4, 4, 4, 4, 3, 1};
+    case 1024: return {1024, 3, 8, 8, 16, 1, 1, 1};
+    case 1536: return {1536, 6, 4, 4, 4, 4, 2, 3};
+    case 2048: return {2048, 3, 8, 16, 16, 1, 1, 1};
+    default: return {0, 0, 1, 1, 1, 1, 1, 1};
   }
 }
 
 __host__ __device__ constexpr Sched sched_default(int n) {
   switch (n) {
-    case 16: return {16, 1, 16, 1, 1, 1, 1};
-    case 32: return {32, 2, 8, 4, 1, 1, 1};
-    case 64: return {64, 2, 8, 8, 1, 1, 1};
-    case 96: return {96, 3, 8, 4, 3, 1, 1};
-    case 128: return {128, 2, 16, 8, 1, 1, 1};
-    case 192: return {192, 3, 8, 8, 3, 1, 1};
-    case 256: return {256, 2, 16, 16, 1, 1, 1};
-    case 384: return {384, 4, 8, 8, 2, 3, 1};
-    case 512: return {512, 3, 16, 8, 4, 1, 1};
-    case 768: return {768, 4, 8, 8, 4, 3, 1};
-    case 1024: return {1024, 3, 16, 8, 8, 1, 1};
-    case 1536: return {1536, 4, 8, 8, 8, 3, 1};
-    case 2048: return {2048, 3, 16, 16, 8, 1, 1};
-    default: return {0, 0, 1, 1, 1, 1, 1};
+    case 16: return {16, 1, 16, 1, 1, 1, 1, 1};
+    case 32: return {32, 2, 8, 4, 1, 1, 1, 1};
+    case 64: return {64, 2, 8, 8, 1, 1, 1, 1};
+    case 96: return {96, 3, 8, 4, 3, 1, 1, 1};
+    case 128: return {128, 2, 16, 8, 1, 1, 1, 1};
+    case 192: return {192, 3, 8, 8, 3, 1, 1, 1};
+    case 256: return {256, 2, 16, 16, 1, 1, 1, 1};
+    case 384: return {384, 4, 8, 8, 2, 3, 1, 1};
+    case 512: return {512, 3, 16, 8, 4, 1, 1, 1};
+    case 768: return {768, 4, 8, 8, 4, 3, 1, 1};
+    case 1024: return {1024, 3, 16, 8, 8, 1, 1, 1};
+    case 1536: return {1536, 4, 8, 8, 8, 3, 1, 1};
+    case 2048: return {2048, 3, 16, 16, 8, 1, 1, 1};
+    default: return {0, 0, 1, 1, 1, 1, 1, 1};
   }
 }
 

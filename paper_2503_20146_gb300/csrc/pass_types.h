@@ -124,7 +124,7 @@ struct ColVariant {
   int sched;  // radix schedule of its transforms (LengthKernels::sched_radix)
 };
 constexpr int MAX_COL_VARIANTS = 20;
-constexpr int MAX_SCHED_STAGES = 5;
+constexpr int MAX_SCHED_STAGES = 6;
 constexpr int MAX_MODE_VARIANTS = 12;
 
 // tables of launchers for one length, filled by the per-length translation units

@@ -353,8 +353,16 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
   }
 }
 
+// Two CTAs per SM where three would make the pass spill: 32 values per
+// thread, and the diffuser multiply at 24 (measured at 768^2 and 1536^2: 3.33
+// -> 3.06 and 11.9 -> 11.2 ms per iteration of the K = 25 batch; the mode
+// intensity pass at 24 lost more with two than it saved, so it keeps three).
+__host__ __device__ constexpr int row_min_blocks(int n, int op) {
+  return ept_for(n) >= 32 || (ept_for(n) >= 24 && op == ROW_MUL_T) ? 2 : 3;
+}
+
 template <int N, int OP>
-__global__ void __launch_bounds__(row_threads(N), ept_for(N) >= 32 ? 2 : 3) row_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(row_threads(N), row_min_blocks(N, OP)) row_kernel(const PassArgs a) {
   pdl_wait();
   constexpr int TPF = tpf_for(N), ROWS = rows_for(N);
   using T = RowT<OP>;

@@ -91,7 +91,7 @@ def test_modal_solve_matches_oracle(pwf, K, n, iters):
 # every mode-pass shape of both radix schedules (passes 6 and 7 of the shape
 # control), forward and gradient against the oracle
 SHAPE_CASES = [("k9_1024x64", 9, 2, 1024, 64), ("k9_2048x32", 9, 1, 2048, 32), ("k9_768x96", 9, 1, 768, 96),
-               ("k9_256x128", 9, 2, 256, 128)]
+               ("k9_256x128", 9, 2, 256, 128), ("k9_1536x32", 9, 1, 1536, 32)]
 
 
 @pytest.mark.parametrize("name,K,batch,ny,nx", SHAPE_CASES, ids=[c[0] for c in SHAPE_CASES])

@@ -334,8 +334,8 @@ def test_pipelined_column_passes_sampled(pwf, name, batch, ny, nx):
 # every column-pass shape the tuner may choose, forced one at a time
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("ny,nx,batch", [(1024, 256, 6), (512, 128, 8), (128, 96, 4), (2048, 64, 2), (768, 128, 3),
-                                           (256, 64, 5)],
-                         ids=["1024x256", "512x128", "128x96", "2048x64", "768x128", "256x64"])
+                                           (256, 64, 5), (1536, 64, 2)],
+                         ids=["1024x256", "512x128", "128x96", "2048x64", "768x128", "256x64", "1536x64"])
 def test_every_column_shape_matches_oracle(pwf, ny, nx, batch):
     w = W2
     geom = geometry(w, ny, nx)
