@@ -123,7 +123,7 @@ struct ColVariant {
   int pipe;
   int sched;  // radix schedule of its transforms (LengthKernels::sched_radix)
 };
-constexpr int MAX_COL_VARIANTS = 20;
+constexpr int MAX_COL_VARIANTS = 24;
 constexpr int MAX_SCHED_STAGES = 6;
 constexpr int MAX_MODE_VARIANTS = 12;
 

@@ -635,6 +635,8 @@ __host__ __device__ constexpr size_t colt_smem_bytes(int n, int c) {
 // then the transforms of both columns share indices, twiddles and barriers and
 // move through shared memory 16 bytes at a time. Single-input passes only.
 __host__ __device__ constexpr int col2_threads(int n, int c) { return c / 2 * tpf_for(n); }
+// two CTAs per SM up to 256 threads, one CTA of 512 (a wide tile, 128 registers a thread)
+__host__ __device__ constexpr int col2_min_blocks(int n, int c) { return col2_threads(n, c) > 256 ? 1 : 2; }
 
 template <int N, int OP, class P>
 __device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int col, size_t base,
@@ -683,7 +685,7 @@ __device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int co
 // at 8 columns); NBUF = 1: one buffer, the copy of the next tile starts after
 // the current one is done, and the overlap comes from the second CTA on the SM.
 template <int N, int OP, int C, int NBUF>
-__global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_pipe2(const PassArgs a, int nproj) {
+__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_kernel_pipe2(const PassArgs a, int nproj) {
   pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int NT = col2_threads(N, C);
@@ -849,7 +851,7 @@ __host__ __device__ constexpr int tma_box_rows(int n) { return n < 256 ? n : 256
 __host__ __device__ constexpr size_t tma_smem_bytes(int n, int c) { return (size_t)n * c * sizeof(float2) + 1024; }
 
 template <int N, int OP, int C>
-__global__ void __launch_bounds__(col2_threads(N, C), 2) col_kernel_tma2(const __grid_constant__ PassArgs a, int nproj) {
+__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_kernel_tma2(const __grid_constant__ PassArgs a, int nproj) {
   pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
@@ -1095,7 +1097,7 @@ __global__ void __launch_bounds__(col_threads(N, C), col_min_blocks(col_threads(
 // not 16-byte aligned for odd mx (and wrap at the edge), so they are read as
 // two 8-byte accesses.
 template <int N, int MOP, int C>
-__global__ void __launch_bounds__(col2_threads(N, C), 2) col_mode_kernel2(const PassArgs a) {
+__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_mode_kernel2(const PassArgs a) {
   pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int RS = first_radix<N, FWD>();
@@ -1279,7 +1281,7 @@ __host__ __device__ constexpr bool colmode_pair(int n) { return ept_for(n) == 16
 template <int N, int MOP, int C, bool PAIR>
 constexpr bool mode_shape_ok() {
   constexpr int th = PAIR ? col2_threads(N, C) : col_threads(N, C);
-  return th >= 32 && th <= (PAIR ? 256 : 512) && col_smem_bytes(N, C) <= 200 * 1024 && N % C == 0 &&
+  return th >= 32 && th <= 512 && col_smem_bytes(N, C) <= 200 * 1024 && N % C == 0 &&
          (!PAIR || (C >= 4 && ept_for(N) <= 16));
 }
 
@@ -1324,6 +1326,7 @@ void add_mode_variant(LengthKernels& k) {
 template <int N, int MOP>
 void add_mode_op(LengthKernels& k) {
   add_mode_variant<N, MOP, colmode_pair(N) ? 8 : colmode_c(N), colmode_pair(N)>(k);  // the default first
+  add_mode_variant<N, MOP, 16, true>(k);
   add_mode_variant<N, MOP, 8, true>(k);
   add_mode_variant<N, MOP, 4, true>(k);
   add_mode_variant<N, MOP, 16, false>(k);
@@ -1342,7 +1345,7 @@ constexpr bool col_shape_ok() {
                                                   : col_smem_bytes(N, C);
   return th >= 16 && th <= 512 && sm <= 200 * 1024 && ((PIPE == 0 || PIPE == 2) || (N * C / 2) % th == 0) &&
          (PIPE != 2 || (OP != COL_PRECOND_REG && (N * C) % th == 0 && C <= 8)) &&
-         (!pair || (OP != COL_PRECOND_REG && C >= 4 && th >= 32 && th <= 256));
+         (!pair || (OP != COL_PRECOND_REG && C >= 4 && th >= 32 && th <= 512));
 }
 
 template <int N, int OP, int C, int PIPE>
@@ -1390,6 +1393,7 @@ void add_schedule_shapes(LengthKernels& k) {
   record_schedule<N>(k, PWF_SCHED_VARIANT);
   auto op_shapes = [&](auto op_tag) {
     constexpr int OP = decltype(op_tag)::value;
+    add_col_variant<N, OP, 16, 4>(k);
     add_col_variant<N, OP, 8, 4>(k);
     add_col_variant<N, OP, 8, 3>(k);
     add_col_variant<N, OP, 4, 4>(k);
