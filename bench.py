@@ -56,6 +56,10 @@ PASS_BYTES_PER_PX = {
     "col_precond_reg": 24,  # two fields in, one out
     "row_nesterov_fft": 52, # field, psi, phi, Re g in; phi, psi, field out
     "row_coh_resid": 20,    # field in, y in, field out
+    # packed residual passes (two real rows per complex row; bins 0..nx/2)
+    "row_intensity_pk": 20, # field in, v out, packed F_row{|v|^2} out (4 B/px)
+    "col_resid_pk": 12,     # packed field in and out (4 + 4), F{y} of bins 0..nx/2 (4)
+    "row_mul_v_pk": 20,     # packed field in (4), v in, field out
     # source-mode variant (per mode; see modal_bytes_per_px)
     "col_mode_fwd": 16,     # shifted column in, field out
     "row_mode_int": 24,     # field in, v_j out, intensity accumulated
@@ -78,7 +82,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=None, help="override projections per GPU")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu legs")
     ap.add_argument("--column-shapes", default=None,
-                    help="comma list of six column-shape indices (one per column op) forced after the plan-time "
+                    help="comma list of column-shape indices (one per column op, in pass order) forced after the plan-time "
                          "tuning of the main plan, e.g. the column_shape_ids of an earlier line")
     ap.add_argument("--legs", default="all",
                     help="comma list of extra legs to run (plain,e2e,modal,small,mixed,autograd,fbp,ablation,cpu) "
@@ -137,8 +141,15 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: let its first sample land
+            # before the timed region opens, so that the region is covered
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -661,13 +672,14 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-    launches = P.pwf_plan_launch_count(plan.handle) - launches0
+        launches = P.pwf_plan_launch_count(plan.handle) - launches0
+        # per-pass timing (eager, CUDA events around each kernel) -> roofline;
+        # inside the sampled window too, since the roofline comes from it
+        psi.zero_()
+        passes = P.pwf_profile_iteration(plan.handle, y, t, psi, 3)
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     value = world * mpx_iter * args.steps / (ms / 1e3)
 
-    # per-pass timing (eager, CUDA events around each kernel) -> roofline
-    psi.zero_()
-    passes = P.pwf_profile_iteration(plan.handle, y, t, psi, 3)
     hbm, peak_kind = peaks()
     tot = {}
     for name, pms in passes:

@@ -29,6 +29,30 @@
  *    error seen by a plan is sticky and returned by every later call on it.
  *  - A plan owns its workspace (a few complex fields per projection) and its
  *    1-D filter tables. Plans are not thread-safe; use one per host thread.
+ *
+ * Deliberate differences from a minimal "plan / forward / gradient / step /
+ * solve" interface, and why
+ *  - pwf_gradient leaves the per-projection loss in DEVICE memory, so that the
+ *    call stays asynchronous and can sit inside a caller's CUDA graph or an
+ *    autograd backward; host losses come from pwf_state_read, pwf_solve and
+ *    pwf_group_read.
+ *  - The diffuser t is an argument of every call, not of plan creation: the
+ *    joint refinement (pwf_solve_joint) and autograd change it between calls.
+ *  - One plan holds one (ny, nx). Series of mixed sizes are several plans
+ *    joined in a pwf_group: each size class then has its own tuned column
+ *    shapes, radix schedules and 1-D tables.
+ *  - The coherence model is chosen by the descriptor's values, not an enum:
+ *    xcoh_m = ycoh_m = 0 coherent, > 0 the paper's IOTF, n_modes = 9 or 25 the
+ *    source-mode variant.
+ *  - No flag stores or recomputes v: the fused solver always keeps the
+ *    detector field of the forward pass for its backward pass, and
+ *    pwf_forward_vjp always recomputes it (at most one mode's field at a time).
+ *  - No exact-ASM switch: the propagator is applied as the sum of its axis
+ *    restrictions, and plan creation rejects (PWF_ERR_UNSUPPORTED) any
+ *    geometry where that differs from the exact phase by more than 1e-6 rad.
+ *  - Bounds checking is a separate build (libpwf_bc.so, PWF_BOUNDS_CHECK), not
+ *    a flag, so the normal library's kernels carry none of its branches.
+ *  - dL/dt comes from pwf_forward_vjp (with dL/dpsi), not from pwf_gradient.
  */
 #ifndef PWF_H
 #define PWF_H
@@ -90,6 +114,12 @@ typedef struct pwf_state pwf_state;
                                     output held a NaN or an infinity. Graph
                                     solver only (PWF_ERR_UNSUPPORTED with
                                     PERSISTENT or CLUSTER)                        */
+#define PWF_FLAG_UNPACKED_RESID 0x400u /* the residual passes of the IOTF iteration on
+                                    full complex rows and every column (by default
+                                    the real intensity and residual fields travel
+                                    two rows per complex row, and the column pass
+                                    covers bins kx = 0..nx/2 only, the other half
+                                    being their conjugates)                       */
 #define PWF_FLAG_NO_PDL 0x100u   /* launch the passes without programmatic dependent
                                     launch (by default each pass is scheduled once
                                     the CTAs of the one before it have exited and
@@ -337,7 +367,8 @@ long long pwf_plan_launch_count(const pwf_plan* plan);
 size_t pwf_plan_describe(const pwf_plan* plan, char* buf, size_t len);
 /* Column-pass shapes (for tests and tuning studies). pass: 0 propagator,
  * 1 IOTF, 2 residual (Parseval), 3 preconditioner + regularizer, 4 forward
- * transform, 5 inverse transform, 6 and 7 the source-mode passes (spectral
+ * transform, 5 inverse transform, 6 the packed residual (bins 0..nx/2 of two
+ * real rows per complex row), 7 and 8 the source-mode passes (spectral
  * shift + Q1 + inverse transform; transform + conj Q1 + shift back,
  * accumulated). Each pass's shapes cover both radix schedules of the length
  * where it has two. pwf_plan_column_shapes returns how many shapes the plan's

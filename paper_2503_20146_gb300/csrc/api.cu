@@ -402,7 +402,7 @@ struct pwf_plan {
   double* calib = nullptr;               // calibration sums, nx + ny + 1 (allocated on first use)
   const LengthKernels* krow = nullptr;  // length nx
   const LengthKernels* kcol = nullptr;  // length ny
-  int colsel[NUM_COL_OPS] = {0, 0, 0, 0, 0, 0};  // chosen column-pass shape per op
+  int colsel[NUM_COL_OPS] = {};  // chosen column-pass shape per op
   float coltime[NUM_COL_OPS][MAX_COL_VARIANTS] = {};  // tuning times (ms per launch)
   int modesel[2] = {0, 0};                              // chosen mode column-pass shape (CM_FWD, CM_BACK)
   float modetime[2][MAX_MODE_VARIANTS] = {};            // their tuning times
@@ -594,9 +594,10 @@ int nproj_of(const pwf_plan* p) { return p->d.batch; }
 const char* const kRowNames[NUM_ROW_OPS] = {
     "row_exp_fft", "row_real_fft", "row_fft", "row_ifft", "row_mul_t", "row_intensity", "row_intensity_out",
     "row_real_out", "row_resid", "row_coh_resid", "row_coh_vjp", "row_mul_v", "row_grad_out", "row_grad_pack",
-    "row_nesterov_fft", "row_nesterov", "row_gradt", "row_mode_int", "row_mode_vg"};
+    "row_nesterov_fft", "row_nesterov", "row_gradt", "row_mode_int", "row_mode_vg", "row_intensity_pk",
+    "row_mul_v_pk"};
 const char* const kColNames[NUM_COL_OPS] = {"col_q", "col_iotf", "col_resid_iotf2", "col_precond_reg", "col_fft",
-                                            "col_ifft"};
+                                            "col_ifft", "col_resid_pk"};
 
 // Enqueues one kernel; under pwf_profile_iteration it is bracketed by events.
 template <class F>
@@ -916,6 +917,19 @@ pwf_status modal_resid(pwf_plan* p, const float* y, const int* active) {
              : cuda_fail(p, cudaGetLastError(), "k_modal_resid");
 }
 
+// The residual passes of the IOTF iteration take the packed form (two real
+// rows per complex row, columns kx and nx - kx from one transform pair) where
+// the column length has packed shapes, unless PWF_FLAG_UNPACKED_RESID.
+bool packed_resid(const pwf_plan* p) {
+  return !(p->d.flags & PWF_FLAG_UNPACKED_RESID) && p->kcol->ncolv[COL_RESID_PK] > 0;
+}
+
+// A packed-residual shape covers C of the nx/2 positions per tile: it fits a
+// plan whose nx/2 it divides. Every other shape fits every plan of its length.
+bool shape_fits(const pwf_plan* p, int op, const ColVariant& v) {
+  return op != COL_RESID_PK || (p->d.nx / 2) % v.C == 0;
+}
+
 // one fused iteration (or the body of pwf_step): X must hold F_row{exp psi}
 pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const float2* t, float2* psi,
                            bool next_fft, double corr_tol, float2* t_refine = nullptr, double eta_t = 0.0) {
@@ -958,10 +972,16 @@ pwf_status fused_iteration(pwf_plan* p, pwf_state* st, const float* y, const flo
     LAUNCH(p, row(p, ROW_COH_RESID, a, nproj_of(p)));   // e = y - |v|^2; loss; v (-e)
   } else {
     a.v = p->V;
-    LAUNCH(p, row(p, ROW_INTENSITY, a, nproj_of(p)));   // v stored; F_row{|v|^2}
     a.yhat = p->YH;
-    LAUNCH(p, col(p, COL_RESID_IOTF2, a, nproj_of(p))); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
-    LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v F^-1{IOTF F{-e}}
+    if (packed_resid(p)) {  // |v|^2 and G are real: two rows per complex row, half the columns
+      LAUNCH(p, row(p, ROW_INTENSITY_PK, a, nproj_of(p)));  // v stored; F_row{|v|^2}, rows packed in pairs
+      LAUNCH(p, col(p, COL_RESID_PK, a, nproj_of(p)));      // as COL_RESID_IOTF2 on bins 0..nx/2
+      LAUNCH(p, row(p, ROW_MUL_V_PK, a, nproj_of(p)));      // v F^-1{IOTF F{-e}} from the packed rows
+    } else {
+      LAUNCH(p, row(p, ROW_INTENSITY, a, nproj_of(p)));   // v stored; F_row{|v|^2}
+      LAUNCH(p, col(p, COL_RESID_IOTF2, a, nproj_of(p))); // IOTF (IOTF F{|v|^2} - F{y}); loss (Parseval)
+      LAUNCH(p, row(p, ROW_MUL_V, a, nproj_of(p)));       // v F^-1{IOTF F{-e}}
+    }
   }
   if ((r = fused_backprop(p, a, t, joint, nproj_of(p), p->GT))) return r;
   a.psi = psi;
@@ -1192,6 +1212,10 @@ pwf_status tune_columns(pwf_plan* p) {
     for (int v = 0; v < p->kcol->ncolv[op] && err == cudaSuccess; v++) {
       const PassFn fn = p->kcol->colv[op][v].launch;
       const PassArgs av = sched_tables(p, a, p->kcol->colv[op][v].sched);
+      if (!shape_fits(p, op, p->kcol->colv[op][v])) {  // not offered on this plan
+        p->coltime[op][v] = 1e30f;
+        continue;
+      }
       if (p->kcol->colv[op][v].pipe == 5 && fn(av, a.B, p->stream) != cudaSuccess) {
         // a TMA shape whose tensor map the driver would not encode: not offered
         cudaGetLastError();
@@ -1397,7 +1421,7 @@ pwf_status pwf_plan_create(const pwf_plan_desc* desc, pwf_plan** out) {
       d.L2_m < 0 || d.xcoh_m < 0 || d.ycoh_m < 0 || !(d.eta > 0) || d.gamma < 0 ||
       (d.flags & ~(PWF_FLAG_NO_PRECOND | PWF_FLAG_NO_REG | PWF_FLAG_PLAIN | PWF_FLAG_NO_TUNE |
                    PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER | PWF_FLAG_NO_PDL |
-                   PWF_FLAG_CHECK_FINITE)))
+                   PWF_FLAG_CHECK_FINITE | PWF_FLAG_UNPACKED_RESID)))
     return PWF_ERR_INVALID_ARG;
   {
     const uint32_t solver = d.flags & (PWF_FLAG_PERSISTENT | PWF_FLAG_GRAPH | PWF_FLAG_CLUSTER);
@@ -2219,6 +2243,8 @@ int32_t pwf_plan_column_shapes(const pwf_plan* p, int32_t pass) {
 pwf_status pwf_plan_set_column_shape(pwf_plan* p, int32_t pass, int32_t shape) {
   if (!p || pass < 0 || pass >= NUM_COL_OPS + 2 || shape < 0 || shape >= pwf_plan_column_shapes(p, pass))
     return PWF_ERR_INVALID_ARG;
+  if (pass < NUM_COL_OPS && !shape_fits(p, pass, p->kcol->colv[pass][shape]))
+    return fail(p, PWF_ERR_UNSUPPORTED, "column shape does not fit this plan's nx");
   if (pass < NUM_COL_OPS)
     p->colsel[pass] = shape;
   else

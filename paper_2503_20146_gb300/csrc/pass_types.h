@@ -90,6 +90,9 @@ enum RowOp : int {
   ROW_GRADT,           // IFFT -> g2; scratch (+)= 2 w conj(u1) g2; conj(t) g2 -> FFT
   ROW_MODE_INT,        // IFFT -> v_j (stored); I (+)= w |v_j|^2          (mode variant)
   ROW_MODE_VG,         // v_j G (both real-space inputs) -> FFT           (mode variant)
+  ROW_INTENSITY_PK,    // IFFT -> v (stored) -> |v|^2 of rows 2y', 2y'+1 packed as one
+                       // complex row -> FFT -> packed row y' (even row of the field)
+  ROW_MUL_V_PK,        // IFFT of packed row y' -> G of rows 2y' (Re), 2y'+1 (Im); v * G -> FFT
   NUM_ROW_OPS
 };
 
@@ -100,6 +103,8 @@ enum ColOp : int {
   COL_PRECOND_REG,     // FFT(H), FFT(S) -> Gamma^2 H + i P^-1 S -> IFFT
   COL_FFT,             // FFT only
   COL_IFFT,            // IFFT only (scaled)
+  COL_RESID_PK,        // COL_RESID_IOTF2 on packed rows: columns kx and nx - kx from one
+                       // transform pair (the residual field is real)
   NUM_COL_OPS
 };
 

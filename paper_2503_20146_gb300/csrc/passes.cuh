@@ -37,6 +37,20 @@ __host__ __device__ constexpr size_t row_smem_bytes(int n) {
 
 
 
+// Barrier of the two rows 2y', 2y' + 1 of a row-pass CTA (the packed passes):
+// the warp when both fit in one, else named barrier 8 + pair over their
+// 2 TPF threads (rows use ids 1..4 only when TPF > 32, so these stay clear).
+template <int N>
+__device__ __forceinline__ void pair_sync() {
+  constexpr int TPF = tpf_for(N), NT = row_threads(N);
+  if constexpr (2 * TPF <= 32) {
+    if constexpr (NT >= 32) __syncwarp();
+    else __syncwarp((1u << NT) - 1u);
+  } else {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(8 + (int)(threadIdx.x / (2 * TPF))), "n"(2 * TPF) : "memory");
+  }
+}
+
 template <int OP>
 struct RowT {
   static constexpr bool ifft_in = !(OP == ROW_EXP_FFT || OP == ROW_REAL_FFT || OP == ROW_FFT || OP == ROW_MODE_VG);
@@ -157,6 +171,25 @@ __device__ __forceinline__ void block_reduce_add(const float (&part)[5], double*
 }
 
 // ---------------------------------------------------------------------------
+// packed real rows
+// ---------------------------------------------------------------------------
+// The intensity |v|^2 and the residual field G of the IOTF form are real, so
+// the row spectrum of row y has X(y, n - kx) = conj X(y, kx). The packed
+// passes keep two rows in one complex row, Z(y', kx) = X(2y', kx) + i X(2y' + 1,
+// kx) (the row DFT of I(2y') + i I(2y' + 1)), stored on the even row 2y' of the
+// field, and the column pass rebuilds
+//   X(2y', kx)     = (Z(y', kx) + conj Z(y', n - kx)) / 2,
+//   X(2y' + 1, kx) = (Z(y', kx) - conj Z(y', n - kx)) / (2i)
+// for kx = 0..n/2 only (the other half is the conjugate). In a packed row, bin
+// kx sits at position kx for kx <= n/2 and at n/2 + (n - kx) above, so that
+// the bins kx and n - kx of an aligned pair of columns sit in two aligned
+// pairs of positions n/2 apart (bins 0 and n/2 pair with each other).
+template <int N>
+__device__ __forceinline__ int pk_pos(int kx) {
+  return kx <= N / 2 ? kx : 3 * N / 2 - kx;
+}
+
+// ---------------------------------------------------------------------------
 // row pass
 // ---------------------------------------------------------------------------
 // One row of a row pass: thread t of the TPF threads that own row `row`
@@ -182,7 +215,7 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
     if constexpr (OP == ROW_MODE_INT) {
       if (a.accumulate) l2_prefetch(a.f_out + rb, N * sizeof(float));
     }
-    if constexpr (OP == ROW_MUL_V) l2_prefetch(a.v + rb, N * sizeof(float2));
+    if constexpr (OP == ROW_MUL_V || OP == ROW_MUL_V_PK) l2_prefetch(a.v + rb, N * sizeof(float2));
     if constexpr (OP == ROW_RESID || OP == ROW_COH_RESID || OP == ROW_COH_VJP) l2_prefetch(a.y + rb, N * sizeof(float));
     if constexpr (OP == ROW_GRAD_PACK || OP == ROW_GRAD_OUT) l2_prefetch(a.psi + rb, N * sizeof(float2));
     if constexpr (OP == ROW_NESTEROV_FFT || OP == ROW_NESTEROV) {
@@ -193,7 +226,14 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
   }
 
   // ---- input ----
-  if constexpr (T::ifft_in) {
+  if constexpr (OP == ROW_MUL_V_PK) {
+    // both rows of the pair read packed row y' (stored on the even row)
+    const size_t rbe = rb - (size_t)(yrow & 1) * N;
+#pragma unroll
+    for (int j = 0; j < EPT; j++) v[j] = a.in[rbe + pk_pos<N>(slot_index<N, RK>(t, j))];
+    pair_sync<N>();  // every read of the even row precedes that row's output
+    fft_run<N, INV>(v, sm, t, a.tw_inv);
+  } else if constexpr (T::ifft_in) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = a.in[rb + slot_index<N, RK>(t, j)];
     fft_run<N, INV>(v, sm, t, a.tw_inv);
@@ -235,6 +275,33 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
       if (a.v != nullptr) a.v[rb + x] = v[j];
       v[j] = make_float2(cabs2(v[j]), 0.f);
     }
+  } else if constexpr (OP == ROW_INTENSITY_PK) {
+    // I = |v|^2 of this row and of its partner row of the pair (the rows of a
+    // CTA come in pairs 2y', 2y' + 1), packed as z = I(2y') + i I(2y' + 1);
+    // both rows transform the same z and store half of it each
+    const bool odd = (yrow & 1) != 0;
+    float* own = reinterpret_cast<float*>(sm.base);  // the row buffers as plain float arrays
+    const float* other = reinterpret_cast<const float*>(sm.base + (odd ? -row_smem_len(N) : row_smem_len(N)));
+    pair_sync<N>();  // the inverse transforms' last reads of both buffers are done
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int x = slot_index<N, RS>(t, j);
+      if (a.v != nullptr) a.v[rb + x] = v[j];
+      v[j].x = cabs2(v[j]);
+      own[x] = v[j].x;
+    }
+    pair_sync<N>();
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float ip = other[slot_index<N, RS>(t, j)];
+      v[j] = odd ? make_float2(ip, v[j].x) : make_float2(v[j].x, ip);
+    }
+    pair_sync<N>();  // the partner's reads precede the forward transform's writes
+  } else if constexpr (OP == ROW_MUL_V_PK) {
+    // the inverse transform of the packed row is G(2y') + i G(2y' + 1)
+    const bool odd = (yrow & 1) != 0;
+#pragma unroll
+    for (int j = 0; j < EPT; j++) v[j] = cscale(a.v[rb + slot_index<N, RS>(t, j)], odd ? v[j].y : v[j].x);
   } else if constexpr (OP == ROW_INTENSITY_OUT) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.f_out[rb + slot_index<N, RS>(t, j)] = cabs2(v[j]);
@@ -346,6 +413,13 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
     fft_run<N, FWD>(v, sm2, t2, a.tw_fwd);
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t2, j)] = v[j];
+  } else if constexpr (OP == ROW_INTENSITY_PK) {
+    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+    const bool odd = (yrow & 1) != 0;
+    const size_t rbe = rb - (odd ? (size_t)N : 0);
+#pragma unroll
+    for (int j = 0; j < EPT; j++)
+      if ((j < EPT / 2) != odd) a.out[rbe + pk_pos<N>(slot_index<N, RK>(t, j))] = v[j];
   } else if constexpr (T::fft_out) {
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
@@ -780,6 +854,163 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
     }
     if constexpr (OP == COL_RESID_IOTF2) block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, cur);
     __syncthreads();  // cur is refilled by the prefetch of the next-but-one tile
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// packed residual column pass (COL_RESID_PK)
+// ---------------------------------------------------------------------------
+// COL_RESID_IOTF2 on the packed rows of ROW_INTENSITY_PK: a tile is C packed
+// positions [c0, c0 + C) (bins kx = c0..c0 + C - 1) and the C positions n/2
+// apart that hold their mirror bins nx - kx, both halves staged by cp.async
+// (16-byte chunks) into one buffer, front rows first. Each thread rebuilds the
+// full-length columns kx, kx + 1 of the row spectrum from the two halves,
+// transforms the pair, forms IOTF (IOTF F{I} - F{y}) and the loss (weight 2:
+// the mirror bin nx - kx carries the same |.|^2), transforms back, and writes
+// the packed residual: the thread holding row 2y' the front pair
+// G(2y') + i G(2y' + 1), the one holding 2y' + 1 the mirror pair
+// conj G(2y') + i conj G(2y' + 1) (the partner's value comes by shuffle).
+// The self-mirrored bins 0 and nx/2 share the first lane of the first tile:
+// their real columns ride as one complex column X(., 0) + i X(., nx/2), split
+// after the forward transform through shared memory (X^(-ky) pairs with
+// X^(ky)), filtered apart and packed again (the results are real columns).
+// Needs the thread holding row y to hold the same slots as the one holding
+// y ^ 1 two lanes apart by C/2 (pk_col_ok).
+template <int N>
+__host__ __device__ constexpr bool pk_col_ok() {
+  return tpf_for(N) % 2 == 0 && (N / first_radix<N, FWD>()) % 2 == 0 && ept_for(N) % 2 == 0;
+}
+
+template <int N, int C>
+__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_kernel_pk(const PassArgs a, int nproj) {
+  pdl_wait();
+  constexpr int EPT = ept_for(N);
+  constexpr int NT = col2_threads(N, C);
+  constexpr int RS = first_radix<N, FWD>();
+  constexpr int RK = last_radix<N, FWD>();
+  constexpr int H = N / 2;             // packed rows
+  constexpr int CHUNKS = H * C / 2;    // 16-byte chunks per half tile
+  static_assert(CHUNKS % NT == 0, "half-tile chunks must divide evenly");
+  static_assert(pk_col_ok<N>(), "row parity must follow the thread index");
+  extern __shared__ float2 smem[];
+
+  const int tid = threadIdx.x;
+  const int c2 = tid % (C / 2), t = tid / (C / 2);
+  const int hx = a.nx / 2;
+  const int tiles_per_proj = hx / C;
+  const int ntiles = nproj * tiles_per_proj;
+  const size_t ldp = 2 * (size_t)a.nx;  // packed rows sit on the even rows of the field
+  const bool odd = (t & 1) != 0;        // this thread holds the odd rows 2y' + 1
+  const ColPairLayout<C> sm{smem + 2 * c2};
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int proj = a.proj0 + tile / tiles_per_proj;
+    const int c0 = (tile % tiles_per_proj) * C;
+    if (skip_proj(a, proj)) continue;  // uniform over the CTA
+    const size_t pbase = (size_t)proj * a.ny * a.nx;
+#pragma unroll
+    for (int k = 0; k < 2 * CHUNKS / NT; k++) {
+      const int q = tid + k * NT;
+      const int half = q / CHUNKS, qq = q - half * CHUNKS;
+      const int row = qq / (C / 2), pr = qq % (C / 2);
+      cp_async16(smem + col_row(half * H + row, C) * C + 2 * pr,
+                 a.in + pbase + (size_t)row * ldp + (half ? hx : 0) + c0 + 2 * pr);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    const int kx = c0 + 2 * c2;             // bins kx, kx + 1 (mirrors nx - kx, nx - kx - 1)
+    const bool special = kx == 0;           // first lane of the first tile: bins 0 and nx/2
+    float2 v[EPT], u[EPT];
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int yp = (t >> 1) + (slot_index<N, RS>(0, j) >> 1);  // the row pair of slot j (t's parity is y's)
+      const float4 f = sm[yp], m = sm[H + yp];
+      if (special) {  // X(., 0) + i X(., nx/2): the real parts (even y) or imaginary parts (odd y)
+        v[j] = odd ? make_float2(f.y, m.y) : make_float2(f.x, m.x);
+      } else if (odd) {
+        v[j] = make_float2(0.5f * (f.y + m.y), 0.5f * (m.x - f.x));
+      } else {
+        v[j] = make_float2(0.5f * (f.x + m.x), 0.5f * (f.y - m.y));
+      }
+      u[j] = odd ? make_float2(0.5f * (f.w + m.w), 0.5f * (m.z - f.z))
+                 : make_float2(0.5f * (f.z + m.z), 0.5f * (f.w - m.w));
+      asm volatile("" ::: "memory");  // one slot's two loads at a time: fewer live registers
+    }
+    fft_run2<N, FWD>(v, u, sm, t, a.tw_fwd);
+
+    if (c0 == 0) {  // uniform over the CTA: the special column's spectrum through shared memory
+      __syncthreads();  // the transform's last reads are done
+      if (special)
+#pragma unroll
+        for (int j = 0; j < EPT; j++) sm[slot_index<N, RK>(t, j)] = make_float4(v[j].x, v[j].y, 0.f, 0.f);
+      __syncthreads();
+    }
+    const float ia = __ldg(&a.ix[kx]), ib = __ldg(&a.ix[kx + 1]);
+    const float wv = special ? 0.f : 2.f;  // the special lane's v is redone below
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const int ky = slot_index<N, RK>(t, j);
+      const float iy = __ldg(&a.iy[ky]);
+      const float4 yh = *reinterpret_cast<const float4*>(a.yhat + pbase + (size_t)ky * a.nx + kx);
+      const float wa = ia * iy, wb = ib * iy;
+      const float2 ra = make_float2(fmaf(wa, v[j].x, -yh.x), fmaf(wa, v[j].y, -yh.y));
+      const float2 rb = make_float2(fmaf(wb, u[j].x, -yh.z), fmaf(wb, u[j].y, -yh.w));
+      part[0] = fmaf(wv * ra.x, ra.x, fmaf(wv * ra.y, ra.y, part[0]));
+      part[0] = fmaf(2.f * rb.x, rb.x, fmaf(2.f * rb.y, rb.y, part[0]));
+      v[j] = cscale(ra, wa * a.scale);
+      u[j] = cscale(rb, wb * a.scale);
+    }
+    if (special) {
+      // X^0(ky) = (V(ky) + conj V(-ky)) / 2, X^h(ky) = (V(ky) - conj V(-ky)) / (2i), each
+      // filtered with its own bin's IOTF and F{y}, then packed again as g0 + i gh
+      const float i0 = __ldg(&a.ix[0]), ih = __ldg(&a.ix[hx]);
+#pragma unroll
+      for (int j = 0; j < EPT; j++) {
+        const int ky = slot_index<N, RK>(t, j);
+        const float iy = __ldg(&a.iy[ky]);
+        const float2 p = reinterpret_cast<const float2&>(sm[ky]);
+        const float2 q = reinterpret_cast<const float2&>(sm[ky == 0 ? 0 : N - ky]);
+        const float2 x0 = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
+        const float2 xh = make_float2(0.5f * (p.y + q.y), 0.5f * (q.x - p.x));
+        const float2 y0 = a.yhat[pbase + (size_t)ky * a.nx];
+        const float2 yh = a.yhat[pbase + (size_t)ky * a.nx + hx];
+        const float w0 = i0 * iy, wh = ih * iy;
+        const float2 r0 = make_float2(fmaf(w0, x0.x, -y0.x), fmaf(w0, x0.y, -y0.y));
+        const float2 rh = make_float2(fmaf(wh, xh.x, -yh.x), fmaf(wh, xh.y, -yh.y));
+        part[0] = fmaf(r0.x, r0.x, fmaf(r0.y, r0.y, part[0]));
+        part[0] = fmaf(rh.x, rh.x, fmaf(rh.y, rh.y, part[0]));
+        const float2 g0 = cscale(r0, w0 * a.scale), gh = cscale(rh, wh * a.scale);
+        v[j] = make_float2(g0.x - gh.y, g0.y + gh.x);
+        asm volatile("" ::: "memory");
+      }
+    }
+    part[0] *= a.scale;
+    fft_run2<N, INV>(v, u, sm, t, a.tw_inv);
+
+    // packed output: rows 2y' and 2y' + 1 of a column sit C/2 lanes apart
+#pragma unroll
+    for (int j = 0; j < EPT; j++) {
+      const float2 pv = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, C / 2), __shfl_xor_sync(0xffffffffu, v[j].y, C / 2));
+      const float2 pu = make_float2(__shfl_xor_sync(0xffffffffu, u[j].x, C / 2), __shfl_xor_sync(0xffffffffu, u[j].y, C / 2));
+      const float2 ve = odd ? pv : v[j], vo = odd ? v[j] : pv;
+      const float2 ue = odd ? pu : u[j], uo = odd ? u[j] : pu;
+      float4 o;
+      if (!odd) {  // front: G(2y') + i G(2y' + 1)
+        const float2 fv = special ? make_float2(ve.x, vo.x) : make_float2(ve.x - vo.y, ve.y + vo.x);
+        o = make_float4(fv.x, fv.y, ue.x - uo.y, ue.y + uo.x);
+      } else {     // mirror: conj G(2y') + i conj G(2y' + 1)
+        const float2 mv = special ? make_float2(ve.y, vo.y) : make_float2(ve.x + vo.y, vo.x - ve.y);
+        o = make_float4(mv.x, mv.y, ue.x + uo.y, uo.x - ue.y);
+      }
+      *reinterpret_cast<float4*>(a.out + pbase + (size_t)((t >> 1) + (slot_index<N, RS>(0, j) >> 1)) * ldp +
+                                 (odd ? hx : 0) + kx) = o;
+    }
+    block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, smem);
+    __syncthreads();  // the buffer is refilled by the next tile's copy
   }
   cp_async_wait<0>();
 }
@@ -1270,6 +1501,49 @@ template <int N, int OP, int C, int PIPE>
 int ColShape<N, OP, C, PIPE>::resident = 1;
 
 
+// Packed residual shapes (COL_RESID_PK): persistent, one staged buffer, column
+// pairs (described like the single-buffered pair shapes, pipe code 4).
+template <int N, int C>
+struct PkShape {
+  static int resident;
+  static cudaError_t prep() {
+    constexpr size_t SM = col_smem_bytes(N, C);
+    cudaError_t e = cudaFuncSetAttribute(col_kernel_pk<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+    if (e != cudaSuccess) return e;
+    int r = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, col_kernel_pk<N, C>, col2_threads(N, C), SM);
+    resident = r > 0 ? r : 1;
+    return e;
+  }
+  static cudaError_t launch(const PassArgs& a, int nproj, cudaStream_t s) {
+    const long long ntiles = (long long)nproj * (a.nx / 2 / C);
+    const long long slots = (long long)device_sms() * resident;
+    const int grid = (int)(ntiles < slots ? ntiles : slots);
+    return launch_pass(col_kernel_pk<N, C>, dim3(grid), dim3(col2_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a,
+                       nproj);
+  }
+};
+template <int N, int C>
+int PkShape<N, C>::resident = 1;
+
+// whole warps (the output pairs rows by shuffle), even chunk split; a plan
+// takes a shape only where C divides nx/2 (pk_fits)
+template <int N, int C>
+constexpr bool pk_shape_ok() {
+  constexpr int th = col2_threads(N, C);
+  return pk_col_ok<N>() && C <= 16 && th >= 32 && th <= 512 && th % 32 == 0 && (N / 2 * C / 2) % th == 0 &&
+         col_smem_bytes(N, C) <= 200 * 1024;
+}
+
+template <int N, int C>
+void add_pk_variant(LengthKernels& k) {
+  if constexpr (pk_shape_ok<N, C>()) {
+    int& n = k.ncolv[COL_RESID_PK];
+    if (n < MAX_COL_VARIANTS)
+      k.colv[COL_RESID_PK][n++] = {PkShape<N, C>::launch, PkShape<N, C>::prep, C, 4, PWF_SCHED_VARIANT};
+  }
+}
+
 // Mode column pass shapes: tile width C, one column per thread or the pair of
 // adjacent columns. The first one registered is the default before tuning:
 // 8 columns per tile from length 1024 on (4 where 8 would exceed 512
@@ -1407,6 +1681,9 @@ void add_schedule_shapes(LengthKernels& k) {
   op_shapes(std::integral_constant<int, COL_PRECOND_REG>{});
   op_shapes(std::integral_constant<int, COL_FFT>{});
   op_shapes(std::integral_constant<int, COL_IFFT>{});
+  add_pk_variant<N, 8>(k);  // the packed residual pass
+  add_pk_variant<N, 4>(k);
+  add_pk_variant<N, 16>(k);
   add_mode_op<N, CM_FWD>(k);  // and the mode column passes
   add_mode_op<N, CM_BACK>(k);
 }
@@ -1423,6 +1700,7 @@ LengthKernels make_length_kernels() {
   PWF_ROW(ROW_INTENSITY) PWF_ROW(ROW_INTENSITY_OUT) PWF_ROW(ROW_REAL_OUT) PWF_ROW(ROW_RESID)
   PWF_ROW(ROW_COH_RESID) PWF_ROW(ROW_COH_VJP) PWF_ROW(ROW_MUL_V) PWF_ROW(ROW_GRAD_OUT) PWF_ROW(ROW_GRAD_PACK)
   PWF_ROW(ROW_NESTEROV_FFT) PWF_ROW(ROW_NESTEROV) PWF_ROW(ROW_GRADT) PWF_ROW(ROW_MODE_INT) PWF_ROW(ROW_MODE_VG)
+  PWF_ROW(ROW_INTENSITY_PK) PWF_ROW(ROW_MUL_V_PK)
 #undef PWF_ROW
   add_col_op<N, COL_Q>(k);
   add_col_op<N, COL_IOTF>(k);
@@ -1430,6 +1708,9 @@ LengthKernels make_length_kernels() {
   add_col_op<N, COL_PRECOND_REG>(k);
   add_col_op<N, COL_FFT>(k);
   add_col_op<N, COL_IFFT>(k);
+  add_pk_variant<N, 8>(k);  // first entry = default before tuning (fits every nx >= 16)
+  add_pk_variant<N, 4>(k);
+  add_pk_variant<N, 16>(k);
   add_mode_op<N, CM_FWD>(k);
   add_mode_op<N, CM_BACK>(k);
   return k;

@@ -26,6 +26,7 @@ FLAG_GRAPH = 0x40
 FLAG_CLUSTER = 0x80
 FLAG_NO_PDL = 0x100
 FLAG_CHECK_FINITE = 0x200
+FLAG_UNPACKED_RESID = 0x400
 
 STATUS = {0: "PWF_OK", 1: "PWF_ERR_INVALID_ARG", 2: "PWF_ERR_UNSUPPORTED", 3: "PWF_ERR_NOMEM",
           4: "PWF_ERR_CUDA", 5: "PWF_ERR_NONFINITE", 6: "PWF_ERR_STATE", 7: "PWF_ERR_TIMEOUT",

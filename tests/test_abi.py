@@ -42,7 +42,7 @@ def _desc(**kw):
     (dict(batch=0), 1),
     (dict(eta=0.0), 1),
     (dict(pixel_m=-1.0), 1),
-    (dict(flags=0x400), 1),        # not a flag
+    (dict(flags=0x800), 1),        # not a flag
     (dict(flags=0x200 | 0x20), 2),  # scans follow the passes, not a single launch
     (dict(flags=0x80 | 0x40), 1),  # two ways to run pwf_solve
     (dict(flags=0x80 | 0x20), 1),

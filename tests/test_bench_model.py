@@ -15,8 +15,21 @@ def modal_passes(k):
                                                                      "row_nesterov_fft"])
 
 
+def iotf_packed_passes():
+    p = iotf_passes()
+    i = p.index("row_intensity")
+    p[i:i + 3] = ["row_intensity_pk", "col_resid_pk", "row_mul_v_pk"]
+    return p
+
+
 def test_iotf_iteration_is_296_bytes_per_pixel():
     assert sum(bench.PASS_BYTES_PER_PX[p] for p in iotf_passes()) == 296
+
+
+def test_packed_residual_saves_20_bytes_per_pixel():
+    # packed F_row{|v|^2} and residual: 4 B/px each way instead of 8; the
+    # column pass reads F{y} of bins 0..nx/2 only
+    assert sum(bench.PASS_BYTES_PER_PX[p] for p in iotf_packed_passes()) == 276
 
 
 def test_modal_iteration_matches_the_closed_form():

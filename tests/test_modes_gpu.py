@@ -106,10 +106,10 @@ def test_every_mode_shape_matches_oracle(pwf, name, K, batch, ny, nx):
     f_ref = O.modal_intensity(P64, T64, geom, modes)
     g_ref, _ = O.modal_gradient(P64, T64, y[b].astype(np.float64), geom, modes)
     with modal_plan(pwf, geom, batch, K) as plan:
-        counts = [pwf.pwf_plan_column_shapes(plan.handle, m) for m in (6, 7)]
+        counts = [pwf.pwf_plan_column_shapes(plan.handle, m) for m in (7, 8)]
         assert min(counts) >= 2
         for k in range(max(counts)):
-            for m, c in zip((6, 7), counts):
+            for m, c in zip((7, 8), counts):
                 pwf.pwf_plan_set_column_shape(plan.handle, m, min(k, c - 1))
             f = plan.forward(dev(psi), dev(t)).cpu().numpy()
             g, _ = plan.gradient(dev(psi), dev(t), dev(y))

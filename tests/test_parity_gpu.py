@@ -348,10 +348,10 @@ def test_every_column_shape_matches_oracle(pwf, ny, nx, batch):
     g_ref, _ = O.wirtinger_gradient(P64[b], T64, y[b].astype(np.float64), geom)
     ref3 = O.solve(y[b].astype(np.float64), T64, geom, 2)
     with plan_for(pwf, geom, batch) as plan:
-        nshape = max(pwf.pwf_plan_column_shapes(plan.handle, op) for op in range(6))
+        nshape = max(pwf.pwf_plan_column_shapes(plan.handle, op) for op in range(7))
         assert nshape >= 3
         for k in range(nshape):
-            for op in range(6):
+            for op in range(7):
                 n_op = pwf.pwf_plan_column_shapes(plan.handle, op)
                 pwf.pwf_plan_set_column_shape(plan.handle, op, min(k, n_op - 1))
             f = plan.forward(dev(psi), dev(t)).cpu().numpy()
@@ -394,3 +394,40 @@ def test_full_size_tomo_forward_sampled(pwf, tomo):
     for b in (0, 97, 179):
         expect = O.intensity(psi32[b].cpu().numpy().astype(np.complex128), t32.astype(np.complex128), geom)
         assert rel_l2(f[b].cpu().numpy(), expect) <= FWD_TOL
+
+
+# ----------------------------------------------------------------------------
+# packed residual passes (two real rows per complex row, bins 0..nx/2)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("ny,nx,batch", [(1024, 256, 3), (128, 96, 4), (768, 128, 3), (64, 16, 4), (2048, 64, 2),
+                                           (1536, 64, 2)],
+                         ids=["1024x256", "128x96", "768x128", "64x16", "2048x64", "1536x64"])
+def test_packed_residual_matches_unpacked_and_oracle(pwf, ny, nx, batch):
+    # The default IOTF iteration carries |v|^2 and the residual as packed real
+    # rows and filters only bins kx = 0..nx/2 (the rest are their conjugates);
+    # PWF_FLAG_UNPACKED_RESID runs the full complex form. Both against the
+    # oracle's iterates and losses, per projection; and the packed form about
+    # as close to the FP64 iterates as the unpacked one. The two FP32 paths
+    # round in a different order (and the tuner may give them different radix
+    # schedules), so at rounding level (1e-5..1e-4 relative after 4
+    # iterations) their errors differ by factors up to ~2 from run to run; a
+    # mistake in the packing (a lost half, a wrong conjugate) is O(1).
+    w = W2
+    geom, t, y = _solve_case(w, batch, ny, nx)
+    n = 4
+    ref = [O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, n) for b in range(batch)]
+    out = {}
+    for flags in (0, pwf.FLAG_UNPACKED_RESID):
+        psi = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+        with plan_for(pwf, geom, batch, flags) as plan:
+            iters, loss = plan.solve(dev(y), dev(t), psi, n)
+            desc = pwf.pwf_plan_describe(plan.handle)
+        out[flags] = psi.cpu().numpy()
+        for b in range(batch):
+            assert iters[b] == n
+            assert phase_rms(out[flags][b], ref[b].psi) <= PHASE_TOL, (flags, b, desc)
+            assert abs(loss[b] - ref[b].losses[-1]) <= 1e-4 * ref[b].losses[-1], (flags, b, desc)
+    exact = np.stack([r.psi for r in ref])
+    err_pk = rel_l2(out[0], exact)
+    err_un = rel_l2(out[pwf.FLAG_UNPACKED_RESID], exact)
+    assert err_pk <= 2.0 * max(err_un, 5e-5), (err_pk, err_un)
