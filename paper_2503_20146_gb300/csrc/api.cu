@@ -705,6 +705,7 @@ cudaError_t col(pwf_plan* p, int op, PassArgs a, int nproj) {
   a = sched_tables(p, col_args(p, a), p->kcol->colv[op][p->colsel[op]].sched);
   cudaError_t e =
       enqueue(p, kColNames[op], [&] { return p->kcol->colv[op][p->colsel[op]].launch(a, nproj, p->stream); });
+  if (op == COL_RESID_PK) p->launches++;  // its second kernel: bins 0 and nx/2
   return e != cudaSuccess ? e : scan_pass(p, kColNames[op], a, nproj, op, false);
 }
 cudaError_t col_q(pwf_plan* p, PassArgs a, int which, int conj, int nproj) {

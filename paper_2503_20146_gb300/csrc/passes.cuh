@@ -862,21 +862,20 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
 // packed residual column pass (COL_RESID_PK)
 // ---------------------------------------------------------------------------
 // COL_RESID_IOTF2 on the packed rows of ROW_INTENSITY_PK: a tile is C packed
-// positions [c0, c0 + C) (bins kx = c0..c0 + C - 1) and the C positions n/2
+// positions [c0, c0 + C) (bins kx = c0..c0 + C - 1) and the C positions nx/2
 // apart that hold their mirror bins nx - kx, both halves staged by cp.async
-// (16-byte chunks) into one buffer, front rows first. Each thread rebuilds the
-// full-length columns kx, kx + 1 of the row spectrum from the two halves,
-// transforms the pair, forms IOTF (IOTF F{I} - F{y}) and the loss (weight 2:
-// the mirror bin nx - kx carries the same |.|^2), transforms back, and writes
-// the packed residual: the thread holding row 2y' the front pair
-// G(2y') + i G(2y' + 1), the one holding 2y' + 1 the mirror pair
-// conj G(2y') + i conj G(2y' + 1) (the partner's value comes by shuffle).
-// The self-mirrored bins 0 and nx/2 share the first lane of the first tile:
-// their real columns ride as one complex column X(., 0) + i X(., nx/2), split
-// after the forward transform through shared memory (X^(-ky) pairs with
-// X^(ky)), filtered apart and packed again (the results are real columns).
+// (16-byte chunks) into one buffer, front rows first. The threads rebuild the
+// full-length columns kx, kx + 1 of the row spectrum in place in shared memory
+// (every read of the packed halves before any write), transform each column
+// pair, form IOTF (IOTF F{I} - F{y}) and the loss (weight 2: the mirror bin
+// nx - kx carries the same sum of |.|^2), transform back and write the packed
+// residual: the thread holding row 2y' the front pair G(2y') + i G(2y' + 1),
+// the one holding 2y' + 1 the mirror pair conj G(2y') + i conj G(2y' + 1)
+// (the partner's value comes by shuffle). Bins 0 and nx/2 are their own
+// mirrors; the first lane of the first tile leaves them (its first column is
+// computed and dropped) to col_kernel_pk_edge, which runs after this kernel.
 // Needs the thread holding row y to hold the same slots as the one holding
-// y ^ 1 two lanes apart by C/2 (pk_col_ok).
+// y ^ 1, C/2 lanes apart (pk_col_ok).
 template <int N>
 __host__ __device__ constexpr bool pk_col_ok() {
   return tpf_for(N) % 2 == 0 && (N / first_radix<N, FWD>()) % 2 == 0 && ept_for(N) % 2 == 0;
@@ -886,11 +885,12 @@ template <int N, int C>
 __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_kernel_pk(const PassArgs a, int nproj) {
   pdl_wait();
   constexpr int EPT = ept_for(N);
+  constexpr int TPFC = tpf_for(N);      // threads per column pair
   constexpr int NT = col2_threads(N, C);
   constexpr int RS = first_radix<N, FWD>();
   constexpr int RK = last_radix<N, FWD>();
-  constexpr int H = N / 2;             // packed rows
-  constexpr int CHUNKS = H * C / 2;    // 16-byte chunks per half tile
+  constexpr int H = N / 2;              // packed rows
+  constexpr int CHUNKS = H * C / 2;     // 16-byte chunks per half tile
   static_assert(CHUNKS % NT == 0, "half-tile chunks must divide evenly");
   static_assert(pk_col_ok<N>(), "row parity must follow the thread index");
   extern __shared__ float2 smem[];
@@ -921,36 +921,39 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
     cp_async_wait<0>();
     __syncthreads();
 
-    const int kx = c0 + 2 * c2;             // bins kx, kx + 1 (mirrors nx - kx, nx - kx - 1)
-    const bool special = kx == 0;           // first lane of the first tile: bins 0 and nx/2
+    const int kx = c0 + 2 * c2;      // bins kx, kx + 1 (mirrors nx - kx, nx - kx - 1)
+    const bool edge = kx == 0;       // bin 0 (and nx/2): col_kernel_pk_edge's
+    {
+      // X(2y') = (Z + conj Zm) / 2 and X(2y' + 1) = (Z - conj Zm) / (2i) of
+      // both columns, from the front (Z) and mirror (Zm) rows y'
+      float4 f[EPT / 2], m[EPT / 2];
+#pragma unroll
+      for (int k = 0; k < EPT / 2; k++) {
+        f[k] = sm[t + k * TPFC];
+        m[k] = sm[H + t + k * TPFC];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < EPT / 2; k++) {
+        const int yp = t + k * TPFC;
+        const float4 z = f[k], w = m[k];
+        sm[2 * yp] = make_float4(0.5f * (z.x + w.x), 0.5f * (z.y - w.y), 0.5f * (z.z + w.z), 0.5f * (z.w - w.w));
+        sm[2 * yp + 1] = make_float4(0.5f * (z.y + w.y), 0.5f * (w.x - z.x), 0.5f * (z.w + w.w), 0.5f * (w.z - z.z));
+      }
+      __syncthreads();
+    }
     float2 v[EPT], u[EPT];
     float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int yp = (t >> 1) + (slot_index<N, RS>(0, j) >> 1);  // the row pair of slot j (t's parity is y's)
-      const float4 f = sm[yp], m = sm[H + yp];
-      if (special) {  // X(., 0) + i X(., nx/2): the real parts (even y) or imaginary parts (odd y)
-        v[j] = odd ? make_float2(f.y, m.y) : make_float2(f.x, m.x);
-      } else if (odd) {
-        v[j] = make_float2(0.5f * (f.y + m.y), 0.5f * (m.x - f.x));
-      } else {
-        v[j] = make_float2(0.5f * (f.x + m.x), 0.5f * (f.y - m.y));
-      }
-      u[j] = odd ? make_float2(0.5f * (f.w + m.w), 0.5f * (m.z - f.z))
-                 : make_float2(0.5f * (f.z + m.z), 0.5f * (f.w - m.w));
-      asm volatile("" ::: "memory");  // one slot's two loads at a time: fewer live registers
+      const float4 q = sm[slot_index<N, RS>(t, j)];
+      v[j] = make_float2(q.x, q.y);
+      u[j] = make_float2(q.z, q.w);
     }
     fft_run2<N, FWD>(v, u, sm, t, a.tw_fwd);
 
-    if (c0 == 0) {  // uniform over the CTA: the special column's spectrum through shared memory
-      __syncthreads();  // the transform's last reads are done
-      if (special)
-#pragma unroll
-        for (int j = 0; j < EPT; j++) sm[slot_index<N, RK>(t, j)] = make_float4(v[j].x, v[j].y, 0.f, 0.f);
-      __syncthreads();
-    }
     const float ia = __ldg(&a.ix[kx]), ib = __ldg(&a.ix[kx + 1]);
-    const float wv = special ? 0.f : 2.f;  // the special lane's v is redone below
+    const float wv = edge ? 0.f : 2.f;  // the edge lane's first column is not this kernel's
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
       const int ky = slot_index<N, RK>(t, j);
@@ -964,30 +967,6 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
       v[j] = cscale(ra, wa * a.scale);
       u[j] = cscale(rb, wb * a.scale);
     }
-    if (special) {
-      // X^0(ky) = (V(ky) + conj V(-ky)) / 2, X^h(ky) = (V(ky) - conj V(-ky)) / (2i), each
-      // filtered with its own bin's IOTF and F{y}, then packed again as g0 + i gh
-      const float i0 = __ldg(&a.ix[0]), ih = __ldg(&a.ix[hx]);
-#pragma unroll
-      for (int j = 0; j < EPT; j++) {
-        const int ky = slot_index<N, RK>(t, j);
-        const float iy = __ldg(&a.iy[ky]);
-        const float2 p = reinterpret_cast<const float2&>(sm[ky]);
-        const float2 q = reinterpret_cast<const float2&>(sm[ky == 0 ? 0 : N - ky]);
-        const float2 x0 = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
-        const float2 xh = make_float2(0.5f * (p.y + q.y), 0.5f * (q.x - p.x));
-        const float2 y0 = a.yhat[pbase + (size_t)ky * a.nx];
-        const float2 yh = a.yhat[pbase + (size_t)ky * a.nx + hx];
-        const float w0 = i0 * iy, wh = ih * iy;
-        const float2 r0 = make_float2(fmaf(w0, x0.x, -y0.x), fmaf(w0, x0.y, -y0.y));
-        const float2 rh = make_float2(fmaf(wh, xh.x, -yh.x), fmaf(wh, xh.y, -yh.y));
-        part[0] = fmaf(r0.x, r0.x, fmaf(r0.y, r0.y, part[0]));
-        part[0] = fmaf(rh.x, rh.x, fmaf(rh.y, rh.y, part[0]));
-        const float2 g0 = cscale(r0, w0 * a.scale), gh = cscale(rh, wh * a.scale);
-        v[j] = make_float2(g0.x - gh.y, g0.y + gh.x);
-        asm volatile("" ::: "memory");
-      }
-    }
     part[0] *= a.scale;
     fft_run2<N, INV>(v, u, sm, t, a.tw_inv);
 
@@ -998,21 +977,87 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
       const float2 pu = make_float2(__shfl_xor_sync(0xffffffffu, u[j].x, C / 2), __shfl_xor_sync(0xffffffffu, u[j].y, C / 2));
       const float2 ve = odd ? pv : v[j], vo = odd ? v[j] : pv;
       const float2 ue = odd ? pu : u[j], uo = odd ? u[j] : pu;
-      float4 o;
-      if (!odd) {  // front: G(2y') + i G(2y' + 1)
-        const float2 fv = special ? make_float2(ve.x, vo.x) : make_float2(ve.x - vo.y, ve.y + vo.x);
-        o = make_float4(fv.x, fv.y, ue.x - uo.y, ue.y + uo.x);
-      } else {     // mirror: conj G(2y') + i conj G(2y' + 1)
-        const float2 mv = special ? make_float2(ve.y, vo.y) : make_float2(ve.x + vo.y, vo.x - ve.y);
-        o = make_float4(mv.x, mv.y, ue.x + uo.y, uo.x - ue.y);
-      }
-      *reinterpret_cast<float4*>(a.out + pbase + (size_t)((t >> 1) + (slot_index<N, RS>(0, j) >> 1)) * ldp +
-                                 (odd ? hx : 0) + kx) = o;
+      // front: G(2y') + i G(2y' + 1); mirror: conj G(2y') + i conj G(2y' + 1)
+      const float4 o = odd ? make_float4(ve.x + vo.y, vo.x - ve.y, ue.x + uo.y, uo.x - ue.y)
+                           : make_float4(ve.x - vo.y, ve.y + vo.x, ue.x - uo.y, ue.y + uo.x);
+      float2* dst = a.out + pbase + (size_t)((t >> 1) + (slot_index<N, RS>(0, j) >> 1)) * ldp + (odd ? hx : 0) + kx;
+      if (edge)
+        dst[1] = make_float2(o.z, o.w);
+      else
+        *reinterpret_cast<float4*>(dst) = o;
     }
     block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, smem);
     __syncthreads();  // the buffer is refilled by the next tile's copy
   }
   cp_async_wait<0>();
+}
+
+// Bins 0 and nx/2 of the packed residual pass, one CTA per projection, after
+// col_kernel_pk: both columns of the row spectrum are real (a real row's DC and
+// Nyquist bins), so they ride as one complex column W = X0 + i Xh, rebuilt from
+// packed positions 0 and nx/2 (X(2y') = Re Z(y'), X(2y' + 1) = Im Z(y')). After
+// the forward transform X0^(ky) = (W^(ky) + conj W^(-ky)) / 2 and
+// Xh^(ky) = (W^(ky) - conj W^(-ky)) / (2i) (through shared memory); each gets
+// its own bin's IOTF and F{y}, the loss (weight 1), and the two residuals go
+// back as one column g0 + i gh, whose inverse transform is G0 + i Gh (both
+// real), packed again into positions 0 and nx/2.
+template <int N>
+__global__ void __launch_bounds__(tpf_for(N)) col_kernel_pk_edge(const PassArgs a) {
+  pdl_wait();
+  constexpr int EPT = ept_for(N), TPF = tpf_for(N);
+  constexpr int RS = first_radix<N, FWD>(), RK = last_radix<N, FWD>();
+  extern __shared__ float2 smem[];
+  const int proj = a.proj0 + blockIdx.x;
+  if (skip_proj(a, proj)) return;
+  const int t = threadIdx.x;
+  const int hx = a.nx / 2;
+  const size_t pbase = (size_t)proj * a.ny * a.nx;
+  const size_t ldp = 2 * (size_t)a.nx;
+  const RowLayout<TPF, TPF> sm{smem, 1};
+  float2 v[EPT];
+#pragma unroll
+  for (int j = 0; j < EPT; j++) {
+    const int y = slot_index<N, RS>(t, j);
+    const float2 z0 = a.in[pbase + (size_t)(y >> 1) * ldp], zh = a.in[pbase + (size_t)(y >> 1) * ldp + hx];
+    v[j] = (y & 1) ? make_float2(z0.y, zh.y) : make_float2(z0.x, zh.x);
+  }
+  fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+  sm.sync();  // the transform's last reads are done
+#pragma unroll
+  for (int j = 0; j < EPT; j++) sm[slot_index<N, RK>(t, j)] = v[j];
+  sm.sync();
+  float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  const float i0 = __ldg(&a.ix[0]), ih = __ldg(&a.ix[hx]);
+#pragma unroll
+  for (int j = 0; j < EPT; j++) {
+    const int ky = slot_index<N, RK>(t, j);
+    const float2 p = v[j], q = sm[ky == 0 ? 0 : N - ky];
+    const float2 x0 = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
+    const float2 xh = make_float2(0.5f * (p.y + q.y), 0.5f * (q.x - p.x));
+    const float iy = __ldg(&a.iy[ky]);
+    const float w0 = i0 * iy, wh = ih * iy;
+    const float2 y0 = a.yhat[pbase + (size_t)ky * a.nx], yh = a.yhat[pbase + (size_t)ky * a.nx + hx];
+    const float2 r0 = make_float2(fmaf(w0, x0.x, -y0.x), fmaf(w0, x0.y, -y0.y));
+    const float2 rh = make_float2(fmaf(wh, xh.x, -yh.x), fmaf(wh, xh.y, -yh.y));
+    part[0] = fmaf(r0.x, r0.x, fmaf(r0.y, r0.y, part[0]));
+    part[0] = fmaf(rh.x, rh.x, fmaf(rh.y, rh.y, part[0]));
+    const float2 g0 = cscale(r0, w0 * a.scale), gh = cscale(rh, wh * a.scale);
+    v[j] = make_float2(g0.x - gh.y, g0.y + gh.x);  // g0 + i gh
+  }
+  part[0] *= a.scale;
+  fft_run<N, INV>(v, sm, t, a.tw_inv);  // its first write waits for the reads above
+  sm.sync();
+#pragma unroll
+  for (int j = 0; j < EPT; j++) sm[slot_index<N, RS>(t, j)] = v[j];
+  sm.sync();
+#pragma unroll
+  for (int k = 0; k < EPT / 2; k++) {
+    const int yp = t + k * TPF;
+    const float2 e = sm[2 * yp], o = sm[2 * yp + 1];
+    a.out[pbase + (size_t)yp * ldp] = make_float2(e.x, o.x);
+    a.out[pbase + (size_t)yp * ldp + hx] = make_float2(e.y, o.y);
+  }
+  block_reduce_add<1>(part, a.acc, proj * NACC + ACC_LOSS, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1519,8 +1564,12 @@ struct PkShape {
     const long long ntiles = (long long)nproj * (a.nx / 2 / C);
     const long long slots = (long long)device_sms() * resident;
     const int grid = (int)(ntiles < slots ? ntiles : slots);
-    return launch_pass(col_kernel_pk<N, C>, dim3(grid), dim3(col2_threads(N, C)), col_smem_bytes(N, C), s, a.pdl, a,
-                       nproj);
+    cudaError_t e = launch_pass(col_kernel_pk<N, C>, dim3(grid), dim3(col2_threads(N, C)), col_smem_bytes(N, C), s,
+                                a.pdl, a, nproj);
+    if (e != cudaSuccess) return e;
+    // then bins 0 and nx/2 of every projection
+    return launch_pass(col_kernel_pk_edge<N>, dim3(nproj), dim3(tpf_for(N)), row_smem_len(N) * sizeof(float2), s, a.pdl,
+                       a);
   }
 };
 template <int N, int C>

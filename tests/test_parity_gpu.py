@@ -406,28 +406,35 @@ def test_packed_residual_matches_unpacked_and_oracle(pwf, ny, nx, batch):
     # The default IOTF iteration carries |v|^2 and the residual as packed real
     # rows and filters only bins kx = 0..nx/2 (the rest are their conjugates);
     # PWF_FLAG_UNPACKED_RESID runs the full complex form. Both against the
-    # oracle's iterates and losses, per projection; and the packed form about
-    # as close to the FP64 iterates as the unpacked one. The two FP32 paths
-    # round in a different order (and the tuner may give them different radix
-    # schedules), so at rounding level (1e-5..1e-4 relative after 4
-    # iterations) their errors differ by factors up to ~2 from run to run; a
-    # mistake in the packing (a lost half, a wrong conjugate) is O(1).
+    # oracle: the first iteration's loss (the Parseval sum over the packed
+    # residual, weight 2 for mirrored bins) to 1e-5, the losses and iterates
+    # after 4 iterations to the usual tolerances. The 4-iteration iterates of
+    # the two FP32 forms are also held to the same order of error against the
+    # FP64 ones: their error there is low-frequency rounding that the
+    # preconditioner amplifies by up to ny nx, one realization per rounding
+    # order, so the two differ by small factors; a slip in the packing (a lost
+    # half, a wrong conjugate, a mis-weighted bin) is O(1).
     w = W2
     geom, t, y = _solve_case(w, batch, ny, nx)
     n = 4
     ref = [O.solve(y[b].astype(np.float64), t.astype(np.complex128), geom, n) for b in range(batch)]
     out = {}
     for flags in (0, pwf.FLAG_UNPACKED_RESID):
-        psi = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
         with plan_for(pwf, geom, batch, flags) as plan:
-            iters, loss = plan.solve(dev(y), dev(t), psi, n)
             desc = pwf.pwf_plan_describe(plan.handle)
+            first = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+            plan.reset()
+            plan.step(dev(y), dev(t), first)
+            loss1, _, _, _ = plan.read()
+            psi = torch.zeros((batch, ny, nx), dtype=torch.complex64, device="cuda")
+            iters, loss = plan.solve(dev(y), dev(t), psi, n)
         out[flags] = psi.cpu().numpy()
         for b in range(batch):
+            assert abs(loss1[b] - ref[b].losses[0]) <= 1e-5 * ref[b].losses[0], (flags, b, desc)
             assert iters[b] == n
             assert phase_rms(out[flags][b], ref[b].psi) <= PHASE_TOL, (flags, b, desc)
             assert abs(loss[b] - ref[b].losses[-1]) <= 1e-4 * ref[b].losses[-1], (flags, b, desc)
     exact = np.stack([r.psi for r in ref])
     err_pk = rel_l2(out[0], exact)
     err_un = rel_l2(out[pwf.FLAG_UNPACKED_RESID], exact)
-    assert err_pk <= 2.0 * max(err_un, 5e-5), (err_pk, err_un)
+    assert err_pk <= 4.0 * max(err_un, 5e-5) and err_un <= 4.0 * max(err_pk, 5e-5), (err_pk, err_un)
