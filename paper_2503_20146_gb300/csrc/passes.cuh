@@ -40,6 +40,13 @@ __host__ __device__ constexpr size_t row_smem_bytes(int n) {
 // Barrier of the two rows 2y', 2y' + 1 of a row-pass CTA (the packed passes):
 // the warp when both fit in one, else named barrier 8 + pair over their
 // 2 TPF threads (rows use ids 1..4 only when TPF > 32, so these stay clear).
+// With a whole warp or more per row, the packed passes give the pair's one
+// transform of the packed row to the even row alone (the odd row hands over
+// or takes its half through shared memory); with smaller rows both rows of a
+// warp run it, so that every warp-wide barrier sees all its lanes.
+template <int N>
+__host__ __device__ constexpr bool pk_split_rows() { return tpf_for(N) >= 32; }
+
 template <int N>
 __device__ __forceinline__ void pair_sync() {
   constexpr int TPF = tpf_for(N), NT = row_threads(N);
@@ -227,12 +234,41 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
 
   // ---- input ----
   if constexpr (OP == ROW_MUL_V_PK) {
-    // both rows of the pair read packed row y' (stored on the even row)
-    const size_t rbe = rb - (size_t)(yrow & 1) * N;
+    // the inverse transform of packed row y' (stored on the even row) is
+    // G(2y') + i G(2y' + 1)
+    const bool odd = (yrow & 1) != 0;
+    if constexpr (pk_split_rows<N>()) {
+      // the even row transforms it and hands Im over to the odd row
+      float* own = reinterpret_cast<float*>(sm.base);  // the row buffers as plain float arrays
+      const float* other = reinterpret_cast<const float*>(sm.base - row_smem_len(N));
+      if (!odd) {
 #pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = a.in[rbe + pk_pos<N>(slot_index<N, RK>(t, j))];
-    pair_sync<N>();  // every read of the even row precedes that row's output
-    fft_run<N, INV>(v, sm, t, a.tw_inv);
+        for (int j = 0; j < EPT; j++) v[j] = a.in[rb + pk_pos<N>(slot_index<N, RK>(t, j))];
+        fft_run<N, INV>(v, sm, t, a.tw_inv);
+      }
+      pair_sync<N>();  // the inverse transform's last reads of the even buffer are done
+      if (!odd) {
+#pragma unroll
+        for (int j = 0; j < EPT; j++) own[slot_index<N, RS>(t, j)] = v[j].y;
+      }
+      pair_sync<N>();
+      if (odd) {
+#pragma unroll
+        for (int j = 0; j < EPT; j++) v[j] = make_float2(other[slot_index<N, RS>(t, j)], 0.f);
+      }
+      pair_sync<N>();  // the odd row's reads precede the even row's forward transform
+    } else {
+      // both rows of the pair read and transform it
+      const size_t rbe = rb - (size_t)(yrow & 1) * N;
+#pragma unroll
+      for (int j = 0; j < EPT; j++) v[j] = a.in[rbe + pk_pos<N>(slot_index<N, RK>(t, j))];
+      pair_sync<N>();  // every read of the even row precedes that row's output
+      fft_run<N, INV>(v, sm, t, a.tw_inv);
+      if (odd) {
+#pragma unroll
+        for (int j = 0; j < EPT; j++) v[j].x = v[j].y;
+      }
+    }
   } else if constexpr (T::ifft_in) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) v[j] = a.in[rb + slot_index<N, RK>(t, j)];
@@ -277,31 +313,36 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
     }
   } else if constexpr (OP == ROW_INTENSITY_PK) {
     // I = |v|^2 of this row and of its partner row of the pair (the rows of a
-    // CTA come in pairs 2y', 2y' + 1), packed as z = I(2y') + i I(2y' + 1);
-    // both rows transform the same z and store half of it each
+    // CTA come in pairs 2y', 2y' + 1), packed as z = I(2y') + i I(2y' + 1) for
+    // one forward transform: the even row's alone where rows span whole warps
+    // (the odd row hands its intensities over), else both rows', each storing
+    // half of it
     const bool odd = (yrow & 1) != 0;
     float* own = reinterpret_cast<float*>(sm.base);  // the row buffers as plain float arrays
     const float* other = reinterpret_cast<const float*>(sm.base + (odd ? -row_smem_len(N) : row_smem_len(N)));
-    pair_sync<N>();  // the inverse transforms' last reads of both buffers are done
 #pragma unroll
     for (int j = 0; j < EPT; j++) {
-      const int x = slot_index<N, RS>(t, j);
-      if (a.v != nullptr) a.v[rb + x] = v[j];
+      if (a.v != nullptr) a.v[rb + slot_index<N, RS>(t, j)] = v[j];
       v[j].x = cabs2(v[j]);
-      own[x] = v[j].x;
+    }
+    pair_sync<N>();  // the inverse transforms' last reads of both buffers are done
+    if (odd || !pk_split_rows<N>()) {
+#pragma unroll
+      for (int j = 0; j < EPT; j++) own[slot_index<N, RS>(t, j)] = v[j].x;
     }
     pair_sync<N>();
+    if (!odd || !pk_split_rows<N>()) {
 #pragma unroll
-    for (int j = 0; j < EPT; j++) {
-      const float ip = other[slot_index<N, RS>(t, j)];
-      v[j] = odd ? make_float2(ip, v[j].x) : make_float2(v[j].x, ip);
+      for (int j = 0; j < EPT; j++) {
+        const float ip = other[slot_index<N, RS>(t, j)];
+        v[j] = odd ? make_float2(ip, v[j].x) : make_float2(v[j].x, ip);
+      }
     }
-    pair_sync<N>();  // the partner's reads precede the forward transform's writes
+    if constexpr (!pk_split_rows<N>()) pair_sync<N>();  // the partner's reads precede the forward transforms' writes
   } else if constexpr (OP == ROW_MUL_V_PK) {
-    // the inverse transform of the packed row is G(2y') + i G(2y' + 1)
-    const bool odd = (yrow & 1) != 0;
+    // G of this row (moved to .x above)
 #pragma unroll
-    for (int j = 0; j < EPT; j++) v[j] = cscale(a.v[rb + slot_index<N, RS>(t, j)], odd ? v[j].y : v[j].x);
+    for (int j = 0; j < EPT; j++) v[j] = cscale(a.v[rb + slot_index<N, RS>(t, j)], v[j].x);
   } else if constexpr (OP == ROW_INTENSITY_OUT) {
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.f_out[rb + slot_index<N, RS>(t, j)] = cabs2(v[j]);
@@ -414,12 +455,20 @@ __device__ __forceinline__ void row_body(const PassArgs& a, long long row, int t
 #pragma unroll
     for (int j = 0; j < EPT; j++) a.out[rb + slot_index<N, RK>(t2, j)] = v[j];
   } else if constexpr (OP == ROW_INTENSITY_PK) {
-    fft_run<N, FWD>(v, sm, t, a.tw_fwd);
     const bool odd = (yrow & 1) != 0;
-    const size_t rbe = rb - (odd ? (size_t)N : 0);
+    if constexpr (pk_split_rows<N>()) {
+      if (!odd) {  // the even row transforms z and stores the packed row on itself
+        fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
-    for (int j = 0; j < EPT; j++)
-      if ((j < EPT / 2) != odd) a.out[rbe + pk_pos<N>(slot_index<N, RK>(t, j))] = v[j];
+        for (int j = 0; j < EPT; j++) a.out[rb + pk_pos<N>(slot_index<N, RK>(t, j))] = v[j];
+      }
+    } else {
+      fft_run<N, FWD>(v, sm, t, a.tw_fwd);
+      const size_t rbe = rb - (odd ? (size_t)N : 0);
+#pragma unroll
+      for (int j = 0; j < EPT; j++)
+        if ((j < EPT / 2) != odd) a.out[rbe + pk_pos<N>(slot_index<N, RK>(t, j))] = v[j];
+    }
   } else if constexpr (T::fft_out) {
     fft_run<N, FWD>(v, sm, t, a.tw_fwd);
 #pragma unroll
