@@ -63,5 +63,6 @@ def test_instruction_count_only_for_the_captured_sources(monkeypatch):
 def test_selected_shape_ids_parse_the_plan_description():
     import bench
     d = ("ny=1024 nx=1024 batch=180 solver=graph loop=none col_q=C8s2[C8p:0.98,C8s2:0.88,C8s2@8.8.16:0.90] "
-         "col_iotf=C8s2@8.8.16[C8p:0.92,C8s2:0.87,C8s2@8.8.16:0.85] col_fft=C8p")
-    assert bench.selected_shape_ids(d) == [1, 2, None]
+         "col_iotf=C8s2@8.8.16[C8p:0.92,C8s2:0.87,C8s2@8.8.16:0.85] col_fft=C8p "
+         "col_resid_pk=C16s2@8.8.16[C8s2:0.74,C16s2:0.71,C16s2@8.8.16:0.70]")
+    assert bench.selected_shape_ids(d) == [1, 2, None, 2]
