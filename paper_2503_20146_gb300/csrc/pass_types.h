@@ -67,7 +67,8 @@ struct PassArgs {
   int accumulate;
   int* kstatus;            // device word set to PWF_ERR_TIMEOUT (7) when a bounded wait runs out
   int pdl;                 // launch with the programmatic stream-serialization attribute
-  CUtensorMap tmap;        // TMA map of `in` (filled by the launcher of a TMA-staged shape)
+  int l2pf;                // single-buffered pair shapes: tmap maps `in`; prefetch the next tile into L2
+  CUtensorMap tmap;        // TMA map of `in` (filled by the launcher of a TMA-staged or prefetching shape)
 };
 
 enum RowOp : int {

@@ -804,11 +804,22 @@ __device__ __forceinline__ void col_pair_filter(const PassArgs& a, int t, int co
   }
 }
 
+// rows of a tensor-map box over a column of n rows (a box dimension is at most 256)
+__host__ __device__ constexpr int tma_box_rows(int n) { return n < 256 ? n : 256; }
+// L2 prefetch of one box of a 3-D tensor map (a hint: no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap* tm, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(tm), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
 // NBUF = 2: tile k + 1 is copied while tile k is transformed (one CTA per SM
 // at 8 columns); NBUF = 1: one buffer, the copy of the next tile starts after
-// the current one is done, and the overlap comes from the second CTA on the SM.
+// the current one is done, and the overlap comes from the second CTA on the SM;
+// with a.l2pf, thread 0 then prefetches the next tile into L2 (a few tensor-map
+// boxes), so that its copy waits on L2 rather than DRAM.
 template <int N, int OP, int C, int NBUF>
-__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col_kernel_pipe2(const PassArgs a, int nproj) {
+__global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C))
+    col_kernel_pipe2(const __grid_constant__ PassArgs a, int nproj) {
   pdl_wait();
   constexpr int EPT = ept_for(N);
   constexpr int NT = col2_threads(N, C);
@@ -858,6 +869,17 @@ __global__ void __launch_bounds__(col2_threads(N, C), col2_min_blocks(N, C)) col
       prefetch(tile, cur);
       cp_async_commit();
       cp_async_wait<0>();
+      if (a.l2pf && tid == 0) {
+        constexpr int PB = tma_box_rows(N);
+        const int next = tile + gridDim.x;
+        if (next < ntiles) {
+          int np, nc;
+          (void)tile_base(next, np, nc);
+          if (!skip_proj(a, np))
+#pragma unroll
+            for (int k = 0; k < N / PB; k++) tma_prefetch_l2_3d(&a.tmap, 2 * nc, k * PB, np);
+        }
+      }
     }
     __syncthreads();
 
@@ -1172,7 +1194,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   __syncthreads();
   return false;
 }
-__host__ __device__ constexpr int tma_box_rows(int n) { return n < 256 ? n : 256; }
 __host__ __device__ constexpr size_t tma_smem_bytes(int n, int c) { return (size_t)n * c * sizeof(float2) + 1024; }
 
 template <int N, int OP, int C>
@@ -1576,9 +1597,12 @@ struct ColShape {
       } else if constexpr (PIPE == 3)
         return launch_pass(col_kernel_pipe2<N, OP, C, 2>, dim3(grid), dim3(col2_threads(N, C)), colp_smem_bytes(N, C), s,
                            a.pdl, a, nproj);
-      else if constexpr (PIPE == 4)
+      else if constexpr (PIPE == 4) {
+        PassArgs b = a;  // with a tensor map of the field, the kernel prefetches each next tile into L2
+        b.l2pf = encode_field_tmap(&b.tmap, a.in, a.proj0 + nproj, a.ny, a.nx, C) ? 1 : 0;
         return launch_pass(col_kernel_pipe2<N, OP, C, 1>, dim3(grid), dim3(col2_threads(N, C)), col_smem_bytes(N, C), s,
-                           a.pdl, a, nproj);
+                           a.pdl, b, nproj);
+      }
       else if constexpr (PIPE == 2)
         return launch_pass(col_kernel_t<N, OP, C>, dim3(grid), dim3(col_threads(N, C)), colt_smem_bytes(N, C), s, a.pdl, a,
                            nproj);
